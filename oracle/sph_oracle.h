@@ -1,0 +1,95 @@
+/* sph_oracle.h -- plain FP64 CPU oracle of the coupled fluid-solid-thermal
+ * weakly-compressible SPH step (test infrastructure only).
+ *
+ * This is a slow, obviously-correct restatement of the paper's equations:
+ * brute-force O(N^2) neighbour search, particles kept in id order, every sum
+ * a plain loop in ascending neighbour id.  Only the test suite, the package
+ * smoke check and the benchmark's CPU-baseline leg may call it; the CUDA
+ * product path never does.  It shares no code with the CUDA library.
+ *
+ * Section / equation references are to the paper (arXiv 2512.09904):
+ *   Sec. 2.1  mass/momentum equations Eq. (1), linear EoS Eq. (2)
+ *   Sec. 2.3  Riemann-based continuity and momentum, Eqs. (10)-(13)
+ *   Sec. 2.4  density re-initialisation, Eqs. (14)-(15)
+ *   Sec. 2.5  wall dummy particles, one-sided Riemann, Eqs. (16)-(19)
+ *   Sec. 2.6  Cleary heat conduction, Eqs. (20)-(22)
+ *   Sec. 2.8  dual-criteria time stepping, Eqs. (25)-(26)
+ */
+#ifndef SPH_ORACLE_H
+#define SPH_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double origin[3], extent[3]; /* domain box (periodic axes wrap on it) */
+    double dx, h_over_dx;        /* lattice spacing; h = h_over_dx * dx */
+    double gravity[3];
+    double c0, u_ref;            /* artificial sound speed; velocity floor */
+    double cfl_ad, cfl_ac;       /* 0.25, 0.6 (Sec. 2.8) */
+    int free_surface;            /* 1: Eq. (14) max() form; 0: Eq. (15) */
+    int periodic_mask;           /* bit a: axis a periodic */
+    int max_substeps;            /* acoustic sub-steps cap per advection step; 0 = default */
+} orc_config;
+
+typedef struct { double rho0, mu, k, cp, T_init; int fixed_T; } orc_material;
+
+typedef struct orc_sim orc_sim;
+
+/* --- scalar pieces (pinned individually by the tests) -------------------- */
+double orc_W(double r, double h);      /* Wendland C2, 3-D, support 2h */
+double orc_dW(double r, double h);     /* dW/dr */
+double orc_sigma0(double dx, double h);/* sum of W over an exact cubic lattice incl. self */
+/* fluid-fluid Riemann (Sec. 2.3): returns U*, p* for states (rho,U,p) L/R */
+void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR, double pR,
+                 double c0, double* Ustar, double* pstar);
+/* wall one-sided Riemann (Sec. 2.5): right state and interface values */
+void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_dot_rfw,
+                      double rho0, double c0, double* UR, double* PR, double* rhoR,
+                      double* Ustar, double* pstar);
+void orc_timesteps(double h, double vmax, double u_ref, double nu_max, double c0,
+                   double cfl_ad, double cfl_ac, double* dt_ad, double* dt_ac);
+double orc_dt_thermal(double rho, double cp, double h, double k);
+
+/* brute-force pair list: pairs (i,j), 0 < |r_i - r_j|^2 < R2 (FP64, strict),
+ * minimum image on periodic axes.  counts[i] = neighbours of i; if list is
+ * non-NULL it receives, for each i in order, its neighbours in ascending j.
+ * Returns total pair entries, or -1 if cap is too small. */
+int64_t orc_neighbors(int64_t n, const double* pos, double R2, int periodic_mask,
+                      const double* extent, int64_t* counts, int32_t* list, int64_t cap);
+/* expected cell order: key = linear cell index (x fastest) of
+ * floor((x - origin)/w) per axis, clamped to the grid; particles sorted by
+ * (key, id).  perm[k] = id at sorted position k; cell_start has ncell+1. */
+void orc_cell_order(int64_t n, const double* pos, const double* origin, const double* cellw,
+                    const int* ncell, int64_t* perm, int64_t* cell_start);
+
+/* --- whole simulation ---------------------------------------------------- */
+orc_sim* orc_create(const orc_config* cfg);
+void orc_destroy(orc_sim*);
+int orc_set_threads(int n);
+int orc_set_material(orc_sim*, int id, const orc_material*);
+int orc_set_rotation(orc_sim*, int body, const double c[3], const double axis[3], double omega);
+/* kind: 0 fluid, 1 solid; body: -1 static; rho NaN -> material rho0 */
+int orc_add_particles(orc_sim*, int64_t n, const int* kind, const int* mat, const int* body,
+                      const double* pos, const double* vel, const double* normal,
+                      const double* T, const double* rho);
+int orc_step(orc_sim*, int n_adv);
+/* fields (id order): 0 pos[3], 1 vel[3], 2 rho, 3 p, 4 T, 5 drho, 6 a_visc[3], 7 dTdt,
+ * 8 sigma (kernel sum of pass D), 9 wall normal[3], 10 wall velocity[3] */
+int orc_get_field(const orc_sim*, int field, double* out);
+/* body: torque about its axis (last sub-step), dt-weighted average since
+ * start, heat into fluid sum m cp (T - T0), mean fluid temperature */
+int orc_torque_heat(const orc_sim*, int body, double* torque, double* torque_avg,
+                    double* heat_into_fluid, double* mean_fluid_T);
+/* body: total force of the fluid on the body (last sub-step; pressure + viscous) */
+int orc_body_force(const orc_sim*, int body, double* force3);
+int orc_time(const orc_sim*, double* t, int64_t* adv_steps, int64_t* substeps,
+             double* last_dt_ad, int* last_nsub);
+int64_t orc_count(const orc_sim*);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

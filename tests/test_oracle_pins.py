@@ -1,0 +1,368 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle.
+
+Each test names what fixes the expected value: a closed form, an integral,
+a lattice count, a library routine, a conservation law, or the analytic
+solution of the paper's own conduction validation (Sec. 3.2).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.spatial import cKDTree
+from scipy.special import erf, erfc
+
+from paper_2512_09904_b300 import workloads as W
+
+DX = 1e-3
+H = 1.3e-3
+
+
+# ---------------------------------------------------------------- kernel ---
+def test_kernel_integrates_to_one(oracle):
+    # normalisation of a smoothing kernel: integral of W over R^3 is 1
+    val, _ = integrate.quad(lambda r: oracle.W(r, H) * 4 * math.pi * r * r, 0, 2 * H, epsabs=1e-14)
+    assert abs(val - 1.0) < 1e-10
+
+
+def test_kernel_compact_support_and_positivity(oracle):
+    rs = np.linspace(0, 2 * H, 401)[:-1]
+    assert all(oracle.W(r, H) > 0 for r in rs)
+    assert oracle.W(2 * H, H) == 0.0 and oracle.W(2.5 * H, H) == 0.0
+    assert oracle.dW(2 * H, H) == 0.0
+    # monotone decreasing
+    w = np.array([oracle.W(r, H) for r in rs])
+    assert np.all(np.diff(w) < 0)
+
+
+def test_kernel_derivative_matches_finite_difference(oracle):
+    for q in [0.05, 0.3, 0.77, 1.0, 1.5, 1.9]:
+        r, e = q * H, 1e-7 * H
+        fd = (oracle.W(r + e, H) - oracle.W(r - e, H)) / (2 * e)
+        assert abs(oracle.dW(r, H) - fd) <= 1e-6 * abs(fd)
+    assert oracle.dW(0.0, H) == 0.0
+
+
+def test_kernel_second_moment_identity(oracle):
+    # integral of r dW/dr dV = -3 (integration by parts of the normalisation)
+    val, _ = integrate.quad(lambda r: r * oracle.dW(r, H) * 4 * math.pi * r * r, 0, 2 * H, epsabs=1e-14)
+    assert abs(val + 3.0) < 1e-9
+
+
+def test_sigma0_tends_to_integral(oracle):
+    # the lattice kernel sum times dx^3 is a quadrature of the unit integral
+    assert abs(oracle.sigma0(DX, 3.0 * DX) * DX ** 3 - 1.0) < 1e-3
+    assert abs(oracle.sigma0(DX, H) * DX ** 3 - 1.0) < 2e-2
+
+
+def test_lattice_neighbour_count(oracle):
+    # support 2h = 2.6 dx: integer points with 0 < |p|^2 < 6.76 -> |p|^2 in {1..6}
+    # 6 + 12 + 8 + 6 + 24 + 24 = 80 neighbours
+    idx = np.stack(np.meshgrid(*[np.arange(-4, 5)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = idx * DX
+    counts, lst = oracle.neighbors(pos, (2 * H) ** 2)
+    centre = np.flatnonzero((idx == 0).all(1))[0]
+    assert counts[centre] == 80
+    # the kernel sum over those neighbours plus self equals sigma0
+    start = np.concatenate([[0], np.cumsum(counts)])
+    nb = lst[start[centre]:start[centre + 1]]
+    s = oracle.W(0, H) + sum(oracle.W(np.linalg.norm(pos[j] - pos[centre]), H) for j in nb)
+    assert abs(s - oracle.sigma0(DX, H)) < 1e-9 * s
+
+
+# ------------------------------------------------------- neighbour search ---
+def test_neighbors_match_kdtree(oracle):
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0, 0.02, size=(3000, 3))
+    R = 2 * H
+    counts, lst = oracle.neighbors(pos, R * R)
+    pairs = cKDTree(pos).query_pairs(R, output_type="ndarray")
+    ref = set(map(tuple, pairs)) | set(map(tuple, pairs[:, ::-1]))
+    start = np.concatenate([[0], np.cumsum(counts)])
+    got = {(i, int(j)) for i in range(len(pos)) for j in lst[start[i]:start[i + 1]]}
+    assert got == ref
+    # ascending order within each particle's list
+    for i in range(0, len(pos), 97):
+        seg = lst[start[i]:start[i + 1]]
+        assert np.all(np.diff(seg) > 0)
+
+
+def test_neighbors_periodic_minimum_image(oracle):
+    rng = np.random.default_rng(4)
+    L = 0.012
+    pos = rng.uniform(0, L, size=(800, 3))
+    R = 2 * H
+    counts, lst = oracle.neighbors(pos, R * R, periodic_mask=0b111, extent=(L, L, L))
+    tree = cKDTree(pos, boxsize=L)
+    pairs = tree.query_pairs(R, output_type="ndarray")
+    ref = set(map(tuple, pairs)) | set(map(tuple, pairs[:, ::-1]))
+    start = np.concatenate([[0], np.cumsum(counts)])
+    got = {(i, int(j)) for i in range(len(pos)) for j in lst[start[i]:start[i + 1]]}
+    assert got == ref
+
+
+def test_neighbors_cutoff_is_strict_fp64(oracle):
+    # pairs placed within a few ulps of R on both sides; the membership rule is
+    # the strict inequality on the FP64 squared distance ((dx^2 + dy^2) + dz^2)
+    case = W.cutoff_pairs(n_random=0, n_pairs=300)
+    pos = W.flatten(case)["pos"]
+    R = case.support_radius()
+    counts, lst = oracle.neighbors(pos, R * R)
+    start = np.concatenate([[0], np.cumsum(counts)])
+    n = 300
+    inside = 0
+    for p in range(n):
+        i, j = p, p + n
+        d = pos[i] - pos[j]
+        r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+        expect = bool(0.0 < r2 < R * R)
+        got = j in set(lst[start[i]:start[i + 1]].tolist())
+        assert got == expect
+        inside += expect
+    assert 0 < inside < n  # both sides of the cut-off are exercised
+
+
+def test_cell_order_matches_lexsort(oracle):
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(-0.001, 0.021, size=(5000, 3))
+    origin = np.zeros(3)
+    ncell = np.array([7, 5, 6])
+    cellw = np.array([0.02 / 7, 0.02 / 5, 0.02 / 6])
+    perm, cs = oracle.cell_order(pos, origin, cellw, ncell)
+    c = np.clip(np.floor((pos - origin) / cellw), 0, ncell - 1).astype(np.int64)
+    key = (c[:, 2] * ncell[1] + c[:, 1]) * ncell[0] + c[:, 0]
+    ref = np.lexsort((np.arange(len(pos)), key))
+    assert np.array_equal(perm, ref)
+    assert np.array_equal(cs, np.searchsorted(key[ref], np.arange(ncell.prod() + 1)))
+
+
+# ------------------------------------------------------------- Riemann ----
+def test_riemann_equal_states(oracle):
+    us, ps = oracle.riemann(900.0, 0.3, 120.0, 900.0, 0.3, 120.0, 10.0)
+    assert us == pytest.approx(0.3, abs=1e-15) and ps == pytest.approx(120.0, abs=1e-12)
+
+
+def test_riemann_expansion_has_no_dissipation(oracle):
+    # U_L < U_R: the limiter gives beta = 0 and p* is the plain mean
+    us, ps = oracle.riemann(900.0, -0.2, 100.0, 950.0, 0.4, 50.0, 10.0)
+    assert ps == pytest.approx(75.0, abs=1e-12)
+    assert us == pytest.approx(0.1 + 50.0 / (10.0 * 1850.0), rel=1e-14)
+
+
+def test_riemann_strong_compression_is_acoustic(oracle):
+    # beta capped at c0: symmetric collision of equal states gives the
+    # acoustic-impedance result p* = p + rho c0 dU / 2
+    rho, c0, u = 1000.0, 10.0, 5.0
+    us, ps = oracle.riemann(rho, u, 0.0, rho, -u, 0.0, c0)
+    assert ps == pytest.approx(rho * c0 * (2 * u) / 2, rel=1e-14)
+    assert us == pytest.approx(0.0, abs=1e-15)
+
+
+def test_riemann_mirror_symmetry(oracle):
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        rl, rr = rng.uniform(800, 1200, 2)
+        ul, ur = rng.uniform(-3, 3, 2)
+        pl, pr = rng.uniform(-500, 500, 2)
+        us1, ps1 = oracle.riemann(rl, ul, pl, rr, ur, pr, 10.0)
+        us2, ps2 = oracle.riemann(rr, -ur, pr, rl, -ul, pl, 10.0)
+        assert ps1 == pytest.approx(ps2, rel=1e-13, abs=1e-9)
+        assert us1 == pytest.approx(-us2, rel=1e-13, abs=1e-12)
+
+
+def test_wall_riemann_still_wall(oracle):
+    # no gravity, wall and fluid at rest: mirror state equals the fluid state
+    s = oracle.wall_riemann(870.0, 0.0, 55.0, 0.0, 0.0, 870.0, 10.0)
+    assert s["UR"] == 0.0 and s["PR"] == 55.0
+    assert s["Ustar"] == pytest.approx(0.0, abs=1e-15) and s["pstar"] == pytest.approx(55.0, rel=1e-14)
+    # moving wall: the mirrored normal velocity is reflected about u_w
+    s = oracle.wall_riemann(870.0, 0.7, 0.0, 0.2, 0.0, 870.0 - 0.0, 10.0)
+    assert s["UR"] == pytest.approx(-0.3, abs=1e-15) and s["Ustar"] == pytest.approx(0.2, abs=1e-15)
+
+
+def test_wall_riemann_hydrostatic_extrapolation(oracle):
+    rho, g, dz, c0 = 870.0, 9.81, 1e-3, 10.0
+    s = oracle.wall_riemann(rho, 0.0, 100.0, 0.0, g * dz, rho, c0)
+    assert s["PR"] == pytest.approx(100.0 + rho * g * dz, rel=1e-14)
+    assert s["rhoR"] == pytest.approx(rho + s["PR"] / c0 ** 2, rel=1e-14)
+
+
+# ----------------------------------------------------------- time steps ---
+def test_substep_count_at_rest(oracle):
+    # fluid at rest: dt_ad = 0.25 h / u_ref, dt_ac = 0.6 h / c0 with c0 = 10 u_ref
+    # -> ceil(0.25/0.6 * 10) = 5 acoustic sub-steps per advection step
+    case = W.periodic_box(n=8, v_amp=0.0, rho_amp=0.0, jitter=0.0)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    t = sim.time()
+    h = case.config["h_over_dx"] * case.config["dx"]
+    assert t["nsub"] == 5
+    assert t["t"] == pytest.approx(0.25 * h / case.config["u_ref"], rel=1e-15)
+
+
+def test_viscous_bound_limits_dt_ad(oracle):
+    h, nu = 1.3e-3, 1.0
+    dt_ad, dt_ac = oracle.timesteps(h, 0.0, 1.0, nu, 10.0)
+    assert dt_ad == pytest.approx(0.25 * h * h / nu)
+    assert dt_ac == pytest.approx(0.6 * h / 10.0)
+
+
+def test_free_fall_is_exact(oracle):
+    # an isolated fluid particle has no neighbours: kick-drift-kick under
+    # constant gravity reproduces z0 - g t^2 / 2 and v = -g t
+    g = 9.81
+    cfg = W._cfg(origin=(0, 0, 0), extent=(1, 1, 1), dx=1e-3, gravity=(0, 0, -g))
+    case = W.Case("fall", cfg, {0: W._mat(1000, 1e-3, 0.6, 4000, 300)},
+                  [dict(mat=0, pos=np.array([[0.5, 0.5, 0.5]]), vel=None, T=None, rho=None)], [])
+    sim = oracle.OracleSim(case)
+    sim.step(7)
+    t = sim.time()["t"]
+    z = sim.field("pos")[0, 2]
+    v = sim.field("vel")[0, 2]
+    assert z == pytest.approx(0.5 - 0.5 * g * t * t, abs=1e-14)
+    assert v == pytest.approx(-g * t, rel=1e-12)
+
+
+# --------------------------------------------------------- pair physics ---
+def _lattice_case(n, vel_fn, g=(0, 0, 0), mu=0.0, rho0=1000.0, c0=10.0):
+    idx = W._grid((0, 0, 0), (n, n, n))
+    pos = (idx + 0.5) * DX
+    cfg = W._cfg(origin=(-5 * DX,) * 3, extent=((n + 10) * DX,) * 3, dx=DX, gravity=g, c0=c0,
+                 max_substeps=1)
+    mats = {0: W._mat(rho0, mu, 0.6, 4000, 300)}
+    case = W.Case("lattice", cfg, mats, [dict(mat=0, pos=pos, vel=vel_fn(pos), T=None, rho=None)], [])
+    centre = (n - 1) / 2 * DX + 0.5 * DX
+    interior = np.all(np.abs(pos - centre) < (n / 2 - 3) * DX, axis=1)
+    return case, pos, interior
+
+
+def test_continuity_recovers_divergence(oracle):
+    # Eq. (10) continuity with equal pressures reduces to rho sum V v_ij.grad W,
+    # i.e. -rho div v: uniform expansion v = eps r gives drho/dt = -3 eps rho
+    eps = 1e-2
+    case, pos, interior = _lattice_case(12, lambda p: eps * (p - p.mean(0)))
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    drho = sim.field("drho")[interior]
+    rho = sim.field("rho")[interior]
+    ratio = drho / (-3.0 * eps * rho)
+    assert np.all(np.abs(ratio - 1.0) < 0.03)
+
+
+def test_viscous_term_recovers_laplacian(oracle):
+    # Eq. (10) viscous term: for v_x = gam z^2 the Laplacian is 2 gam, so
+    # a_visc_x = mu / rho * 2 gam in the interior
+    gam, mu, rho0 = 50.0, 0.2, 1000.0
+    case, pos, interior = _lattice_case(12, lambda p: np.stack(
+        [gam * p[:, 2] ** 2, 0 * p[:, 0], 0 * p[:, 0]], 1), mu=mu, rho0=rho0)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    av = sim.field("a_visc")[interior]
+    ratio = av[:, 0] / (mu / rho0 * 2 * gam)
+    assert np.all(np.abs(ratio - 1.0) < 0.03)
+    assert np.abs(av[:, 1:]).max() < 1e-6 * mu / rho0 * 2 * gam
+
+
+def test_momentum_conserved_in_periodic_box(oracle):
+    # pair forces are antisymmetric (Eqs. 10-12): total momentum is constant
+    case = W.periodic_box(n=10)
+    sim = oracle.OracleSim(case)
+    m = case.materials[0]["rho0"] * case.config["dx"] ** 3
+    P0 = m * sim.field("vel").sum(0)
+    scale = m * np.abs(sim.field("vel")).sum()
+    sim.step(4)
+    P1 = m * sim.field("vel").sum(0)
+    assert np.abs(P1 - P0).max() < 1e-12 * scale
+    assert sim.time()["substeps"] > 4
+
+
+def test_thermal_energy_conserved(oracle):
+    # Cleary form (Eq. 22) is pairwise antisymmetric: sum m cp T is constant
+    case = W.periodic_box(n=10)
+    sim = oracle.OracleSim(case)
+    m = case.materials[0]["rho0"] * case.config["dx"] ** 3
+    cp = case.materials[0]["cp"]
+    E0 = (m * cp * sim.field("T")).sum()
+    T0 = sim.field("T").copy()
+    sim.step(3)
+    T1 = sim.field("T")
+    assert np.abs(T1 - T0).max() > 1e-6  # heat actually flowed
+    assert abs((m * cp * T1).sum() - E0) < 1e-13 * E0
+
+
+def test_slab_conduction_matches_erf_solution(oracle):
+    # Sec. 3.2 / Table 3: two semi-infinite media in contact; interface
+    # temperature from the contact coefficients e = sqrt(k rho cp).  Note the
+    # table's diffusivities alpha = k / (rho cp): 0.001 and 0.0015.
+    case = W.slab()
+    m = case.materials
+    assert m[0]["k"] / (m[0]["rho0"] * m[0]["cp"]) == pytest.approx(0.001)
+    assert m[1]["k"] / (m[1]["rho0"] * m[1]["cp"]) == pytest.approx(0.0015)
+    sim = oracle.OracleSim(case)
+    cp_rho = np.where(W.flatten(case)["mat"] == 0, 1000.0, 2000.0)
+    E0 = (cp_rho * sim.field("T")).sum()
+    sim.step(100)
+    t = sim.time()["t"]
+    assert t == pytest.approx(2.0, rel=1e-12)
+    x = sim.field("pos")[:, 0]
+    T = sim.field("T")
+    el, er = math.sqrt(1.0 * 1000 * 1.0), math.sqrt(3.0 * 2000 * 1.0)
+    Ti = er / (el + er)
+    ana = np.where(x < 0.5, Ti * erfc((0.5 - x) / (2 * np.sqrt(0.001 * t))),
+                   Ti + (1 - Ti) * erf((x - 0.5) / (2 * np.sqrt(0.0015 * t))))
+    assert np.abs(T - ana).max() < 1e-2
+    # closed adiabatic system: thermal energy conserved
+    assert abs((cp_rho * T).sum() - E0) < 1e-12 * E0
+
+
+@pytest.mark.slow
+def test_still_tank_relaxes_to_hydrostatic(oracle):
+    # still oil tank (reduced 12x12x8 lattice so the O(N^2) oracle runs in
+    # seconds): after 200 advection steps the pressure is hydrostatic
+    case = W.still_tank(nx=12, ny=12, nz=8, wall_h=12)
+    # the tank walls form one non-rotating body so the fluid's force on them
+    # can be read back
+    for s in case.solids:
+        s["body"] = 0
+    case.bodies[0] = dict(center=[0.0, 0.0, 0.0], axis=[0.0, 0.0, 1.0], omega=0.0)
+    sim = oracle.OracleSim(case)
+    sim.step(200)
+    fl = sim.kind == 0
+    z = sim.field("pos")[fl, 2]
+    p = sim.field("p")[fl]
+    rho0, g, Hs = 870.0, 9.81, case.meta["H"]
+    scale = rho0 * g * Hs
+    err = p - rho0 * g * (Hs - z)
+    assert np.abs(err).mean() < 0.02 * scale
+    slope = np.polyfit(z, p, 1)[0]
+    assert slope == pytest.approx(-rho0 * g, rel=0.03)
+    assert np.abs(sim.field("vel")[fl]).max() < 1e-3 * case.config["c0"]
+    # at rest the walls carry the oil's weight (Newton's third law on the
+    # wall pressure and viscous forces, Eqs. 18-19)
+    weight = rho0 * case.config["dx"] ** 3 * fl.sum() * g
+    F = sim.body_force(0)
+    assert F[2] == pytest.approx(-weight, rel=0.05)  # instantaneous: acoustic ringing remains
+    assert abs(F[0]) < 0.01 * weight and abs(F[1]) < 0.01 * weight
+    # the hot bottom wall has started heating the oil
+    th = sim.torque_heat(0)
+    assert th["heat"] > 0.0 and th["mean_T"] > 313.15
+
+
+def test_rotating_cylinder_drag_opposes_rotation(oracle):
+    # fluid at rest around a spinning rigid cylinder: the wall viscous term
+    # (Eq. 18) drags the fluid along, so the fluid's torque on the body opposes
+    # omega; the pressure torque of a radially symmetric body vanishes at start
+    for omega in (50.0, -50.0):
+        case = W.rotating_cylinder(omega=omega, jitter=0.0)
+        sim = oracle.OracleSim(case)
+        sim.step(1)
+        th = sim.torque_heat(0)
+        assert th["torque_avg"] * omega < 0.0
+        assert th["torque"] * omega < 0.0
+        # the fixed-temperature hot cylinder heats the fluid
+        assert th["heat"] > 0.0
+        v = sim.field("vel")[sim.kind == 0]
+        p = sim.field("pos")[sim.kind == 0] - np.array(case.bodies[0]["center"])
+        # fluid near the wall moves with the wall: positive angular velocity sense
+        lz = p[:, 0] * v[:, 1] - p[:, 1] * v[:, 0]
+        assert lz.sum() * omega > 0.0
