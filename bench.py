@@ -1,0 +1,284 @@
+"""Benchmark: coupled SPH step on the 2M-oil gear bath (one B300 per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A "step" is one advection step of the coupled method (Sec. 2.8): the cell
+sort, density re-initialisation, viscous and thermal passes, and all its
+acoustic sub-steps (Riemann pressure force + continuity), plus the FP64
+torque / heat reductions.  The metric is oil particle-substeps per second:
+(oil particles) x (acoustic sub-steps) / device time.  Inputs are seeded
+synthetic data of the paper's workload shape (spur gear, pitch radius 50 mm,
+24 teeth, omega = 600 rad/s, half immersed), resident in HBM and far larger
+than L2.  N > 1 runs independent replicas (one case per GPU, weak scaling).
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (coupled step, 2M)"
+UNIT = "oil particle-substeps/s"
+
+# FP32 operations per directed pair, counted from the pair arithmetic of the
+# kernels (distance, kernel derivative, Riemann state, accumulation; FMA = 2):
+FLOP_M = dict(ff=53, fw=43)   # pass M: fluid-fluid, fluid-wall
+FLOP_C = dict(ff=40, fw=56)   # pass C
+# HBM bytes per oil particle per launch (own state in and out; neighbour data
+# is served from L1/L2): pass M reads snapshot 16, state 16, rate 4, viscous
+# acceleration 16, cell 4, position 24 and writes state 16, position 24;
+# pass C reads snapshot 16, state 16, cell 4 and writes state 16, rate 4.
+BYTES_M, BYTES_C = 120, 56
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dx", type=float, default=1e-3)
+    ap.add_argument("--omega", type=float, default=600.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(dx, omega):
+    from paper_2512_09904_b300 import workloads as W
+    return W.gear_bath(dx=dx, omega=omega, depth_frac=0.5, mu=0.1)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) around the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as g:
+            for line in g:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(omega, steps=1):
+    """The FP64 O(N^2) oracle, as it stands, on a bounded sample of the
+    workload: the same gear bath at dx = 5 mm, one advection step per step."""
+    from oracle import oracle as O
+    threads = O.set_threads(0)
+    case = workload(5e-3, omega)
+    sim = O.OracleSim(case)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sub = sim.time()["substeps"]
+    return dict(value=case.n_fluid * sub / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"gear bath at dx=5 mm ({case.n_fluid} oil + {case.n_solid} solid particles), "
+                       f"{steps} advection step(s) = {sub} sub-steps, brute-force FP64 oracle",
+                seconds=dt)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    from oracle import oracle as O
+    threads = O.set_threads(0)
+    case = workload(5e-3, args.omega)
+    sim = O.OracleSim(case)
+    sim.step(warm)
+    s0 = sim.time()["substeps"]
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sub = sim.time()["substeps"] - s0
+    v = case.n_fluid * sub / dt
+    sample = (f"gear bath at dx=5 mm ({case.n_fluid} oil + {case.n_solid} solid particles), "
+              f"omega={args.omega}; the O(N^2) oracle cannot run the 2.19M-oil case")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "gear_bath_coarse_5mm", "n_fluid": case.n_fluid, "n_solid": case.n_solid},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2512_09904_b300 import sph
+
+    case = workload(args.dx, args.omega)
+    stream = torch.cuda.current_stream()
+    ctx = sph.from_case(case, stream=stream.cuda_stream)
+    ctx.sph_step(1)                     # upload + first advection step
+    ctx.sph_profile(True)               # event records between kernel groups
+    ctx.sph_step(max(args.warmup, 3) - 1)
+    info0 = ctx.sph_get_info()
+    ctx.sph_profile_read(reset=True)
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.sph_step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    info1 = ctx.sph_get_info()
+    prof = ctx.sph_profile_read(reset=True)
+    substeps = info1["substeps"] - info0["substeps"]
+    units = case.n_fluid * substeps
+    ff, fw = ctx.sph_pair_stats()
+    th = ctx.sph_read_torque_heat(0)
+    ctx.close()
+    del ctx
+
+    if world > 1:
+        t = torch.tensor([ms, float(units)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, units_all = float(tmax[0]), float(t[1])
+    else:
+        ms_max, units_all = ms, float(units)
+    value = units_all / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (largest share of device time)
+    peaks, src = measured_peaks()
+    dom = max(("pass_M", "pass_C"), key=lambda k: prof[k][0])
+    dms, dcnt = prof[dom]
+    avg_s = dms / max(dcnt, 1) * 1e-3
+    fl = FLOP_M if dom == "pass_M" else FLOP_C
+    flops = ff * fl["ff"] + fw * fl["fw"]
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
+    achieved = flops / avg_s / 1e12
+    bytes_launch = case.n_fluid * (BYTES_M if dom == "pass_M" else BYTES_C)
+    hbm_gbs = bytes_launch / avg_s / 1e9
+    total_prof = sum(v[0] for v in prof.values())
+    roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max from {src} peaks file)",
+                "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
+                "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw,
+                "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
+                        "frac": hbm_gbs / peaks.get("hbm_gbs", 6505.9), "bytes_per_launch": bytes_launch},
+                "share": {k: round(v[0] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "gear_bath_2M_omega600", "n_fluid": case.n_fluid, "n_solid": case.n_solid,
+                      "dx": args.dx, "omega": args.omega, "substeps_timed": substeps,
+                      "pair_arith": "f32", "integration_and_reductions": "f64",
+                      "l2": "inputs larger than L2 (~0.7 GB resident state)",
+                      "parallelism": f"replicas x{world}", "torque_avg_Nm": th["torque_avg"],
+                      "heat_J": th["heat"]},
+           "roofline": roofline,
+           "gpu_launches": int(info1["graph_launches"]) * args.steps,
+           "clocks": clk}
+
+    # end to end through the C ABI from host arrays: create + upload + steps +
+    # per-step torque/heat read + final temperature field read
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = sph.from_case(case, stream=stream.cuda_stream)
+        for _ in range(args.steps):
+            c2.sph_step(1)
+            c2.sph_read_torque_heat(0)
+        T = c2.sph_read_fields("T")
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sub2 = c2.sph_get_info()["substeps"]
+        c2.close()
+        n = case.n_total
+        h2d = n * (24 + 24 + 16 + 16 + 8 + 4 + 4)
+        d2h = args.steps * 4 * 8 + T.nbytes
+        out["e2e"] = {"value": case.n_fluid * sub2 / wall, "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+                      "note": "includes context creation, upload, graph capture and the first cell sort"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.omega)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

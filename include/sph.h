@@ -1,0 +1,216 @@
+/* sph.h -- C ABI of the B300 (sm_103a) coupled fluid-solid-thermal SPH library.
+ *
+ * One library call advances weakly-compressible SPH particles through the
+ * method of arXiv 2512.09904 (Sec. 2): a cell-linked-list neighbour search,
+ * Riemann-based continuity and pressure force, viscous force, fluid-wall and
+ * rotating-rigid-body coupling, Cleary heat conduction, and dual-criteria
+ * time integration.  Every step runs in this library's CUDA kernels; there is
+ * no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns sph_status and never throws.  On error,
+ *    sph_last_error(ctx) gives a one-line message (per context).
+ *  - Pointers documented as "host" are read (or written) before the call
+ *    returns; the caller keeps ownership.  Pointers documented as "device"
+ *    must be CUDA device allocations on the current device.
+ *  - Device memory of a context is allocated by the library (cudaMalloc) and
+ *    freed by sph_destroy / sph_batch_destroy.
+ *  - Work is issued on the CUDA stream given at creation (NULL = legacy
+ *    default stream).  Calls that return host data synchronise that stream.
+ *  - One context must not be used by two host threads at the same time.
+ *  - Particle ids are assigned in call order starting at 0; fields are read
+ *    back in id order.  Particles may only be added before the first step
+ *    (SPH_ESTATE afterwards).
+ *  - Units are SI, temperatures in kelvin.
+ */
+#ifndef SPH_B300_H
+#define SPH_B300_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_EINVAL = -1,    /* bad argument (size, id, layout) */
+    SPH_ENOMEM = -2,    /* device allocation or admission budget failed */
+    SPH_ECUDA = -3,     /* a CUDA runtime call failed */
+    SPH_EUNSTABLE = -4, /* NaN/Inf state or a fluid particle left the domain box */
+    SPH_ETIMEOUT = -5,  /* reserved: a bounded device wait gave up */
+    SPH_ESTATE = -6     /* call not valid in the current state */
+} sph_status;
+
+/* Case configuration.  The domain box holds every particle for the whole run;
+ * it is cut into cells of width >= 2h per axis (27-cell neighbour stencil).
+ * A periodic axis wraps particle positions on this machine and needs at least 3
+ * cells along it. */
+typedef struct {
+    double origin[3], extent[3]; /* domain box, m */
+    double dx;                   /* particle spacing, m (mass = rho0 dx^3, wall volume dx^3) */
+    double h_over_dx;            /* smoothing length h = h_over_dx * dx (Wendland C2, support 2h) */
+    double gravity[3];           /* m/s^2 */
+    double c0;                   /* artificial sound speed of the EoS p = c0^2 (rho - rho0), Eq. (2) */
+    double u_ref;                /* velocity floor of the advection criterion, normally c0/10 */
+    double cfl_ad, cfl_ac;       /* 0.25 and 0.6 in the paper, Eq. (25) */
+    int free_surface;            /* 1: re-initialise rho = max(rho, rho0 sumW/sumW0), Eq. (14); 0: Eq. (15) */
+    int periodic_mask;           /* bit a set: axis a is periodic */
+    int max_substeps;            /* cap on acoustic sub-steps per advection step; 0 = ceil(cfl_ad/cfl_ac (c0/u_ref + 1)) + 2 */
+} sph_config;
+
+/* Material table entry (Sec. 2.6 and the paper's property tables). */
+typedef struct {
+    double rho0;    /* reference density, kg/m^3 */
+    double mu;      /* dynamic viscosity, Pa s (fluids) */
+    double k;       /* thermal conductivity, W/(m K); 0 = adiabatic */
+    double cp;      /* specific heat, J/(kg K) */
+    double T_init;  /* default initial temperature, K */
+    int fixed_T;    /* solids only: 1 = temperature held (heat source/sink) */
+} sph_material;
+
+/* Create a single-case context.  cfg: host, copied.  cuda_stream: a
+ * cudaStream_t or NULL.  *out receives the context.
+ * Errors: SPH_EINVAL (non-positive dx/h/extent, periodic axis with < 3 cells),
+ * SPH_ECUDA. */
+sph_status sph_create(const sph_config* cfg, void* cuda_stream, sph_ctx** out);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+sph_status sph_destroy(sph_ctx* ctx);
+
+/* Set material `material_id` (0..15).  Must precede the particles that use it
+ * and the first step.  Errors: SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_set_material(sph_ctx* ctx, int material_id, const sph_material* mat);
+
+/* Append n fluid particles of material `material_id`.
+ * pos: host double[n*3] (x,y,z per particle).  vel: host double[n*3] or NULL
+ * (rest).  T: host double[n] or NULL (material T_init).  rho: host double[n]
+ * or NULL (material rho0).  *first_id (may be NULL) receives the first id.
+ * Errors: SPH_EINVAL, SPH_ESTATE (after the first step). */
+sph_status sph_add_fluid(sph_ctx* ctx, int material_id, int64_t n, const double* pos,
+                         const double* vel, const double* T, const double* rho, int64_t* first_id);
+
+/* Append n solid (dummy wall) particles, Sec. 2.5.  body_id: -1 for a static
+ * wall, 0..3 for a rigid body whose motion is set by sph_set_rotation.
+ * pos: host double[n*3] reference positions (at time 0).  normal: host
+ * double[n*3] unit wall normals pointing into the fluid.  T: host double[n] or
+ * NULL.  Errors: SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_add_solid(sph_ctx* ctx, int body_id, int material_id, int64_t n, const double* pos,
+                         const double* normal, const double* T, int64_t* first_id);
+
+/* Prescribed rigid rotation of body `body_id` (0..3): angle omega*t about the
+ * unit axis through center.  Errors: SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_set_rotation(sph_ctx* ctx, int body_id, const double center[3], const double axis[3],
+                            double omega);
+
+/* Advance n advection steps (each with its acoustic sub-steps, Sec. 2.8).
+ * *sim_time_out (may be NULL) receives the simulated time.  The first call
+ * uploads the particles and builds the step's CUDA graph.
+ * Errors: SPH_EUNSTABLE (state no longer finite or a fluid particle left the
+ * box; the context stays readable), SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_step(sph_ctx* ctx, int n_advection_steps, double* sim_time_out);
+
+/* Churning torque and heat-up.  torque_axis: torque of the fluid on body
+ * `body_id` about its axis at the last acoustic sub-step (pressure + viscous
+ * wall forces of Eq. 18, applied at the wall particles), N m.
+ * torque_time_avg: its sub-step-weighted mean since the first step.
+ * heat_into_fluid: sum over fluid of m cp (T - T_initial), J.
+ * mean_fluid_T: mass-weighted mean fluid temperature, K.  Any output pointer
+ * may be NULL.  All four are FP64 reductions in a fixed order.
+ * Errors: SPH_EINVAL (body id), SPH_ESTATE (no step taken yet). */
+sph_status sph_read_torque_heat(sph_ctx* ctx, int body_id, double* torque_axis,
+                                double* torque_time_avg, double* heat_into_fluid,
+                                double* mean_fluid_T);
+
+/* Field ids for sph_read_fields (values as double, original id order). */
+enum {
+    SPH_FIELD_POS = 0,      /* n*3 */
+    SPH_FIELD_VEL = 1,      /* n*3; wall velocity for solids */
+    SPH_FIELD_RHO = 2,      /* n; rho0 for solids */
+    SPH_FIELD_P = 3,        /* n; 0 for solids */
+    SPH_FIELD_T = 4,        /* n */
+    SPH_FIELD_DRHO = 5,     /* n; last continuity rate */
+    SPH_FIELD_AVISC = 6,    /* n*3; viscous acceleration of the last advection step */
+    SPH_FIELD_DTDT = 7,     /* n; conduction rate of the last advection step */
+    SPH_FIELD_NORMAL = 9    /* n*3; current wall normal (solids) */
+};
+
+/* Copy field `field` of all n particles (n must equal the particle count)
+ * into host_dst (double, n or n*3 values).  Errors: SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_read_fields(sph_ctx* ctx, int field, void* host_dst, int64_t n);
+
+/* Neighbour pairs of the current advection step's frozen snapshot (pair
+ * membership 0 < |r_i - r_j|^2 < (2h)^2 decided exactly as in FP64).
+ * counts: host int64[n] (per id).  ids: host int32[cap] or NULL; receives,
+ * for each id in order, its neighbour ids in ascending order.  *total gets the
+ * number of entries.  Errors: SPH_EINVAL (cap too small), SPH_ESTATE. */
+sph_status sph_read_neighbors(sph_ctx* ctx, int64_t* counts, int32_t* ids, int64_t cap,
+                              int64_t* total);
+
+/* Cell order of the last neighbour search: perm[k] = id at sorted position k
+ * (sorted by cell index, x fastest, then id).  host int64[n]. */
+sph_status sph_read_cell_order(sph_ctx* ctx, int64_t* perm, int64_t n);
+
+typedef struct {
+    int64_t n_fluid, n_solid;
+    double t;                 /* simulated time */
+    int64_t adv_steps, substeps;
+    double last_dt_ad;
+    int last_nsub;
+    int kcap;                 /* sub-step cap per advection step */
+    int ncell[3];
+    double cell_width[3];
+    int error_bits;           /* 1 NaN/Inf, 2 fluid left the box */
+    int graph_launches;       /* kernels launched per advection step */
+} sph_info;
+
+sph_status sph_get_info(sph_ctx* ctx, sph_info* info);
+
+/* Directed neighbour pairs of fluid particles in the current snapshot, by
+ * partner kind (fluid, wall).  Used to turn kernel times into pair rates.
+ * Errors: SPH_ESTATE (no step yet), SPH_ECUDA. */
+sph_status sph_pair_stats(sph_ctx* ctx, int64_t* fluid_fluid, int64_t* fluid_wall);
+
+/* Device-time profile of the advection step, by kernel group. */
+enum {
+    SPH_PROF_SORT = 0,     /* step set-up + cell hash, count, scan, scatter, id order, reorder */
+    SPH_PROF_PASS_D = 1,   /* density re-initialisation */
+    SPH_PROF_PASS_VT = 2,  /* viscous acceleration + heat conduction */
+    SPH_PROF_PASS_M = 3,   /* Riemann pressure force + kick/drift (one per active sub-step) */
+    SPH_PROF_PASS_C = 4,   /* Riemann continuity (one per active sub-step) */
+    SPH_PROF_CONTROL = 5,  /* sub-step size + torque reduction */
+    SPH_PROF_ADV_END = 6,  /* temperature update + heat reductions */
+    SPH_PROF_IDLE = 7,     /* kernels of sub-step slots past the end of the advection step */
+    SPH_PROF_NCLASS = 8
+};
+
+/* enable != 0: re-capture the step graph with CUDA event records between
+ * kernel groups; sph_step then synchronises after every advection step and
+ * adds each group's device time (cudaEventElapsedTime) to a per-group total.
+ * enable == 0: plain graph again.  Counters are reset either way. */
+sph_status sph_profile(sph_ctx* ctx, int enable);
+
+/* ms: host double[SPH_PROF_NCLASS] accumulated device milliseconds;
+ * launches: host int64[SPH_PROF_NCLASS] intervals counted.  reset != 0
+ * clears the counters after reading. */
+sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* Message of the last failed call on ctx ("" if none).  Never NULL. */
+const char* sph_last_error(const sph_ctx* ctx);
+
+/* Stateless cell sort (the neighbour-search core of Sec. 2.8's per-advection
+ * step update).  pos: device double[n*3].  Particle k goes to the cell
+ * floor((pos - origin)/cellw) (clamped to the grid); particles are ordered by
+ * (linear cell index with x fastest, k).  perm: device int32[n] receives the
+ * particle index at each sorted position; cell_start: device int32[ncells+1]
+ * receives each cell's first sorted position (last entry n).  Scratch of
+ * about 12 n + 4 ncells bytes is allocated and freed on `stream` with
+ * cudaMallocAsync.  Errors: SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], const double cellw[3],
+                         const int ncell[3], int32_t* perm, int32_t* cell_start, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

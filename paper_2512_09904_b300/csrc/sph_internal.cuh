@@ -1,0 +1,223 @@
+// sph_internal.cuh -- device-side data layout and helpers of the SPH library.
+//
+// Layout in HBM (one engine = one packed particle array over all resident
+// cases; a case's particles are contiguous after every cell sort):
+//   X[3]   double, work positions (fluid drift target), slot order
+//   Y[3]   double, frozen snapshot positions of the advection step, slot order
+//   V[2]   float4 (vx, vy, vz, drho_rel = rho - rho0), ping-pong across passes;
+//          for solids (wall velocity, 0)
+//   DR[2]  float, continuity rate carried between sub-steps
+//   T64[2] double temperature; T32 float (T - T_ref) for pair arithmetic
+//   SNAP   float4 (offset of the snapshot position from its cell corner, tag)
+//   CELLK  uint32 global cell index of each slot
+//   AV     float4 (viscous acceleration held for the sub-steps, dT/dt)
+//   NRM    float4 wall normal (solids)
+//   per-id arrays (indexed by particle id, never reordered): reference
+//   positions/normals of solids, per-solid torque contributions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int MAX_MAT = 16;
+constexpr int MAX_BODY = 4;
+constexpr uint32_t KIND_FLUID = 0u, KIND_STATIC = 1u, KIND_ROT = 2u;
+constexpr int ERR_NAN = 1, ERR_ESCAPE = 2, ERR_NB_OVERFLOW = 4;
+
+// Per-particle neighbour lists, rebuilt once per advection step (the pair
+// set is frozen for the step).  Entry = j | code << 26 (code: cell offset,
+// see for_each_neighbor).  Fluid partners fill slots 0, 1, ... and wall
+// partners slots NB_CAP-1, NB_CAP-2, ...; slot k of particle i lives at
+// NB[k * stride + i] so a warp's loads of one slot are coalesced.
+// NBC[i] = nf | nw << 8 | NB_HAS; NB_OVF marks a particle whose partners did
+// not fit (its passes fall back to the 27-cell loop).
+constexpr int NB_CAP = 128;
+constexpr uint32_t NB_HAS = 1u << 30, NB_OVF = 1u << 31;
+constexpr uint32_t NB_JMASK = (1u << 26) - 1u;
+constexpr int MAX_PARTICLES = 1 << 26;
+
+// particle tag: material (4 bits) | kind (2) | body (2) | case (24)
+__host__ __device__ __forceinline__ uint32_t make_tag(uint32_t mat, uint32_t kind, uint32_t body,
+                                                      uint32_t cs) {
+    return mat | (kind << 4) | (body << 6) | (cs << 8);
+}
+__host__ __device__ __forceinline__ uint32_t tag_mat(uint32_t t) { return t & 15u; }
+__host__ __device__ __forceinline__ uint32_t tag_kind(uint32_t t) { return (t >> 4) & 3u; }
+__host__ __device__ __forceinline__ uint32_t tag_body(uint32_t t) { return (t >> 6) & 3u; }
+__host__ __device__ __forceinline__ uint32_t tag_case(uint32_t t) { return t >> 8; }
+
+struct MatDev {
+    float rho0, mass, mu, k, cp, inv_rho0_cp;
+    int fixed_T, pad;
+};
+
+struct BodyDev {
+    double c[3], axis[3], omega;
+    int id_lo, id_hi;   // id range holding the body's particles
+    int set, pad;
+};
+
+struct CaseDev {
+    double origin[3], ext[3], cellw[3];
+    float cellwf[3];
+    int ncell[3];
+    int cell_base, ncells;
+    int periodic;
+    double R2;                    // (2h)^2 in FP64: the membership rule
+    float R2lo, R2hi, R2eps;      // FP32 guard band around the rule
+    float h, inv_h, w0, kw, kdw;  // W(0), alpha, -5 alpha / h
+    float inv_sigma0, vol;
+    float c0, c02, inv_c0, inv_c02;
+    float g[3];
+    double h64, c0_64, u_ref, cfl_ad, cfl_ac, nu_max;
+    double T_ref;
+    int free_surface, kcap, n_body, pad;
+    MatDev mat[MAX_MAT];
+    BodyDev body[MAX_BODY];
+};
+
+struct CaseState {
+    double t, dt_ad, tau, dt;
+    float dtf, hdtf;
+    int active, last, nsub, reach;
+    unsigned vmax_bits;
+    int err;       // error bits that fail sph_step (NaN, particle escaped)
+    int err_info;  // informational bits (neighbour list overflow)
+    long long adv_steps, substeps;
+    double cs[MAX_BODY], sn[MAX_BODY];
+    double tq_p[MAX_BODY], tq_v[MAX_BODY], tq_inst[MAX_BODY], tq_int[MAX_BODY];
+    double time_int;
+    double sum_mcpT, sum_mT, sum_m, heat0;
+    double heat, mean_T;
+    int seg_lo, seg_hi;
+    int chunk_lo, nchunks;
+    int last_nsub, pad;
+    double last_dt_ad;
+};
+
+// ---------------------------------------------------------------- kernel ---
+// Wendland C2 (3-D, support 2h): W = alpha (1 - q/2)^4 (1 + 2q),
+// dW/dr = -(5 alpha / h) q (1 - q/2)^3, q = r/h.
+__device__ __forceinline__ float kernel_W(const CaseDev& C, float r) {
+    float q = r * C.inv_h;
+    float t = 1.0f - 0.5f * q;
+    float t2 = t * t;
+    return C.kw * t2 * t2 * (1.0f + 2.0f * q);
+}
+__device__ __forceinline__ float kernel_dW(const CaseDev& C, float r) {
+    float q = r * C.inv_h;
+    float t = 1.0f - 0.5f * q;
+    return C.kdw * q * t * t * t;
+}
+
+__device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, float by, float bz) {
+    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
+
+// Exact pair-membership rule on the FP64 snapshot: 0 < r^2 < R2 with
+// r^2 = ((dx*dx + dy*dy) + dz*dz) in round-to-nearest, no contraction, and
+// the minimum image on periodic axes.
+static __device__ __noinline__ bool member_fp64(const CaseDev& C, const double* __restrict__ Yx,
+                                         const double* __restrict__ Yy,
+                                         const double* __restrict__ Yz, int i, int j) {
+    double d[3] = {__dsub_rn(Yx[i], Yx[j]), __dsub_rn(Yy[i], Yy[j]), __dsub_rn(Yz[i], Yz[j])};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (C.periodic & (1 << a)) {
+            double L = C.ext[a];
+            if (d[a] > 0.5 * L) d[a] = __dsub_rn(d[a], L);
+            else if (d[a] < -0.5 * L) d[a] = __dadd_rn(d[a], L);
+        }
+    }
+    double r2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+    r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
+    return r2 > 0.0 && r2 < C.R2;
+}
+
+// Visit every neighbour j of slot i (27-cell stencil, cells of width >= 2h).
+// Pair geometry comes from the FP32 cell-corner offsets of the frozen
+// snapshot: r_ij = off_i - off_j - dc * w.  Membership is decided in FP32
+// away from the cut-off and re-decided from the FP64 snapshot inside a
+// relative guard band, so the pair set equals the FP64 rule exactly.
+// f(j, sj, rx, ry, rz, r2, code) receives r_ij = r_i - r_j and the cell
+// offset packed as code = (dx+1) | (dy+1) << 2 | (dz+1) << 4.
+template <class F>
+__device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32_t* __restrict__ cstart,
+                                                  const float4* __restrict__ snap,
+                                                  const double* __restrict__ Yx,
+                                                  const double* __restrict__ Yy,
+                                                  const double* __restrict__ Yz, int i, float4 si,
+                                                  uint32_t key_i, F&& f) {
+    const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
+    int cl = (int)key_i - C.cell_base;
+    const int cx = cl % nx;
+    const int cy = (cl / nx) % ny;
+    const int cz = cl / (nx * ny);
+    const bool px = C.periodic & 1, py = C.periodic & 2, pz = C.periodic & 4;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= nz) {
+            if (!pz) continue;
+            z = (z + nz) % nz;
+        }
+        const float oz = si.z - (float)dz * C.cellwf[2];
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= ny) {
+                if (!py) continue;
+                y = (y + ny) % ny;
+            }
+            const float oy = si.y - (float)dy * C.cellwf[1];
+            const int row = C.cell_base + (z * ny + y) * nx;
+#pragma unroll 1
+            for (int dxc = -1; dxc <= 1; ++dxc) {
+                int x = cx + dxc;
+                if (x < 0 || x >= nx) {
+                    if (!px) continue;
+                    x = (x + nx) % nx;
+                }
+                const float ox = si.x - (float)dxc * C.cellwf[0];
+                const int a = (int)__ldg(cstart + row + x), b = (int)__ldg(cstart + row + x + 1);
+                for (int j = a; j < b; ++j) {
+                    if (j == i) continue;
+                    const float4 sj = __ldg(snap + j);
+                    const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
+                    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    bool in;
+                    if (r2 >= C.R2hi) in = false;
+                    else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
+                    else in = member_fp64(C, Yx, Yy, Yz, i, j);
+                    if (in) f(j, sj, rx, ry, rz, r2, (dxc + 1) | ((dy + 1) << 2) | ((dz + 1) << 4));
+                }
+            }
+        }
+    }
+}
+
+// Position of a solid particle at the current advection step: static walls
+// sit at their reference position; rigid bodies are rotated by the step's
+// angle about (c, axis) (Rodrigues' formula, FP64).
+__device__ __forceinline__ void solid_position(const CaseDev& C, const CaseState& S, uint32_t tag,
+                                               const double* __restrict__ RPx,
+                                               const double* __restrict__ RPy,
+                                               const double* __restrict__ RPz, int id, double p[3]) {
+    p[0] = RPx[id];
+    p[1] = RPy[id];
+    p[2] = RPz[id];
+    if (tag_kind(tag) == KIND_ROT) {
+        const int b = tag_body(tag);
+        const BodyDev& B = C.body[b];
+        const double cs = S.cs[b], sn = S.sn[b];
+        double d[3] = {p[0] - B.c[0], p[1] - B.c[1], p[2] - B.c[2]};
+        double axd[3] = {B.axis[1] * d[2] - B.axis[2] * d[1], B.axis[2] * d[0] - B.axis[0] * d[2],
+                         B.axis[0] * d[1] - B.axis[1] * d[0]};
+        double ad = B.axis[0] * d[0] + B.axis[1] * d[1] + B.axis[2] * d[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[k] = B.c[k] + (cs * d[k] + sn * axd[k] + (1.0 - cs) * ad * B.axis[k]);
+    }
+}
+
+}  // namespace sph

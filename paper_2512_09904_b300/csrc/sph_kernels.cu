@@ -1,0 +1,1072 @@
+// sph_kernels.cu -- CUDA kernels of the coupled SPH step (sm_103a).
+//
+// Per advection step (Sec. 2.8): adv_begin -> cell sort (hash, count, scan,
+// scatter, id-order, reorder) -> pass D (Eq. 14/15) -> pass VT (viscous
+// part of Eq. 10 and Eq. 18; conduction Eq. 22) -> acoustic sub-steps
+// [sub_begin -> pass M (Eqs. 10-12, 16-19) -> pass C (Eqs. 10-13, 16-17) ->
+// sub_end] x cap -> T update and fixed-order FP64 reductions.
+//
+// Pair arithmetic is FP32 on the frozen snapshot geometry; positions,
+// temperatures, time and all reductions are FP64.  No kernel waits on
+// another block, so no kernel can hang.
+#include <cstdio>
+
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+static int g_grid_cap = 148 * 8;
+void set_grid_cap(int sms) { g_grid_cap = sms * 8; }
+
+static inline int grid_stride_grid(int n, int block) {
+    int g = (n + block - 1) / block;
+    if (g > g_grid_cap) g = g_grid_cap;
+    return g < 1 ? 1 : g;
+}
+static inline int grid_1to1(int n, int block) {
+    int g = (n + block - 1) / block;
+    return g < 1 ? 1 : g;
+}
+
+#define GSTRIDE_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// --------------------------------------------------------------- control ---
+__global__ void k_vmax_init(Bufs B, int par) {
+    GSTRIDE_LOOP(i, B.n) {
+        uint32_t tag = B.TAG[par][i];
+        if (tag_kind(tag) != KIND_FLUID) continue;
+        float4 v = B.V[par][i];
+        float m = sqrtf(dot3f(v.x, v.y, v.z, v.x, v.y, v.z));
+        atomicMax(&B.st[tag_case(tag)].vmax_bits, __float_as_uint(m));
+    }
+}
+
+// Eq. (25) first line: dt_ad = cfl_ad min(h / max(|v|max, u_ref), h^2 / nu).
+__global__ void k_adv_begin(Bufs B) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.ncases) return;
+    const CaseDev& C = B.cases[c];
+    CaseState& S = B.st[c];
+    double vmax = (double)__uint_as_float(S.vmax_bits);
+    double U = vmax > C.u_ref ? vmax : C.u_ref;
+    double a = C.h64 / U;
+    if (C.nu_max > 0.0) {
+        double b = C.h64 * C.h64 / C.nu_max;
+        if (b < a) a = b;
+    }
+    S.dt_ad = C.cfl_ad * a;
+    S.tau = 0.0;
+    S.nsub = 0;
+    S.active = 1;
+    S.last = 0;
+    for (int b = 0; b < MAX_BODY; ++b) {
+        double th = C.body[b].omega * S.t;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        S.cs[b] = cs;
+        S.sn[b] = sn;
+    }
+}
+
+// Eq. (25) second line, clipped to land exactly on dt_ad.
+__global__ void k_sub_begin(Bufs B) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.ncases) return;
+    const CaseDev& C = B.cases[c];
+    CaseState& S = B.st[c];
+    if (!S.active) {
+        S.dt = 0.0;
+        S.dtf = 0.0f;
+        S.hdtf = 0.0f;
+        return;
+    }
+    double vmax = (double)__uint_as_float(S.vmax_bits);
+    double dt_ac = C.cfl_ac * C.h64 / (C.c0_64 + vmax);
+    double rem = S.dt_ad - S.tau;
+    int reach = rem <= dt_ac;
+    double dt = reach ? rem : dt_ac;
+    S.reach = reach;
+    S.last = reach || (S.nsub + 1 >= C.kcap);
+    S.dt = dt;
+    S.dtf = (float)dt;
+    S.hdtf = (float)(0.5 * dt);
+    S.vmax_bits = 0u;
+}
+
+// fixed-order block reduction of doubles (blockDim = 256)
+__device__ double block_sum_256(double v, double* sh) {
+    int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Torque of the fluid on each rigid body: sum of per-particle contributions
+// over the body's id range (id order: independent of the sort and of other
+// resident cases), then sub-step time bookkeeping.
+__global__ void __launch_bounds__(256) k_sub_end(Bufs B) {
+    const int c = blockIdx.x;
+    const CaseDev& C = B.cases[c];
+    CaseState& S = B.st[c];
+    __shared__ double sh[256];
+    const int active = S.active;
+    const int first = S.nsub == 0;
+    __syncthreads();  // every thread has read the state before thread 0 updates it
+    if (!active) return;
+    for (int b = 0; b < C.n_body; ++b) {
+        const BodyDev& Bd = C.body[b];
+        if (!Bd.set) continue;
+        double acc = 0.0, accv = 0.0;
+        for (int id = Bd.id_lo + threadIdx.x; id < Bd.id_hi; id += 256) {
+            acc += (double)B.TORQ[id];
+            if (first) accv += (double)B.TORQV[id];
+        }
+        double tq = block_sum_256(acc, sh);
+        double tqv = first ? block_sum_256(accv, sh) : 0.0;
+        if (threadIdx.x == 0) {
+            S.tq_p[b] = tq;
+            if (first) S.tq_v[b] = tqv;
+            S.tq_inst[b] = S.tq_p[b] + S.tq_v[b];
+            S.tq_int[b] += S.dt * S.tq_inst[b];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S.time_int += S.dt;
+        S.tau = S.reach ? S.dt_ad : S.tau + S.dt;
+        S.nsub += 1;
+        S.substeps += 1;
+        if (S.last) S.active = 0;
+    }
+}
+
+// ------------------------------------------------------------ cell sort ---
+__device__ __forceinline__ uint32_t cell_key(const CaseDev& C, const double p[3], bool* out) {
+    int cc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = floor((p[a] - C.origin[a]) / C.cellw[a]);
+        double top = (double)(C.ncell[a] - 1);
+        if (!(f >= 0.0)) {
+            f = 0.0;
+            *out = true;
+        } else if (f > top) {
+            f = top;
+            *out = true;
+        }
+        cc[a] = (int)f;
+    }
+    return (uint32_t)(C.cell_base + (cc[2] * C.ncell[1] + cc[1]) * C.ncell[0] + cc[0]);
+}
+
+__global__ void k_hash(Bufs B, int par) {
+    GSTRIDE_LOOP(s, B.n) {
+        const uint32_t tag = B.TAG[par][s];
+        const int c = tag_case(tag);
+        const CaseDev& C = B.cases[c];
+        double p[3];
+        const bool fluid = tag_kind(tag) == KIND_FLUID;
+        if (fluid) {
+            p[0] = B.X[0][s];
+            p[1] = B.X[1][s];
+            p[2] = B.X[2][s];
+            bool moved = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (C.periodic & (1 << a)) {
+                    double L = C.ext[a], o = C.origin[a];
+                    if (p[a] >= o + L) { p[a] -= L; moved = true; }
+                    else if (p[a] < o) { p[a] += L; moved = true; }
+                }
+            if (moved) {
+                B.X[0][s] = p[0];
+                B.X[1][s] = p[1];
+                B.X[2][s] = p[2];
+            }
+        } else {
+            solid_position(C, B.st[c], tag, B.RP[0], B.RP[1], B.RP[2], B.ID[par][s], p);
+        }
+        bool out = false;
+        uint32_t key = cell_key(C, p, &out);
+        if (out && fluid) atomicOr(&B.st[c].err, ERR_ESCAPE);
+        B.KEYS[s] = key;
+        B.RANK[s] = atomicAdd(&B.CNT[key], 1u);
+    }
+}
+
+// exclusive scan of cnt[0..ncells) into cstart, tiles of SCAN_TILE cells
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ cnt, uint32_t* cstart,
+                                                     uint32_t* blk, int ncells) {
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x;
+    const int base = blockIdx.x * SCAN_TILE + 2 * t;
+    uint32_t a = base < ncells ? cnt[base] : 0u;
+    uint32_t b = base + 1 < ncells ? cnt[base + 1] : 0u;
+    uint32_t v = a + b;
+    const int lane = t & 31, w = t >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    uint32_t excl = x - v + (w > 0 ? wsum[w - 1] : 0u);
+    if (base < ncells) cstart[base] = excl;
+    if (base + 1 < ncells) cstart[base + 1] = excl + a;
+    if (t == 1023) blk[blockIdx.x] = wsum[31];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* blk, int nblk, uint32_t* cstart, int ncells) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) carry = 0u;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += 1024) {
+        uint32_t v = base + t < nblk ? blk[base + t] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        uint32_t excl = x - v + (w > 0 ? wsum[w - 1] : 0u) + carry;
+        if (base + t < nblk) blk[base + t] = excl;
+        __syncthreads();
+        if (t == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (t == 0) cstart[ncells] = carry;
+}
+
+__global__ void k_scan_add(uint32_t* cstart, const uint32_t* __restrict__ blk, uint32_t* cnt, int ncells) {
+    GSTRIDE_LOOP(i, ncells) {
+        cstart[i] += blk[i / SCAN_TILE];
+        cnt[i] = 0u;
+    }
+}
+
+__global__ void k_scatter(int n, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
+                          const uint32_t* __restrict__ cstart, uint32_t* tmp) {
+    GSTRIDE_LOOP(s, n) tmp[cstart[keys[s]] + rank[s]] = (uint32_t)s;
+}
+
+// Within a cell, order by particle id: rank = #{cell members with smaller id}.
+__global__ void k_order(int n, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cstart,
+                        const uint32_t* __restrict__ tmp, const int* __restrict__ ids, uint32_t* perm) {
+    GSTRIDE_LOOP(s, n) {
+        const uint32_t key = keys[s];
+        const uint32_t a = cstart[key], b = cstart[key + 1];
+        const int my = ids ? ids[s] : s;
+        uint32_t r = 0;
+        for (uint32_t t = a; t < b; ++t) {
+            const uint32_t o = tmp[t];
+            const int id = ids ? ids[o] : (int)o;
+            r += id < my;
+        }
+        perm[a + r] = (uint32_t)s;
+    }
+}
+
+// Gather every per-particle field into cell order; build the frozen snapshot.
+__global__ void k_reorder(Bufs B, int par) {
+    const int in = par, out = 1 - par;
+    GSTRIDE_LOOP(d, B.n) {
+        const int s = (int)B.PERM[d];
+        const uint32_t tag = B.TAG[in][s];
+        const int id = B.ID[in][s];
+        const int c = tag_case(tag);
+        const CaseDev& C = B.cases[c];
+        const uint32_t key = B.KEYS[s];
+        const bool fluid = tag_kind(tag) == KIND_FLUID;
+        double p[3];
+        if (fluid) {
+            p[0] = B.X[0][s];
+            p[1] = B.X[1][s];
+            p[2] = B.X[2][s];
+        } else {
+            solid_position(C, B.st[c], tag, B.RP[0], B.RP[1], B.RP[2], id, p);
+        }
+        B.Y[0][d] = p[0];
+        B.Y[1][d] = p[1];
+        B.Y[2][d] = p[2];
+        int cl = (int)key - C.cell_base;
+        int cc[3] = {cl % C.ncell[0], (cl / C.ncell[0]) % C.ncell[1], cl / (C.ncell[0] * C.ncell[1])};
+        float off[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) off[a] = (float)((p[a] - C.origin[a]) - (double)cc[a] * C.cellw[a]);
+        B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
+        B.CELLK[d] = key;
+        if (fluid) {
+            B.V[out][d] = B.V[in][s];
+            B.DR[out][d] = B.DR[in][s];
+        } else {
+            float4 n0 = B.RN[id];
+            float vw[3] = {0.f, 0.f, 0.f};
+            float nn[3] = {n0.x, n0.y, n0.z};
+            if (tag_kind(tag) == KIND_ROT) {
+                const int b = tag_body(tag);
+                const BodyDev& Bd = C.body[b];
+                const float cs = (float)B.st[c].cs[b], sn = (float)B.st[c].sn[b];
+                const float ax = (float)Bd.axis[0], ay = (float)Bd.axis[1], az = (float)Bd.axis[2];
+                float an = ax * n0.x + ay * n0.y + az * n0.z;
+                float axn[3] = {ay * n0.z - az * n0.y, az * n0.x - ax * n0.z, ax * n0.y - ay * n0.x};
+                float A[3] = {ax, ay, az};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) nn[k] = cs * nn[k] + sn * axn[k] + (1.0f - cs) * an * A[k];
+                // v_w = omega axis x (r_w - c)
+                float d0 = (float)(p[0] - Bd.c[0]), d1 = (float)(p[1] - Bd.c[1]), d2 = (float)(p[2] - Bd.c[2]);
+                float w = (float)Bd.omega;
+                vw[0] = w * (ay * d2 - az * d1);
+                vw[1] = w * (az * d0 - ax * d2);
+                vw[2] = w * (ax * d1 - ay * d0);
+            }
+            B.V[out][d] = make_float4(vw[0], vw[1], vw[2], 0.0f);
+            B.DR[out][d] = 0.0f;
+            B.NRM[d] = make_float4(nn[0], nn[1], nn[2], 0.0f);
+        }
+        const double T = B.T64[in][s];
+        B.T64[out][d] = T;
+        B.T32[d] = (float)(T - C.T_ref);
+        B.ID[out][d] = id;
+        B.TAG[out][d] = tag;
+    }
+}
+
+// Case segments and the fixed reduction-chunk table (one thread).
+__global__ void k_segments(Bufs B) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int q = 0;
+    for (int c = 0; c < B.ncases; ++c) {
+        const CaseDev& C = B.cases[c];
+        CaseState& S = B.st[c];
+        S.seg_lo = (int)B.CSTART[C.cell_base];
+        S.seg_hi = (int)B.CSTART[C.cell_base + C.ncells];
+        int nch = (S.seg_hi - S.seg_lo + RED_CHUNK - 1) / RED_CHUNK;
+        S.chunk_lo = q;
+        S.nchunks = nch;
+        for (int k = 0; k < nch && q < B.max_chunks; ++k) B.CHUNK_CASE[q++] = c;
+    }
+    for (; q < B.max_chunks; ++q) B.CHUNK_CASE[q] = -1;
+}
+
+// --------------------------------------------------------- pair passes ----
+#define PAIR_ARGS C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2]
+
+// Walk `cnt` list slots starting at slot k0 with step ks (+1 fluid part,
+// -1 wall part); geometry from the snapshot offsets and the packed cell code.
+template <class F>
+__device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i, float4 si, int k0, int ks,
+                                          int cnt, F&& f) {
+    const size_t stride = (size_t)B.nb_stride;
+    const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
+    const float sx = si.x + C.cellwf[0], sy = si.y + C.cellwf[1], sz = si.z + C.cellwf[2];
+    for (int q = 0; q < cnt; ++q) {
+        const uint32_t e = __ldg(nb);
+        nb += ks * (ptrdiff_t)stride;
+        const int j = (int)(e & NB_JMASK);
+        const uint32_t d = e >> 26;
+        const float4 sj = __ldg(B.SNAP + j);
+        // r_ij = off_i - off_j - dc w with dc = field - 1
+        const float rx = fmaf(-(float)(d & 3u), C.cellwf[0], sx) - sj.x;
+        const float ry = fmaf(-(float)((d >> 2) & 3u), C.cellwf[1], sy) - sj.y;
+        const float rz = fmaf(-(float)(d >> 4), C.cellwf[2], sz) - sj.z;
+        const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        f(j, sj, rx, ry, rz, r2);
+    }
+}
+
+constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
+
+// Visit the frozen neighbours of slot i whose kind matches PART, from the
+// particle's list, or through the 27-cell loop when its list overflowed.
+template <int PART, class F>
+__device__ __forceinline__ void visit(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
+    const uint32_t cnt = B.NBC[i];
+    if ((cnt & NB_HAS) && !(cnt & NB_OVF)) {
+        if (PART & PART_FLUID) list_walk(C, B, i, si, 0, 1, (int)(cnt & 255u), f);
+        if (PART & PART_WALL) list_walk(C, B, i, si, NB_CAP - 1, -1, (int)((cnt >> 8) & 255u), f);
+    } else {
+        for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i],
+                          [&](int j, float4 sj, float rx, float ry, float rz, float r2, int) {
+                              const bool fj = tag_kind(__float_as_uint(sj.w)) == KIND_FLUID;
+                              if ((fj && (PART & PART_FLUID)) || (!fj && (PART & PART_WALL)))
+                                  f(j, sj, rx, ry, rz, r2);
+                          });
+    }
+}
+
+// Pass D: the advection step's neighbour search (27-cell loop, exact FP64
+// membership) writes every particle's partner list, and fluid particles get
+// their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
+// runs over all partners (fluid and wall) plus the particle itself.  Static
+// walls of fixed temperature have no pair sums of their own and get no list.
+__global__ void __launch_bounds__(128) k_passD(Bufs B, int par) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    const uint32_t kind = tag_kind(tag);
+    const CaseDev& C = B.cases[tag_case(tag)];
+    const MatDev& Mi = C.mat[tag_mat(tag)];
+    if (kind == KIND_STATIC && Mi.fixed_T) {
+        B.NBC[i] = 0u;
+        return;
+    }
+    const size_t stride = (size_t)B.nb_stride;
+    uint32_t* nb = B.NB + i;
+    float sum = C.w0;
+    uint32_t nf = 0, nw = 0;
+    for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i], [&](int j, float4 sj, float, float, float, float r2, int code) {
+        sum += kernel_W(C, sqrtf(r2));
+        const uint32_t e = (uint32_t)j | ((uint32_t)code << 26);
+        const bool room = nf + nw < (uint32_t)NB_CAP;
+        if (tag_kind(__float_as_uint(sj.w)) == KIND_FLUID) {
+            if (room) nb[(size_t)nf * stride] = e;
+            ++nf;
+        } else {
+            if (room) nb[(size_t)(NB_CAP - 1 - nw) * stride] = e;
+            ++nw;
+        }
+    });
+    if (nf + nw > (uint32_t)NB_CAP) {
+        B.NBC[i] = NB_HAS | NB_OVF;
+        atomicOr(&B.st[tag_case(tag)].err_info, ERR_NB_OVERFLOW);
+    } else {
+        B.NBC[i] = NB_HAS | nf | (nw << 8);
+    }
+    if (kind != KIND_FLUID) return;
+    float4* V = B.V[1 - par];
+    const float rr = Mi.rho0 * fmaf(sum, C.inv_sigma0, -1.0f);
+    const float d = V[i].w;
+    V[i].w = C.free_surface ? fmaxf(d, rr) : rr;
+}
+
+__device__ __forceinline__ float axial_torque(const BodyDev& Bd, const double* __restrict__ Yx,
+                                              const double* __restrict__ Yy, const double* __restrict__ Yz,
+                                              int i, float fx, float fy, float fz) {
+    float dx = (float)(Yx[i] - Bd.c[0]), dy = (float)(Yy[i] - Bd.c[1]), dz = (float)(Yz[i] - Bd.c[2]);
+    float tx = dy * fz - dz * fy, ty = dz * fx - dx * fz, tz = dx * fy - dy * fx;
+    return tx * (float)Bd.axis[0] + ty * (float)Bd.axis[1] + tz * (float)Bd.axis[2];
+}
+
+__device__ __forceinline__ float harmonic2(float a, float b) {
+    const float s = a + b;
+    return s > 0.f ? __fdividef(2.f * a * b, s) : 0.f;
+}
+
+// Pass VT: viscous acceleration (Eq. 10 second term; wall term of Eq. 18),
+// held for the sub-steps, and dT/dt by the Cleary form (Eq. 22).  Rigid-body
+// particles also record the viscous torque of the fluid on them.
+__global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    const uint32_t kind = tag_kind(tag);
+    const CaseDev& C = B.cases[tag_case(tag)];
+    const MatDev& Mi = C.mat[tag_mat(tag)];
+    const float4* __restrict__ V = B.V[1 - par];
+    const float* __restrict__ T32 = B.T32;
+    const float Ti = T32[i];
+    if (kind == KIND_FLUID) {
+        const float4 vi = V[i];
+        const float rho_i = Mi.rho0 + vi.w;
+        float ax = 0.f, ay = 0.f, az = 0.f, dT = 0.f;
+        visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+            const float inv_r = rsqrtf(r2);
+            const float dW = kernel_dW(C, r2 * inv_r);
+            const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+            const float4 vj = __ldg(V + j);
+            const float Vj = __fdividef(Mj.mass, Mj.rho0 + vj.w);
+            const float cv = 2.f * Vj * harmonic2(Mi.mu, Mj.mu) * inv_r * dW;
+            ax = fmaf(cv, vi.x - vj.x, ax);
+            ay = fmaf(cv, vi.y - vj.y, ay);
+            az = fmaf(cv, vi.z - vj.z, az);
+            const float K = 2.f * harmonic2(Mi.k, Mj.k);
+            dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+        });
+        visit<PART_WALL>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+            const float inv_r = rsqrtf(r2);
+            const float dW = kernel_dW(C, r2 * inv_r);
+            const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+            const float4 vw = __ldg(V + j);
+            const float cv = 2.f * C.vol * Mi.mu * inv_r * dW;  // the wall takes the fluid's viscosity
+            ax = fmaf(cv, vi.x - vw.x, ax);
+            ay = fmaf(cv, vi.y - vw.y, ay);
+            az = fmaf(cv, vi.z - vw.z, az);
+            const float K = 2.f * harmonic2(Mi.k, Mj.k);
+            dT = fmaf(C.vol * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+        });
+        const float inv_rho = 1.0f / rho_i;
+        B.AV[i] = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, dT * inv_rho / Mi.cp);
+        return;
+    }
+    const bool thermal = !Mi.fixed_T;
+    const bool rot = kind == KIND_ROT;
+    if (!thermal && !rot) {
+        B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float4 vw = V[i];
+    float dT = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    visit<PART_ALL>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+        const float inv_r = rsqrtf(r2);
+        const float dW = kernel_dW(C, r2 * inv_r);
+        const uint32_t tj = __float_as_uint(sj.w);
+        const MatDev& Mj = C.mat[tag_mat(tj)];
+        const bool fj = tag_kind(tj) == KIND_FLUID;
+        float Vj = C.vol;
+        float rho_j = 1.f;
+        float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fj) {
+            vj = __ldg(V + j);
+            rho_j = Mj.rho0 + vj.w;
+            Vj = __fdividef(Mj.mass, rho_j);
+        }
+        if (thermal) {
+            const float K = 2.f * harmonic2(Mi.k, Mj.k);
+            dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+        }
+        if (rot && fj) {
+            // force of fluid j on this wall particle: -m_j a_jw, with
+            // a_jw = 2 V_w / rho_j mu_j (v_j - v_w) / r dW/dr
+            const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * Mj.mu * inv_r * dW;
+            fx = fmaf(cf, vj.x - vw.x, fx);
+            fy = fmaf(cf, vj.y - vw.y, fy);
+            fz = fmaf(cf, vj.z - vw.z, fz);
+        }
+    });
+    B.AV[i] = make_float4(0.f, 0.f, 0.f, thermal ? dT * Mi.inv_rho0_cp : 0.f);
+    if (rot) {
+        const BodyDev& Bd = C.body[tag_body(tag)];
+        B.TORQV[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
+    }
+}
+
+// Pass M: half kick of density + EoS on the fly, Riemann pressure force,
+// velocity kick, both half drifts of the position (FP64).
+__device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, int i, int* case_out,
+                                           unsigned* vbits_out) {
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    const uint32_t kind = tag_kind(tag);
+    const int c = tag_case(tag);
+    const CaseState& S = B.st[c];
+    if (!S.active) return;
+    const CaseDev& C = B.cases[c];
+    const float4* __restrict__ Vin = B.V[1 - par];
+    float4* Vout = B.V[par];
+    const float* __restrict__ DR = B.DR[1 - par];
+    const float hdt = S.hdtf, dt = S.dtf;
+    const MatDev& Mi = C.mat[tag_mat(tag)];
+    const float4 vi = Vin[i];
+    if (kind == KIND_FLUID) {
+        const float dh_i = fmaf(hdt, DR[i], vi.w);
+        const float rho_i = Mi.rho0 + dh_i;
+        const float p_i = C.c02 * dh_i;
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+            const float inv_r = rsqrtf(r2);
+            const float dW = kernel_dW(C, r2 * inv_r);
+            const float ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+            const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+            const float4 vj = __ldg(Vin + j);
+            const float dh_j = fmaf(hdt, __ldg(DR + j), vj.w);
+            const float rho_j = Mj.rho0 + dh_j;
+            const float p_j = C.c02 * dh_j;
+            const float rs = rho_i + rho_j;
+            const float dU = -dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, ex, ey, ez);  // U_L - U_R
+            const float beta = fminf(3.f * fmaxf(dU, 0.f), C.c0);
+            const float pstar = fmaf(0.5f, p_i + p_j, __fdividef(rho_i * rho_j * beta * dU, rs));
+            const float coef = __fdividef(Mj.mass, rho_j) * pstar * dW;
+            ax = fmaf(coef, ex, ax);
+            ay = fmaf(coef, ey, ay);
+            az = fmaf(coef, ez, az);
+        });
+        visit<PART_WALL>(C, B, i, si, [&](int, float4, float rx, float ry, float rz, float r2) {
+            const float inv_r = rsqrtf(r2);
+            const float dW = kernel_dW(C, r2 * inv_r);
+            // one-sided wall problem: P_R = p_f + rho_f g.r_fw, r_fw = -r_ij
+            const float g_rfw = -dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
+            const float PR = fmaf(rho_i, g_rfw, p_i);
+            const float rhoR = fmaf(PR, C.inv_c02, Mi.rho0);
+            const float pstar = __fdividef(fmaf(rho_i, PR, rhoR * p_i), rho_i + rhoR);
+            const float coef = C.vol * pstar * dW * inv_r;
+            ax = fmaf(coef, rx, ax);
+            ay = fmaf(coef, ry, ay);
+            az = fmaf(coef, rz, az);
+        });
+        const float k = -2.f / rho_i;
+        const float4 av = B.AV[i];
+        const float nvx = vi.x + dt * (k * ax + av.x + C.g[0]);
+        const float nvy = vi.y + dt * (k * ay + av.y + C.g[1]);
+        const float nvz = vi.z + dt * (k * az + av.z + C.g[2]);
+        Vout[i] = make_float4(nvx, nvy, nvz, dh_i);
+        const double hd = (double)S.hdtf;
+        const double* Xs[3] = {first ? B.Y[0] : B.X[0], first ? B.Y[1] : B.X[1], first ? B.Y[2] : B.X[2]};
+        const float vo[3] = {vi.x, vi.y, vi.z}, vn[3] = {nvx, nvy, nvz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double x = Xs[a][i];
+            x = x + hd * (double)vo[a];
+            x = x + hd * (double)vn[a];
+            B.X[a][i] = x;
+        }
+        const float sp = sqrtf(dot3f(nvx, nvy, nvz, nvx, nvy, nvz));
+        if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[c].err, ERR_NAN);
+        *case_out = c;
+        *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
+        return;
+    }
+    Vout[i] = vi;
+    if (kind != KIND_ROT) return;
+    // rigid-body particle: pressure force of its fluid neighbours on it
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+        const float inv_r = rsqrtf(r2);
+        const float dW = kernel_dW(C, r2 * inv_r);
+        const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+        const float4 vj = __ldg(Vin + j);
+        const float dh_j = fmaf(hdt, __ldg(DR + j), vj.w);
+        const float rho_j = Mj.rho0 + dh_j;
+        const float p_j = C.c02 * dh_j;
+        // for fluid j: r_fw = r_w - r_j = r_ij (this thread is the wall)
+        const float g_rfw = dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
+        const float PR = fmaf(rho_j, g_rfw, p_j);
+        const float rhoR = fmaf(PR, C.inv_c02, Mj.rho0);
+        const float pstar = __fdividef(fmaf(rho_j, PR, rhoR * p_j), rho_j + rhoR);
+        // a_jw = -2 V_w / rho_j p* dW e_jw with e_jw = -r_ij / r; force on wall = -m_j a_jw
+        const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * pstar * dW * inv_r;
+        fx = fmaf(cf, rx, fx);
+        fy = fmaf(cf, ry, fy);
+        fz = fmaf(cf, rz, fz);
+    });
+    const BodyDev& Bd = C.body[tag_body(tag)];
+    B.TORQ[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
+}
+
+__global__ void __launch_bounds__(128) k_passM(Bufs B, int par, int first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = -1;
+    unsigned vb = 0u;
+    if (i < B.n) passM_body(B, par, first, i, &c, &vb);
+    // per-case max speed for the next step sizes: warp-aggregated atomics
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const unsigned m = __reduce_max_sync(peers, vb);
+    if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&B.st[c].vmax_bits, m);
+}
+
+// Pass C: Riemann continuity (Eq. 10 first line with v* of Eq. 13) and the
+// wall problem of Eqs. (16)-(17); second half kick of density.
+__global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    const int c = tag_case(tag);
+    const CaseState& S = B.st[c];
+    if (!S.active) return;
+    const CaseDev& C = B.cases[c];
+    const float4* __restrict__ Vin = B.V[par];
+    float4* Vout = B.V[1 - par];
+    const float4 vi = Vin[i];
+    if (tag_kind(tag) != KIND_FLUID) {
+        Vout[i] = vi;
+        return;
+    }
+    const MatDev& Mi = C.mat[tag_mat(tag)];
+    const float rho_i = Mi.rho0 + vi.w;
+    float d = 0.f;
+    visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+        const float inv_r = rsqrtf(r2);
+        const float dW = kernel_dW(C, r2 * inv_r);
+        const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+        const float4 vj = __ldg(Vin + j);
+        const float rho_j = Mj.rho0 + vj.w;
+        // U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)), with
+        // U_R - U_L = (v_i - v_j).e and p_i - p_j = c0^2 (drho_i - drho_j)
+        const float du = fmaf(0.5f * inv_r, dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz),
+                              __fdividef(C.c0 * (vi.w - vj.w), rho_i + rho_j));
+        d = fmaf(__fdividef(Mj.mass, rho_j) * du, dW, d);
+    });
+    visit<PART_WALL>(C, B, i, si, [&](int j, float4, float rx, float ry, float rz, float r2) {
+        const float inv_r = rsqrtf(r2);
+        const float dW = kernel_dW(C, r2 * inv_r);
+        const float4 nw = __ldg(B.NRM + j);
+        const float4 vw = __ldg(Vin + j);
+        const float g_rfw = -dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
+        const float PR = fmaf(rho_i, g_rfw, C.c02 * vi.w);
+        const float rhoR = fmaf(PR, C.inv_c02, Mi.rho0);
+        // U*_w - U_L = n.(v_f - v_w) + (p_f - P_R) / (c0 (rho_f + rho_R))
+        const float du = dot3f(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z) -
+                         __fdividef(rho_i * g_rfw * C.inv_c0, rho_i + rhoR);
+        d = fmaf(C.vol * du * dot3f(nw.x, nw.y, nw.z, rx, ry, rz) * inv_r, dW, d);
+    });
+    const float drho = 2.f * rho_i * d;
+    Vout[i] = make_float4(vi.x, vi.y, vi.z, fmaf(S.hdtf, drho, vi.w));
+    B.DR[1 - par][i] = drho;
+}
+
+// -------------------------------------------------- end of advection step ---
+__global__ void k_T_update(Bufs B, int par) {
+    const int cur = 1 - par;
+    GSTRIDE_LOOP(i, B.n) {
+        const uint32_t tag = B.TAG[cur][i];
+        const float r = B.AV[i].w;
+        if (r != 0.0f) B.T64[cur][i] += B.st[tag_case(tag)].tau * (double)r;
+    }
+}
+
+// fixed-order partial sums per chunk of a case segment (blockDim 256)
+__global__ void __launch_bounds__(256) k_reduce_chunks(Bufs B, int cur) {
+    __shared__ double sh[256];
+    for (int q = blockIdx.x; q < B.max_chunks; q += gridDim.x) {
+        const int c = B.CHUNK_CASE[q];
+        if (c < 0) break;
+        const CaseState& S = B.st[c];
+        const CaseDev& C = B.cases[c];
+        const int lo = S.seg_lo + (q - S.chunk_lo) * RED_CHUNK;
+        const int hi = min(lo + RED_CHUNK, S.seg_hi);
+        double a = 0.0, b = 0.0, m = 0.0;
+        for (int i = lo + threadIdx.x; i < hi; i += 256) {
+            const uint32_t tag = B.TAG[cur][i];
+            if (tag_kind(tag) != KIND_FLUID) continue;
+            const MatDev& M = C.mat[tag_mat(tag)];
+            const double T = B.T64[cur][i];
+            const double mm = (double)M.mass;
+            a += mm * (double)M.cp * T;
+            b += mm * T;
+            m += mm;
+        }
+        a = block_sum_256(a, sh);
+        b = block_sum_256(b, sh);
+        m = block_sum_256(m, sh);
+        if (threadIdx.x == 0) {
+            B.PART[3 * q + 0] = a;
+            B.PART[3 * q + 1] = b;
+            B.PART[3 * q + 2] = m;
+        }
+    }
+}
+
+__global__ void k_reduce_cases(Bufs B, int init) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.ncases) return;
+    CaseState& S = B.st[c];
+    double a = 0.0, b = 0.0, m = 0.0;
+    for (int k = 0; k < S.nchunks; ++k) {
+        const int q = S.chunk_lo + k;
+        a += B.PART[3 * q + 0];
+        b += B.PART[3 * q + 1];
+        m += B.PART[3 * q + 2];
+    }
+    if (init) {
+        S.heat0 = a;
+        S.heat = 0.0;
+    } else {
+        S.heat = a - S.heat0;
+    }
+    S.sum_mcpT = a;
+    S.sum_mT = b;
+    S.sum_m = m;
+    S.mean_T = m > 0.0 ? b / m : 0.0;
+}
+
+__global__ void k_adv_end_cases(Bufs B) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.ncases) return;
+    CaseState& S = B.st[c];
+    S.t += S.tau;
+    S.adv_steps += 1;
+    S.last_nsub = S.nsub;
+    S.last_dt_ad = S.dt_ad;
+    if (B.HIST && B.hist_cap > 0) {
+        double* h = B.HIST + ((size_t)c * B.hist_cap + (size_t)((S.adv_steps - 1) % B.hist_cap)) * 8;
+        h[0] = S.t;
+        h[1] = S.tq_inst[0];
+        h[2] = S.time_int > 0.0 ? S.tq_int[0] / S.time_int : 0.0;
+        h[3] = S.heat;
+        h[4] = S.mean_T;
+        h[5] = S.dt_ad;
+        h[6] = (double)S.nsub;
+        h[7] = (double)__uint_as_float(S.vmax_bits);
+    }
+}
+
+// ------------------------------------------------------------- readback ---
+__global__ void k_gather_field(Bufs B, int par, int field, double* out) {
+    const int cur = 1 - par;
+    GSTRIDE_LOOP(i, B.n) {
+        const uint32_t tag = B.TAG[cur][i];
+        const int id = B.ID[cur][i];
+        const CaseDev& C = B.cases[tag_case(tag)];
+        const bool fluid = tag_kind(tag) == KIND_FLUID;
+        const float4 v = B.V[cur][i];
+        const MatDev& M = C.mat[tag_mat(tag)];
+        switch (field) {
+        case 0:
+            out[3 * (size_t)id + 0] = fluid ? B.X[0][i] : B.Y[0][i];
+            out[3 * (size_t)id + 1] = fluid ? B.X[1][i] : B.Y[1][i];
+            out[3 * (size_t)id + 2] = fluid ? B.X[2][i] : B.Y[2][i];
+            break;
+        case 1:
+            out[3 * (size_t)id + 0] = v.x;
+            out[3 * (size_t)id + 1] = v.y;
+            out[3 * (size_t)id + 2] = v.z;
+            break;
+        case 2: out[id] = fluid ? (double)M.rho0 + (double)v.w : (double)M.rho0; break;
+        case 3: out[id] = fluid ? (double)C.c02 * (double)v.w : 0.0; break;
+        case 4: out[id] = B.T64[cur][i]; break;
+        case 5: out[id] = fluid ? (double)B.DR[cur][i] : 0.0; break;
+        case 6: {
+            const float4 a = B.AV[i];
+            out[3 * (size_t)id + 0] = fluid ? a.x : 0.0;
+            out[3 * (size_t)id + 1] = fluid ? a.y : 0.0;
+            out[3 * (size_t)id + 2] = fluid ? a.z : 0.0;
+            break;
+        }
+        case 7: out[id] = B.AV[i].w; break;
+        case 9: {
+            const float4 nn = B.NRM[i];
+            out[3 * (size_t)id + 0] = fluid ? 0.0 : nn.x;
+            out[3 * (size_t)id + 1] = fluid ? 0.0 : nn.y;
+            out[3 * (size_t)id + 2] = fluid ? 0.0 : nn.z;
+            break;
+        }
+        default: break;
+        }
+    }
+}
+
+// neighbour read-back: from the particle's list when it has one (what the
+// passes use), else from the 27-cell loop (walls without pair sums)
+template <class F>
+__device__ __forceinline__ void visit_any(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
+    if (B.NBC[i] & NB_HAS) visit<PART_ALL>(C, B, i, si, [&](int j, float4, float, float, float, float) { f(j); });
+    else for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i], [&](int j, float4, float, float, float, float, int) { f(j); });
+}
+
+__global__ void __launch_bounds__(128) k_nb_count(Bufs B, int par, int64_t* counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
+    int64_t k = 0;
+    visit_any(C, B, i, si, [&](int) { ++k; });
+    counts[B.ID[1 - par][i]] = k;
+}
+
+__global__ void __launch_bounds__(128) k_nb_list(Bufs B, int par, const int64_t* start, int32_t* list) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
+    const int* ID = B.ID[1 - par];
+    int64_t k = start[ID[i]];
+    visit_any(C, B, i, si, [&](int j) { list[k++] = ID[j]; });
+}
+
+// directed neighbour pairs of fluid particles by partner kind: [fluid, wall]
+__global__ void __launch_bounds__(128) k_pair_stats(Bufs B, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long ff = 0, fw = 0;
+    if (i < B.n) {
+        const float4 si = B.SNAP[i];
+        const uint32_t tag = __float_as_uint(si.w);
+        if (tag_kind(tag) == KIND_FLUID) {
+            const CaseDev& C = B.cases[tag_case(tag)];
+            visit<PART_FLUID>(C, B, i, si, [&](int, float4, float, float, float, float) { ++ff; });
+            visit<PART_WALL>(C, B, i, si, [&](int, float4, float, float, float, float) { ++fw; });
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ff += __shfl_down_sync(0xffffffffu, ff, o);
+        fw += __shfl_down_sync(0xffffffffu, fw, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, ff);
+        atomicAdd(out + 1, fw);
+    }
+}
+
+cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s) {
+    k_pair_stats<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- stateless sort ----
+__global__ void k_cs_hash(const double* __restrict__ pos, int n, double ox, double oy, double oz,
+                          double wx, double wy, double wz, int nx, int ny, int nz, uint32_t* keys,
+                          uint32_t* rank, uint32_t* cnt) {
+    GSTRIDE_LOOP(s, n) {
+        const double o[3] = {ox, oy, oz}, w[3] = {wx, wy, wz};
+        const int nc[3] = {nx, ny, nz};
+        int cc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double f = floor((pos[3 * (size_t)s + a] - o[a]) / w[a]);
+            if (!(f >= 0.0)) f = 0.0;
+            else if (f > (double)(nc[a] - 1)) f = (double)(nc[a] - 1);
+            cc[a] = (int)f;
+        }
+        const uint32_t key = (uint32_t)((cc[2] * ny + cc[1]) * nx + cc[0]);
+        keys[s] = key;
+        rank[s] = atomicAdd(&cnt[key], 1u);
+    }
+}
+
+// ------------------------------------------------------------ launchers ---
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e__ = (x);                  \
+        if (e__ != cudaSuccess) return e__;     \
+    } while (0)
+
+size_t scan_blocks(int ncells) { return (size_t)((ncells + SCAN_TILE - 1) / SCAN_TILE); }
+
+static cudaError_t launch_scan(uint32_t* cnt, uint32_t* cstart, uint32_t* blk, int ncells, cudaStream_t s) {
+    const int nb = (int)scan_blocks(ncells);
+    k_scan_tiles<<<nb, 1024, 0, s>>>(cnt, cstart, blk, ncells);
+    k_scan_top<<<1, 1024, 0, s>>>(blk, nb, cstart, ncells);
+    k_scan_add<<<grid_stride_grid(ncells, 256), 256, 0, s>>>(cstart, blk, cnt, ncells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vmax_init(const Bufs& B, int par, cudaStream_t s) {
+    k_vmax_init<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s) {
+    k_adv_begin<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s) {
+    const int g = grid_stride_grid(B.n, 256);
+    k_hash<<<g, 256, 0, s>>>(B, par);
+    CK(launch_scan(B.CNT, B.CSTART, B.SCANBLK, B.ncells, s));
+    k_scatter<<<g, 256, 0, s>>>(B.n, B.KEYS, B.RANK, B.CSTART, B.TMP);
+    k_order<<<g, 256, 0, s>>>(B.n, B.KEYS, B.CSTART, B.TMP, B.ID[par], B.PERM);
+    k_reorder<<<g, 256, 0, s>>>(B, par);
+    k_segments<<<1, 32, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
+    k_passD<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
+    k_passVT<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s) {
+    k_sub_begin<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
+    k_passM<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
+    k_passC<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s) {
+    k_sub_end<<<B.ncases, 256, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s) {
+    int g = B.max_chunks < g_grid_cap ? B.max_chunks : g_grid_cap;
+    k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, 1 - par);
+    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_heat0(const Bufs& B, cudaStream_t s) {
+    // called right after an initial sort with parity 0 (current buffers = 1)
+    int g = B.max_chunks < g_grid_cap ? B.max_chunks : g_grid_cap;
+    k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, 1);
+    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s) {
+    k_T_update<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
+    CK(launch_reduce_heat(B, par, s));
+    k_adv_end_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+int kernels_per_advection_step(int kcap) {
+    // adv_begin + sort(hash, 3 scan, scatter, order, reorder, segments)
+    // + D + VT + kcap * (sub_begin, M, C, sub_end) + T_update + 2 reduce + adv_end
+    return 1 + 8 + 2 + 4 * kcap + 4;
+}
+
+cudaError_t launch_gather_field(const Bufs& B, int par, int field, double* out, cudaStream_t s) {
+    k_gather_field<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par, field, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbors(const Bufs& B, int par, int64_t* counts, const int64_t* start, int32_t* list,
+                             cudaStream_t s) {
+    if (!list) k_nb_count<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, counts);
+    else k_nb_list<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, start, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_sort(const double* pos, int n, const double origin[3], const double cellw[3],
+                             const int ncell[3], uint32_t* keys, uint32_t* rank, uint32_t* cnt, uint32_t* tmp,
+                             uint32_t* scanblk, int32_t* perm, int32_t* cell_start, cudaStream_t s) {
+    const int ncells = ncell[0] * ncell[1] * ncell[2];
+    CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ncells, s));
+    const int g = grid_stride_grid(n, 256);
+    k_cs_hash<<<g, 256, 0, s>>>(pos, n, origin[0], origin[1], origin[2], cellw[0], cellw[1], cellw[2], ncell[0],
+                                ncell[1], ncell[2], keys, rank, cnt);
+    uint32_t* cs = reinterpret_cast<uint32_t*>(cell_start);
+    CK(launch_scan(cnt, cs, scanblk, ncells, s));
+    k_scatter<<<g, 256, 0, s>>>(n, keys, rank, cs, tmp);
+    k_order<<<g, 256, 0, s>>>(n, keys, cs, tmp, nullptr, reinterpret_cast<uint32_t*>(perm));
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,69 @@
+// sph_kernels.cuh -- buffer table and launchers shared by the engine and the kernels.
+#pragma once
+#include "sph_internal.cuh"
+
+namespace sph {
+
+constexpr int RED_CHUNK = 4096;  // slots per fixed-order reduction chunk
+constexpr int SCAN_TILE = 2048;  // cells per scan tile
+
+// All device buffers of one engine (pointers only; passed by value).
+struct Bufs {
+    int n;             // particle slots in use
+    int ncases;
+    int ncells;        // total cells over all cases
+    int max_chunks;
+    int hist_cap;
+    CaseDev* cases;
+    CaseState* st;
+    double *X[3], *Y[3];
+    float4* V[2];
+    float* DR[2];
+    double* T64[2];
+    int* ID[2];
+    uint32_t* TAG[2];
+    float* T32;
+    float4* SNAP;
+    uint32_t* CELLK;
+    float4* AV;
+    float4* NRM;
+    double* RP[3];
+    float4* RN;
+    float* TORQ;
+    float* TORQV;
+    uint32_t *KEYS, *RANK, *TMP, *PERM, *CNT, *CSTART, *SCANBLK;
+    double* PART;
+    int* CHUNK_CASE;
+    double* HIST;
+    uint32_t* NB;   // neighbour lists, NB_CAP slots of nb_stride entries
+    uint32_t* NBC;  // per-slot list counts
+    int nb_stride;
+};
+
+// launchers (stream-ordered; all return the launch error)
+cudaError_t launch_vmax_init(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s);
+cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s);  // hash..reorder + segments
+cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s);
+cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s);
+cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s);
+cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_init_heat0(const Bufs& B, cudaStream_t s);
+cudaError_t launch_gather_field(const Bufs& B, int par, int field, double* out, cudaStream_t s);
+cudaError_t launch_neighbors(const Bufs& B, int par, int64_t* counts_by_id, const int64_t* start_by_id,
+                             int32_t* list, cudaStream_t s);
+int kernels_per_advection_step(int kcap);
+cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
+
+// stateless cell sort (positions AoS)
+cudaError_t launch_cell_sort(const double* pos, int n, const double origin[3], const double cellw[3],
+                             const int ncell[3], uint32_t* keys, uint32_t* rank, uint32_t* cnt,
+                             uint32_t* tmp, uint32_t* scanblk, int32_t* perm, int32_t* cell_start,
+                             cudaStream_t s);
+size_t scan_blocks(int ncells);
+
+}  // namespace sph

@@ -1,0 +1,102 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must build for sm_103a, load, and export every function that
+include/*.h declares; argument validation that happens before any CUDA call
+is exercised here.
+"""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_09904_b300 import build as B
+from paper_2512_09904_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sphlib():
+    B.build()
+    from paper_2512_09904_b300 import sph
+    return sph
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sph_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(sphlib):
+    names = declared_functions()
+    assert "sph_create" in names and "sph_step" in names and "sph_read_torque_heat" in names
+    L = C.CDLL(sphlib.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm103a(sphlib):
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+    assert os.path.getsize(sphlib.LIB_PATH) > 0
+
+
+def test_create_validates_config(sphlib):
+    cfg = W.still_tank(nx=4, ny=4, nz=4, wall_h=6).config
+    ctx = sphlib.Context(cfg, stream=0)
+    info = ctx.sph_get_info()
+    R = 2 * cfg["h_over_dx"] * cfg["dx"]
+    for a in range(3):
+        assert info["ncell"][a] == int(np.floor(cfg["extent"][a] / R))
+        assert info["cell_width"][a] >= R
+    # default sub-step cap: ceil(cfl_ad / cfl_ac (c0 / u_ref + 1)) + 2
+    assert info["kcap"] == int(np.ceil(0.25 / 0.6 * (cfg["c0"] / cfg["u_ref"] + 1))) + 2
+    ctx.close()
+    bad = dict(cfg, dx=-1.0)
+    with pytest.raises(sphlib.SphError) as e:
+        sphlib.Context(bad, stream=0)
+    assert e.value.status == sphlib.SPH_EINVAL
+    # a periodic axis needs at least 3 cells
+    bad = dict(cfg, periodic_mask=1, extent=[2.5 * R, cfg["extent"][1], cfg["extent"][2]])
+    with pytest.raises(sphlib.SphError):
+        sphlib.Context(bad, stream=0)
+
+
+def test_add_validates_arguments(sphlib):
+    case = W.still_tank(nx=4, ny=4, nz=4, wall_h=6)
+    ctx = sphlib.Context(case.config, stream=0)
+    with pytest.raises(sphlib.SphError) as e:
+        ctx.sph_add_fluid(0, case.fluids[0]["pos"])  # material 0 not set yet
+    assert e.value.status == sphlib.SPH_EINVAL
+    for mid, m in case.materials.items():
+        ctx.sph_set_material(mid, m)
+    with pytest.raises(sphlib.SphError):
+        ctx.sph_set_material(16, case.materials[0])
+    first = ctx.sph_add_fluid(0, case.fluids[0]["pos"], rho=case.fluids[0]["rho"])
+    assert first == 0
+    s = case.solids[0]
+    assert ctx.sph_add_solid(-1, s["mat"], s["pos"], s["normal"]) == case.n_fluid
+    with pytest.raises(sphlib.SphError):
+        ctx.sph_add_solid(7, 1, s["pos"], s["normal"])  # body id out of range
+    with pytest.raises(sphlib.SphError):
+        ctx.sph_set_rotation(0, [0, 0, 0], [0, 0, 2.0], 1.0)  # axis not unit
+    bad = case.fluids[0]["pos"].copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(sphlib.SphError):
+        ctx.sph_add_fluid(0, bad)
+    ctx.close()
+
+
+def test_reads_before_first_step_are_state_errors(sphlib):
+    case = W.periodic_box(n=8)
+    ctx = sphlib.Context(case.config, stream=0)
+    with pytest.raises(sphlib.SphError) as e:
+        ctx.sph_read_torque_heat(0)
+    assert e.value.status == sphlib.SPH_ESTATE
+    ctx.close()
