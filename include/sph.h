@@ -196,7 +196,9 @@ sph_status sph_profile(sph_ctx* ctx, int enable);
  * clears the counters after reading. */
 sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* launches, int reset);
 
-/* Message of the last failed call on ctx ("" if none).  Never NULL. */
+/* Message of the last failed call on ctx ("" if none).  With ctx == NULL:
+ * the last failed context-free call (sph_cell_sort*) of this host thread.
+ * Never NULL. */
 const char* sph_last_error(const sph_ctx* ctx);
 
 /* Stateless cell sort (the neighbour-search core of Sec. 2.8's per-advection
@@ -209,6 +211,33 @@ const char* sph_last_error(const sph_ctx* ctx);
  * cudaMallocAsync.  Errors: SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA. */
 sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], const double cellw[3],
                          const int ncell[3], int32_t* perm, int32_t* cell_start, void* stream);
+
+/* Allocation-free variant of sph_cell_sort, for callers that cannot let a
+ * library allocate device memory: a process whose free HBM is already held by
+ * its own caching allocator, a latency-critical loop that cannot take the
+ * device synchronisation of cudaMalloc/cudaFree, or a host whose memory
+ * manager forbids outside allocations.  (The paper has no counterpart; this
+ * is a deployment variant of the neighbour-search sort.)
+ *
+ * Same arguments, layout and result as sph_cell_sort.  Scratch lives in one
+ * fixed device array of about 12 SPH_NOALLOC_MAX_N + 4 SPH_NOALLOC_MAX_CELLS
+ * bytes (16 MiB), which every GPU that loads this library holds until the
+ * process exits.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *  - n > SPH_NOALLOC_MAX_N or more than SPH_NOALLOC_MAX_CELLS cells:
+ *    SPH_EINVAL, with the reason in sph_last_error(NULL).
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    outside any stream capture.  A failed lookup returns SPH_ECUDA.
+ *  - All calls share the one array (it keeps the last call's contents; the
+ *    per-cell counters are cleared by each call).  Calls whose work overlaps
+ *    on the GPU (different streams, or different host threads) race on it:
+ *    serialise them on one stream.
+ * Errors: SPH_EINVAL, SPH_ECUDA. */
+#define SPH_NOALLOC_MAX_N (1 << 20)
+#define SPH_NOALLOC_MAX_CELLS (1 << 20)
+sph_status sph_cell_sort_noalloc(const double* pos, int64_t n, const double origin[3], const double cellw[3],
+                                 const int ncell[3], int32_t* perm, int32_t* cell_start, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,10 @@
 
 namespace sph {
 void set_grid_cap(int sms);
+
+// message of the last failed call that has no context (sph_last_error(NULL))
+static thread_local std::string g_stateless_err;
+void set_stateless_error(const char* msg) { g_stateless_err = msg; }
 }
 
 using namespace sph;
@@ -105,7 +109,7 @@ static cudaError_t dalloc(sph_ctx* c, T** p, size_t count) {
 
 extern "C" {
 
-const char* sph_last_error(const sph_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char* sph_last_error(const sph_ctx* ctx) { return ctx ? ctx->err.c_str() : sph::g_stateless_err.c_str(); }
 
 sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     if (!cfg || !out) return SPH_EINVAL;

@@ -78,11 +78,12 @@ def lib():
         L.sph_cell_sort.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile.argtypes = [vp, C.c_int]
         L.sph_pair_stats.argtypes = [vp, PI64, PI64]
+        L.sph_cell_sort_noalloc.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile_read.argtypes = [vp, PD, PI64, C.c_int]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
-                     "sph_profile", "sph_profile_read", "sph_pair_stats"):
+                     "sph_profile", "sph_profile_read", "sph_pair_stats", "sph_cell_sort_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -267,3 +268,21 @@ def sph_cell_sort(pos_dev_ptr: int, n: int, origin, cellw, ncell, perm_dev_ptr: 
                              C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream))
     if rc != SPH_OK:
         raise SphError(rc, "sph_cell_sort")
+
+
+NOALLOC_MAX_N = 1 << 20
+NOALLOC_MAX_CELLS = 1 << 20
+
+
+def sph_cell_sort_noalloc(pos_dev_ptr: int, n: int, origin, cellw, ncell, perm_dev_ptr: int,
+                          cell_start_dev_ptr: int, stream: int = 0):
+    """Allocation-free cell sort: same contract as sph_cell_sort, scratch in
+    the library's fixed device array (n <= NOALLOC_MAX_N, cells <=
+    NOALLOC_MAX_CELLS)."""
+    o, w = _f64(origin, (3,)), _f64(cellw, (3,))
+    nc = (C.c_int * 3)(*[int(v) for v in ncell])
+    L = lib()
+    rc = L.sph_cell_sort_noalloc(C.c_void_p(pos_dev_ptr), int(n), _pd(o), _pd(w), nc, C.c_void_p(perm_dev_ptr),
+                                 C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream))
+    if rc != SPH_OK:
+        raise SphError(rc, "sph_cell_sort_noalloc: " + L.sph_last_error(None).decode())
