@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--omega", type=float, default=600.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--list-batch", type=int, default=0, help="override the list-batch kernel variant")
     return ap.parse_args()
 
 
@@ -178,6 +179,8 @@ def main():
     case = workload(args.dx, args.omega)
     stream = torch.cuda.current_stream()
     ctx = sph.from_case(case, stream=stream.cuda_stream)
+    if args.list_batch:
+        ctx.sph_set_tuning("list_batch", args.list_batch)
     ctx.sph_step(1)                     # upload + first advection step
     ctx.sph_profile(True)               # event records between kernel groups
     ctx.sph_step(max(args.warmup, 3) - 1)

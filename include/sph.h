@@ -172,6 +172,17 @@ sph_status sph_get_info(sph_ctx* ctx, sph_info* info);
  * Errors: SPH_ESTATE (no step yet), SPH_ECUDA. */
 sph_status sph_pair_stats(sph_ctx* ctx, int64_t* fluid_fluid, int64_t* fluid_wall);
 
+/* Kernel-variant knobs (performance only: results do not depend on them). */
+enum {
+    SPH_TUNE_LIST_BATCH = 0  /* neighbour-list entries each thread loads together in the
+                                pair passes: 1, 2, 4 or 8 (default) */
+};
+
+/* Select a kernel variant; re-captures the step graph if the context has
+ * started.  Errors: SPH_EINVAL (unknown key or value), SPH_ECUDA. */
+sph_status sph_set_tuning(sph_ctx* ctx, int key, int value);
+sph_status sph_get_tuning(sph_ctx* ctx, int key, int* value);
+
 /* Device-time profile of the advection step, by kernel group. */
 enum {
     SPH_PROF_SORT = 0,     /* step set-up + cell hash, count, scan, scatter, id order, reorder */

@@ -146,6 +146,7 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
                   ? cfg->max_substeps
                   : (int)std::ceil(cfg->cfl_ad / cfg->cfl_ac * (cfg->c0 / cfg->u_ref + 1.0)) + 2;
     c->sigma0 = lattice_sigma0(cfg->dx, h);
+    c->B.tune_batch = 8;
     *out = c;
     return SPH_OK;
 }
@@ -437,7 +438,20 @@ static sph_status upload(sph_ctx* c) {
     AL(c->d_field, (size_t)3 * n);
     AL(B.NB, (size_t)NB_CAP * n);
     AL(B.NBC, n);
+    AL(B.OVFL, n);
+    AL(B.novf, 1);
+    AL(B.VH, n);
     B.nb_stride = (int)n;
+    {
+        int fm = -1;
+        bool uni = true;
+        for (size_t i = 0; i < c->kind.size(); ++i)
+            if (c->kind[i] == 0) {
+                if (fm < 0) fm = c->mat[i];
+                else if (c->mat[i] != fm) uni = false;
+            }
+        B.uni_fluid = uni ? 1 : 0;
+    }
 #undef AL
     if (e != cudaSuccess) return fail(c, e == cudaErrorMemoryAllocation ? SPH_ENOMEM : SPH_ECUDA,
                                       "device allocation: %s", cudaGetErrorString(e));
@@ -656,6 +670,29 @@ sph_status sph_pair_stats(sph_ctx* c, int64_t* fluid_fluid, int64_t* fluid_wall)
     *fluid_fluid = (int64_t)h[0];
     *fluid_wall = (int64_t)h[1];
     return SPH_OK;
+}
+
+sph_status sph_set_tuning(sph_ctx* c, int key, int value) {
+    if (!c) return SPH_EINVAL;
+    switch (key) {
+    case SPH_TUNE_LIST_BATCH:
+        if (value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(c, SPH_EINVAL, "list batch must be 1, 2, 4 or 8");
+        c->B.tune_batch = value;
+        break;
+    default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
+    }
+    if (!c->started) return SPH_OK;
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return capture(c);
+}
+
+sph_status sph_get_tuning(sph_ctx* c, int key, int* value) {
+    if (!c || !value) return SPH_EINVAL;
+    switch (key) {
+    case SPH_TUNE_LIST_BATCH: *value = c->B.tune_batch; return SPH_OK;
+    default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
+    }
 }
 
 sph_status sph_profile(sph_ctx* c, int enable) {

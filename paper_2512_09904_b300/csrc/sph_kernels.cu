@@ -378,45 +378,70 @@ __global__ void k_segments(Bufs B) {
         for (int k = 0; k < nch && q < B.max_chunks; ++k) B.CHUNK_CASE[q++] = c;
     }
     for (; q < B.max_chunks; ++q) B.CHUNK_CASE[q] = -1;
+    *B.novf = 0;  // overflow list of this advection step's neighbour search
 }
 
 // --------------------------------------------------------- pair passes ----
 #define PAIR_ARGS C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2]
 
+constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
+
 // Walk `cnt` list slots starting at slot k0 with step ks (+1 fluid part,
 // -1 wall part); geometry from the snapshot offsets and the packed cell code.
-template <class F>
+// The list entries of a batch are loaded together so that BATCH independent
+// loads of the (DRAM-resident) list stream are in flight per thread.
+template <int BATCH, class F>
 __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i, float4 si, int k0, int ks,
                                           int cnt, F&& f) {
     const size_t stride = (size_t)B.nb_stride;
     const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
+    const ptrdiff_t step = ks * (ptrdiff_t)stride;
     const float sx = si.x + C.cellwf[0], sy = si.y + C.cellwf[1], sz = si.z + C.cellwf[2];
-    for (int q = 0; q < cnt; ++q) {
-        const uint32_t e = __ldg(nb);
-        nb += ks * (ptrdiff_t)stride;
-        const int j = (int)(e & NB_JMASK);
-        const uint32_t d = e >> 26;
-        const float4 sj = __ldg(B.SNAP + j);
-        // r_ij = off_i - off_j - dc w with dc = field - 1
-        const float rx = fmaf(-(float)(d & 3u), C.cellwf[0], sx) - sj.x;
-        const float ry = fmaf(-(float)((d >> 2) & 3u), C.cellwf[1], sy) - sj.y;
-        const float rz = fmaf(-(float)(d >> 4), C.cellwf[2], sz) - sj.z;
-        const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        f(j, sj, rx, ry, rz, r2);
+    for (int q0 = 0; q0 < cnt; q0 += BATCH) {
+        uint32_t e[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) e[u] = (q0 + u < cnt) ? __ldg(nb + (q0 + u) * step) : 0u;
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            if (q0 + u < cnt) {
+                const int j = (int)(e[u] & NB_JMASK);
+                const uint32_t d = e[u] >> 26;
+                const float4 sj = __ldg(B.SNAP + j);
+                // r_ij = off_i - off_j - dc w with dc = field - 1
+                const float rx = fmaf(-(float)(d & 3u), C.cellwf[0], sx) - sj.x;
+                const float ry = fmaf(-(float)((d >> 2) & 3u), C.cellwf[1], sy) - sj.y;
+                const float rz = fmaf(-(float)(d >> 4), C.cellwf[2], sz) - sj.z;
+                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                f(j, sj, rx, ry, rz, r2);
+            }
+        }
     }
 }
 
-constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
+// Neighbours of a particle from its list (the common case) ...
+template <int BATCH>
+struct ListVis {
+    const CaseDev& C;
+    const Bufs& B;
+    int i;
+    float4 si;
+    uint32_t cnt;
+    template <int PART, class F>
+    __device__ __forceinline__ void run(F&& f) const {
+        if (PART & PART_FLUID) list_walk<BATCH>(C, B, i, si, 0, 1, (int)(cnt & 255u), f);
+        if (PART & PART_WALL) list_walk<BATCH>(C, B, i, si, NB_CAP - 1, -1, (int)((cnt >> 8) & 255u), f);
+    }
+};
 
-// Visit the frozen neighbours of slot i whose kind matches PART, from the
-// particle's list, or through the 27-cell loop when its list overflowed.
-template <int PART, class F>
-__device__ __forceinline__ void visit(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
-    const uint32_t cnt = B.NBC[i];
-    if ((cnt & NB_HAS) && !(cnt & NB_OVF)) {
-        if (PART & PART_FLUID) list_walk(C, B, i, si, 0, 1, (int)(cnt & 255u), f);
-        if (PART & PART_WALL) list_walk(C, B, i, si, NB_CAP - 1, -1, (int)((cnt >> 8) & 255u), f);
-    } else {
+// ... or, for a particle whose partners did not fit its list, from the
+// 27-cell loop with the same exact membership rule.
+struct CellVis {
+    const CaseDev& C;
+    const Bufs& B;
+    int i;
+    float4 si;
+    template <int PART, class F>
+    __device__ __forceinline__ void run(F&& f) const {
         for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i],
                           [&](int j, float4 sj, float rx, float ry, float rz, float r2, int) {
                               const bool fj = tag_kind(__float_as_uint(sj.w)) == KIND_FLUID;
@@ -424,7 +449,9 @@ __device__ __forceinline__ void visit(const CaseDev& C, const Bufs& B, int i, fl
                                   f(j, sj, rx, ry, rz, r2);
                           });
     }
-}
+};
+
+__device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && !(cnt & NB_OVF); }
 
 // Pass D: the advection step's neighbour search (27-cell loop, exact FP64
 // membership) writes every particle's partner list, and fluid particles get
@@ -461,6 +488,7 @@ __global__ void __launch_bounds__(128) k_passD(Bufs B, int par) {
     });
     if (nf + nw > (uint32_t)NB_CAP) {
         B.NBC[i] = NB_HAS | NB_OVF;
+        B.OVFL[atomicAdd(B.novf, 1)] = i;
         atomicOr(&B.st[tag_case(tag)].err_info, ERR_NB_OVERFLOW);
     } else {
         B.NBC[i] = NB_HAS | nf | (nw << 8);
@@ -485,16 +513,20 @@ __device__ __forceinline__ float harmonic2(float a, float b) {
     return s > 0.f ? __fdividef(2.f * a * b, s) : 0.f;
 }
 
-// Pass VT: viscous acceleration (Eq. 10 second term; wall term of Eq. 18),
-// held for the sub-steps, and dT/dt by the Cleary form (Eq. 22).  Rigid-body
-// particles also record the viscous torque of the fluid on them.
-__global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B.n) return;
-    const float4 si = B.SNAP[i];
-    const uint32_t tag = __float_as_uint(si.w);
+// UNI: every fluid particle of the case has the same material, so a fluid
+// partner's material equals the particle's own (no per-pair table loads).
+template <bool UNI>
+__device__ __forceinline__ const MatDev& fluid_mat(const CaseDev& C, const MatDev& Mi, uint32_t tj) {
+    return UNI ? Mi : C.mat[tag_mat(tj)];
+}
+
+// Pass VT for one particle: viscous acceleration (Eq. 10 second term; wall
+// term of Eq. 18), held for the sub-steps, and dT/dt by the Cleary form
+// (Eq. 22).  Rigid-body particles also record the viscous torque on them.
+template <bool UNI, class Vis>
+__device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag,
+                                            const CaseDev& C, const Vis& vis) {
     const uint32_t kind = tag_kind(tag);
-    const CaseDev& C = B.cases[tag_case(tag)];
     const MatDev& Mi = C.mat[tag_mat(tag)];
     const float4* __restrict__ V = B.V[1 - par];
     const float* __restrict__ T32 = B.T32;
@@ -503,20 +535,21 @@ __global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
         const float4 vi = V[i];
         const float rho_i = Mi.rho0 + vi.w;
         float ax = 0.f, ay = 0.f, az = 0.f, dT = 0.f;
-        visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+        const float Kii = 2.f * harmonic2(Mi.k, Mi.k), eii = harmonic2(Mi.mu, Mi.mu);
+        vis.template run<PART_FLUID>([&](int j, float4 sj, float, float, float, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
-            const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+            const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
             const float4 vj = __ldg(V + j);
             const float Vj = __fdividef(Mj.mass, Mj.rho0 + vj.w);
-            const float cv = 2.f * Vj * harmonic2(Mi.mu, Mj.mu) * inv_r * dW;
+            const float cv = 2.f * Vj * (UNI ? eii : harmonic2(Mi.mu, Mj.mu)) * inv_r * dW;
             ax = fmaf(cv, vi.x - vj.x, ax);
             ay = fmaf(cv, vi.y - vj.y, ay);
             az = fmaf(cv, vi.z - vj.z, az);
-            const float K = 2.f * harmonic2(Mi.k, Mj.k);
+            const float K = UNI ? Kii : 2.f * harmonic2(Mi.k, Mj.k);
             dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
         });
-        visit<PART_WALL>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+        vis.template run<PART_WALL>([&](int j, float4 sj, float, float, float, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
             const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
@@ -534,13 +567,9 @@ __global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
     }
     const bool thermal = !Mi.fixed_T;
     const bool rot = kind == KIND_ROT;
-    if (!thermal && !rot) {
-        B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
     const float4 vw = V[i];
     float dT = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    visit<PART_ALL>(C, B, i, si, [&](int j, float4 sj, float, float, float, float r2) {
+    vis.template run<PART_ALL>([&](int j, float4 sj, float, float, float, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
         const uint32_t tj = __float_as_uint(sj.w);
@@ -574,47 +603,83 @@ __global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
     }
 }
 
-// Pass M: half kick of density + EoS on the fly, Riemann pressure force,
-// velocity kick, both half drifts of the position (FP64).
-__device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, int i, int* case_out,
-                                           unsigned* vbits_out) {
+template <bool UNI, int BATCH>
+__global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const uint32_t cnt = B.NBC[i];
+    if (!listed(cnt)) {
+        if (!(cnt & NB_HAS)) B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // fixed-temperature static wall
+        return;                                                            // overflow: k_passVT_ovf
+    }
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
-    const uint32_t kind = tag_kind(tag);
-    const int c = tag_case(tag);
-    const CaseState& S = B.st[c];
-    if (!S.active) return;
-    const CaseDev& C = B.cases[c];
+    const CaseDev& C = B.cases[tag_case(tag)];
+    vt_particle<UNI>(B, par, i, si, tag, C, ListVis<BATCH>{C, B, i, si, cnt});
+}
+
+template <bool UNI>
+__global__ void __launch_bounds__(128) k_passVT_ovf(Bufs B, int par) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < *B.novf; k += gridDim.x * blockDim.x) {
+        const int i = B.OVFL[k];
+        const float4 si = B.SNAP[i];
+        const uint32_t tag = __float_as_uint(si.w);
+        const CaseDev& C = B.cases[tag_case(tag)];
+        vt_particle<UNI>(B, par, i, si, tag, C, CellVis{C, B, i, si});
+    }
+}
+
+// Half kick of density for the sub-step (rho += dt/2 drho), written with the
+// velocity into VH, the input of pass M for the particle and its partners.
+__global__ void k_halfkick(Bufs B, int par) {
     const float4* __restrict__ Vin = B.V[1 - par];
-    float4* Vout = B.V[par];
     const float* __restrict__ DR = B.DR[1 - par];
+    GSTRIDE_LOOP(i, B.n) {
+        const uint32_t tag = B.TAG[1 - par][i];
+        const CaseState& S = B.st[tag_case(tag)];
+        if (!S.active) continue;
+        float4 v = Vin[i];
+        if (tag_kind(tag) == KIND_FLUID) v.w = fmaf(S.hdtf, DR[i], v.w);
+        B.VH[i] = v;
+    }
+}
+
+// Pass M for one particle: Riemann pressure force (Eqs. 10-12) and the wall
+// problem (Eqs. 16-19) with half-kicked densities and the EoS (Eq. 2),
+// velocity kick, both half drifts of the position (FP64).  Rigid-body
+// particles record the pressure torque of their fluid partners.
+template <bool UNI, class Vis>
+__device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, int i, float4 si, uint32_t tag,
+                                           const CaseDev& C, const CaseState& S, const Vis& vis, int* case_out,
+                                           unsigned* vbits_out) {
+    const uint32_t kind = tag_kind(tag);
+    const float4* __restrict__ VH = B.VH;
+    float4* Vout = B.V[par];
     const float hdt = S.hdtf, dt = S.dtf;
     const MatDev& Mi = C.mat[tag_mat(tag)];
-    const float4 vi = Vin[i];
+    const float4 vi = VH[i];
     if (kind == KIND_FLUID) {
-        const float dh_i = fmaf(hdt, DR[i], vi.w);
+        const float dh_i = vi.w;
         const float rho_i = Mi.rho0 + dh_i;
         const float p_i = C.c02 * dh_i;
         float ax = 0.f, ay = 0.f, az = 0.f;
-        visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+        vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
-            const float ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-            const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
-            const float4 vj = __ldg(Vin + j);
-            const float dh_j = fmaf(hdt, __ldg(DR + j), vj.w);
-            const float rho_j = Mj.rho0 + dh_j;
-            const float p_j = C.c02 * dh_j;
-            const float rs = rho_i + rho_j;
-            const float dU = -dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, ex, ey, ez);  // U_L - U_R
+            const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
+            const float4 vj = __ldg(VH + j);
+            const float rho_j = Mj.rho0 + vj.w;
+            const float p_j = C.c02 * vj.w;
+            // U_L - U_R = -(v_i - v_j).e_ij
+            const float dU = -inv_r * dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz);
             const float beta = fminf(3.f * fmaxf(dU, 0.f), C.c0);
-            const float pstar = fmaf(0.5f, p_i + p_j, __fdividef(rho_i * rho_j * beta * dU, rs));
-            const float coef = __fdividef(Mj.mass, rho_j) * pstar * dW;
-            ax = fmaf(coef, ex, ax);
-            ay = fmaf(coef, ey, ay);
-            az = fmaf(coef, ez, az);
+            const float pstar = fmaf(0.5f, p_i + p_j, __fdividef(rho_i * rho_j * beta * dU, rho_i + rho_j));
+            const float coef = __fdividef(Mj.mass, rho_j) * pstar * dW * inv_r;
+            ax = fmaf(coef, rx, ax);
+            ay = fmaf(coef, ry, ay);
+            az = fmaf(coef, rz, az);
         });
-        visit<PART_WALL>(C, B, i, si, [&](int, float4, float rx, float ry, float rz, float r2) {
+        vis.template run<PART_WALL>([&](int, float4, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
             // one-sided wall problem: P_R = p_f + rho_f g.r_fw, r_fw = -r_ij
@@ -633,7 +698,7 @@ __device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, in
         const float nvy = vi.y + dt * (k * ay + av.y + C.g[1]);
         const float nvz = vi.z + dt * (k * az + av.z + C.g[2]);
         Vout[i] = make_float4(nvx, nvy, nvz, dh_i);
-        const double hd = (double)S.hdtf;
+        const double hd = (double)hdt;
         const double* Xs[3] = {first ? B.Y[0] : B.X[0], first ? B.Y[1] : B.X[1], first ? B.Y[2] : B.X[2]};
         const float vo[3] = {vi.x, vi.y, vi.z}, vn[3] = {nvx, nvy, nvz};
 #pragma unroll
@@ -644,8 +709,8 @@ __device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, in
             B.X[a][i] = x;
         }
         const float sp = sqrtf(dot3f(nvx, nvy, nvz, nvx, nvy, nvz));
-        if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[c].err, ERR_NAN);
-        *case_out = c;
+        if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[tag_case(tag)].err, ERR_NAN);
+        *case_out = (int)tag_case(tag);
         *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
         return;
     }
@@ -653,14 +718,13 @@ __device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, in
     if (kind != KIND_ROT) return;
     // rigid-body particle: pressure force of its fluid neighbours on it
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+    vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
         const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
-        const float4 vj = __ldg(Vin + j);
-        const float dh_j = fmaf(hdt, __ldg(DR + j), vj.w);
-        const float rho_j = Mj.rho0 + dh_j;
-        const float p_j = C.c02 * dh_j;
+        const float4 vj = __ldg(VH + j);
+        const float rho_j = Mj.rho0 + vj.w;
+        const float p_j = C.c02 * vj.w;
         // for fluid j: r_fw = r_w - r_j = r_ij (this thread is the wall)
         const float g_rfw = dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
         const float PR = fmaf(rho_j, g_rfw, p_j);
@@ -676,28 +740,48 @@ __device__ __forceinline__ void passM_body(const Bufs& B, int par, int first, in
     B.TORQ[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
 }
 
+template <bool UNI, int BATCH>
 __global__ void __launch_bounds__(128) k_passM(Bufs B, int par, int first) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int c = -1;
     unsigned vb = 0u;
-    if (i < B.n) passM_body(B, par, first, i, &c, &vb);
+    if (i < B.n) {
+        const uint32_t cnt = B.NBC[i];
+        const float4 si = B.SNAP[i];
+        const uint32_t tag = __float_as_uint(si.w);
+        const CaseState& S = B.st[tag_case(tag)];
+        if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
+            const CaseDev& C = B.cases[tag_case(tag)];
+            m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH>{C, B, i, si, cnt}, &c, &vb);
+        }
+    }
     // per-case max speed for the next step sizes: warp-aggregated atomics
     const unsigned peers = __match_any_sync(0xffffffffu, c);
     const unsigned m = __reduce_max_sync(peers, vb);
     if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&B.st[c].vmax_bits, m);
 }
 
-// Pass C: Riemann continuity (Eq. 10 first line with v* of Eq. 13) and the
-// wall problem of Eqs. (16)-(17); second half kick of density.
-__global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B.n) return;
-    const float4 si = B.SNAP[i];
-    const uint32_t tag = __float_as_uint(si.w);
-    const int c = tag_case(tag);
-    const CaseState& S = B.st[c];
-    if (!S.active) return;
-    const CaseDev& C = B.cases[c];
+template <bool UNI>
+__global__ void __launch_bounds__(128) k_passM_ovf(Bufs B, int par, int first) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < *B.novf; k += gridDim.x * blockDim.x) {
+        const int i = B.OVFL[k];
+        const float4 si = B.SNAP[i];
+        const uint32_t tag = __float_as_uint(si.w);
+        const CaseState& S = B.st[tag_case(tag)];
+        if (!S.active) continue;
+        const CaseDev& C = B.cases[tag_case(tag)];
+        int c = -1;
+        unsigned vb = 0u;
+        m_particle<UNI>(B, par, first, i, si, tag, C, S, CellVis{C, B, i, si}, &c, &vb);
+        if (c >= 0) atomicMax(&B.st[c].vmax_bits, vb);
+    }
+}
+
+// Pass C for one particle: Riemann continuity (Eq. 10 first line with v* of
+// Eq. 13) and the wall problem of Eqs. (16)-(17); second half kick.
+template <bool UNI, class Vis>
+__device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag,
+                                           const CaseDev& C, const CaseState& S, const Vis& vis) {
     const float4* __restrict__ Vin = B.V[par];
     float4* Vout = B.V[1 - par];
     const float4 vi = Vin[i];
@@ -708,10 +792,10 @@ __global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
     const MatDev& Mi = C.mat[tag_mat(tag)];
     const float rho_i = Mi.rho0 + vi.w;
     float d = 0.f;
-    visit<PART_FLUID>(C, B, i, si, [&](int j, float4 sj, float rx, float ry, float rz, float r2) {
+    vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
-        const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+        const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
         const float4 vj = __ldg(Vin + j);
         const float rho_j = Mj.rho0 + vj.w;
         // U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)), with
@@ -720,7 +804,7 @@ __global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
                               __fdividef(C.c0 * (vi.w - vj.w), rho_i + rho_j));
         d = fmaf(__fdividef(Mj.mass, rho_j) * du, dW, d);
     });
-    visit<PART_WALL>(C, B, i, si, [&](int j, float4, float rx, float ry, float rz, float r2) {
+    vis.template run<PART_WALL>([&](int j, float4, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
         const float4 nw = __ldg(B.NRM + j);
@@ -736,6 +820,33 @@ __global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
     const float drho = 2.f * rho_i * d;
     Vout[i] = make_float4(vi.x, vi.y, vi.z, fmaf(S.hdtf, drho, vi.w));
     B.DR[1 - par][i] = drho;
+}
+
+template <bool UNI, int BATCH>
+__global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const uint32_t cnt = B.NBC[i];
+    if ((cnt & NB_HAS) && (cnt & NB_OVF)) return;  // k_passC_ovf
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    const CaseState& S = B.st[tag_case(tag)];
+    if (!S.active) return;
+    const CaseDev& C = B.cases[tag_case(tag)];
+    c_particle<UNI>(B, par, i, si, tag, C, S, ListVis<BATCH>{C, B, i, si, cnt});
+}
+
+template <bool UNI>
+__global__ void __launch_bounds__(128) k_passC_ovf(Bufs B, int par) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < *B.novf; k += gridDim.x * blockDim.x) {
+        const int i = B.OVFL[k];
+        const float4 si = B.SNAP[i];
+        const uint32_t tag = __float_as_uint(si.w);
+        const CaseState& S = B.st[tag_case(tag)];
+        if (!S.active) continue;
+        const CaseDev& C = B.cases[tag_case(tag)];
+        c_particle<UNI>(B, par, i, si, tag, C, S, CellVis{C, B, i, si});
+    }
 }
 
 // -------------------------------------------------- end of advection step ---
@@ -873,8 +984,10 @@ __global__ void k_gather_field(Bufs B, int par, int field, double* out) {
 // passes use), else from the 27-cell loop (walls without pair sums)
 template <class F>
 __device__ __forceinline__ void visit_any(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
-    if (B.NBC[i] & NB_HAS) visit<PART_ALL>(C, B, i, si, [&](int j, float4, float, float, float, float) { f(j); });
-    else for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i], [&](int j, float4, float, float, float, float, int) { f(j); });
+    const uint32_t cnt = B.NBC[i];
+    auto g = [&](int j, float4, float, float, float, float) { f(j); };
+    if (listed(cnt)) ListVis<1>{C, B, i, si, cnt}.template run<PART_ALL>(g);
+    else CellVis{C, B, i, si}.template run<PART_ALL>(g);
 }
 
 __global__ void __launch_bounds__(128) k_nb_count(Bufs B, int par, int64_t* counts) {
@@ -906,8 +1019,14 @@ __global__ void __launch_bounds__(128) k_pair_stats(Bufs B, unsigned long long* 
         const uint32_t tag = __float_as_uint(si.w);
         if (tag_kind(tag) == KIND_FLUID) {
             const CaseDev& C = B.cases[tag_case(tag)];
-            visit<PART_FLUID>(C, B, i, si, [&](int, float4, float, float, float, float) { ++ff; });
-            visit<PART_WALL>(C, B, i, si, [&](int, float4, float, float, float, float) { ++fw; });
+            const uint32_t cnt = B.NBC[i];
+            if (listed(cnt)) {
+                ff = cnt & 255u;
+                fw = (cnt >> 8) & 255u;
+            } else {
+                CellVis{C, B, i, si}.template run<PART_FLUID>([&](int, float4, float, float, float, float) { ++ff; });
+                CellVis{C, B, i, si}.template run<PART_WALL>([&](int, float4, float, float, float, float) { ++fw; });
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -989,8 +1108,24 @@ cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+static const int kOvfGrid = 32;
+
+#define DISPATCH_BATCH(KERNEL, UNI, GRID, BLOCK, S, ...)                               \
+    switch (B.tune_batch) {                                                            \
+    case 1: KERNEL<UNI, 1><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
+    case 2: KERNEL<UNI, 2><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
+    case 4: KERNEL<UNI, 4><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
+    default: KERNEL<UNI, 8><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                \
+    }
+
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
-    k_passVT<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    if (B.uni_fluid) {
+        DISPATCH_BATCH(k_passVT, true, grid_1to1(B.n, 128), 128, s, B, par);
+        k_passVT_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
+    } else {
+        DISPATCH_BATCH(k_passVT, false, grid_1to1(B.n, 128), 128, s, B, par);
+        k_passVT_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par);
+    }
     return cudaGetLastError();
 }
 
@@ -1000,12 +1135,26 @@ cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s) {
 }
 
 cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
-    k_passM<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, first ? 1 : 0);
+    k_halfkick<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
+    const int f = first ? 1 : 0;
+    if (B.uni_fluid) {
+        DISPATCH_BATCH(k_passM, true, grid_1to1(B.n, 128), 128, s, B, par, f);
+        k_passM_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par, f);
+    } else {
+        DISPATCH_BATCH(k_passM, false, grid_1to1(B.n, 128), 128, s, B, par, f);
+        k_passM_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par, f);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
-    k_passC<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    if (B.uni_fluid) {
+        DISPATCH_BATCH(k_passC, true, grid_1to1(B.n, 128), 128, s, B, par);
+        k_passC_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
+    } else {
+        DISPATCH_BATCH(k_passC, false, grid_1to1(B.n, 128), 128, s, B, par);
+        k_passC_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par);
+    }
     return cudaGetLastError();
 }
 
@@ -1038,8 +1187,9 @@ cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s) {
 
 int kernels_per_advection_step(int kcap) {
     // adv_begin + sort(hash, 3 scan, scatter, order, reorder, segments)
-    // + D + VT + kcap * (sub_begin, M, C, sub_end) + T_update + 2 reduce + adv_end
-    return 1 + 8 + 2 + 4 * kcap + 4;
+    // + D + VT(+ovf) + kcap * (sub_begin, halfkick, M(+ovf), C(+ovf), sub_end)
+    // + T_update + 2 reduce + adv_end
+    return 1 + 8 + 3 + 7 * kcap + 4;
 }
 
 cudaError_t launch_gather_field(const Bufs& B, int par, int field, double* out, cudaStream_t s) {

@@ -38,6 +38,11 @@ struct Bufs {
     uint32_t* NB;   // neighbour lists, NB_CAP slots of nb_stride entries
     uint32_t* NBC;  // per-slot list counts
     int nb_stride;
+    int* OVFL;      // slots whose partners overflowed their list (this step)
+    int* novf;      // number of entries in OVFL
+    float4* VH;     // (v, half-kicked drho) input of pass M
+    int uni_fluid;  // every case has a single fluid material
+    int tune_batch; // list entries loaded together per thread in the pair passes (1, 2, 4, 8)
 };
 
 // launchers (stream-ordered; all return the launch error)

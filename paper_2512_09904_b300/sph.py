@@ -23,6 +23,7 @@ PI32 = C.POINTER(C.c_int32)
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "SPH_OK", -1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_EUNSTABLE",
           -5: "SPH_ETIMEOUT", -6: "SPH_ESTATE"}
+TUNE = dict(list_batch=0)
 PROF_CLASSES = ("sort", "pass_D", "pass_VT", "pass_M", "pass_C", "control", "adv_end", "idle")
 FIELDS = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1), a_visc=(6, 3),
               dTdt=(7, 1), normal=(9, 3))
@@ -78,12 +79,15 @@ def lib():
         L.sph_cell_sort.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile.argtypes = [vp, C.c_int]
         L.sph_pair_stats.argtypes = [vp, PI64, PI64]
+        L.sph_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        L.sph_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.sph_cell_sort_noalloc.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile_read.argtypes = [vp, PD, PI64, C.c_int]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
-                     "sph_profile", "sph_profile_read", "sph_pair_stats", "sph_cell_sort_noalloc"):
+                     "sph_profile", "sph_profile_read", "sph_pair_stats", "sph_cell_sort_noalloc",
+                     "sph_set_tuning", "sph_get_tuning"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -222,6 +226,14 @@ class Context:
         ff, fw = C.c_int64(), C.c_int64()
         self._check(self._L.sph_pair_stats(self._p, C.byref(ff), C.byref(fw)), "sph_pair_stats")
         return ff.value, fw.value
+
+    def sph_set_tuning(self, key, value):
+        self._check(self._L.sph_set_tuning(self._p, int(TUNE[key]), int(value)), "sph_set_tuning")
+
+    def sph_get_tuning(self, key):
+        v = C.c_int()
+        self._check(self._L.sph_get_tuning(self._p, int(TUNE[key]), C.byref(v)), "sph_get_tuning")
+        return v.value
 
     def sph_profile(self, enable=True):
         self._check(self._L.sph_profile(self._p, int(bool(enable))), "sph_profile")

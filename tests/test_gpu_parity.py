@@ -44,14 +44,19 @@ NEIGHBOR_CASES = [
 
 @pytest.mark.parametrize("name,make", NEIGHBOR_CASES, ids=[c[0] for c in NEIGHBOR_CASES])
 def test_neighbor_sets_bit_exact(sph, oracle, name, make):
+    # step 0: the upload's cell sort, read through the 27-cell loop;
+    # step 1: the per-particle lists the passes of the first advection step
+    # use, built from the same snapshot (positions at t = 0)
     case = make()
-    ctx = _ctx(sph, case)
-    counts, lst = ctx.sph_read_neighbors()
     f = W.flatten(case)
     R2 = case.support_radius() ** 2
     ref_counts, ref_lst = oracle.neighbors(f["pos"], R2, case.config["periodic_mask"], case.config["extent"])
-    assert np.array_equal(counts, ref_counts)
-    assert np.array_equal(lst, ref_lst)
+    ctx = _ctx(sph, case)
+    for steps in (0, 1):
+        ctx.sph_step(steps)
+        counts, lst = ctx.sph_read_neighbors()
+        assert np.array_equal(counts, ref_counts), steps
+        assert np.array_equal(lst, ref_lst), steps
 
 
 @pytest.mark.parametrize("name,make", NEIGHBOR_CASES[:4], ids=[c[0] for c in NEIGHBOR_CASES[:4]])
