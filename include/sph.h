@@ -13,8 +13,9 @@
  *  - Pointers documented as "host" are read (or written) before the call
  *    returns; the caller keeps ownership.  Pointers documented as "device"
  *    must be CUDA device allocations on the current device.
- *  - Device memory of a context is allocated by the library (cudaMalloc) and
- *    freed by sph_destroy / sph_batch_destroy.
+ *  - Device memory of a context is allocated by the library (cudaMalloc) at
+ *    its first step and freed by sph_destroy; a batch allocates at
+ *    sph_batch_create and frees at sph_batch_destroy.
  *  - Work is issued on the CUDA stream given at creation (NULL = legacy
  *    default stream).  Calls that return host data synchronise that stream.
  *  - One context must not be used by two host threads at the same time.
@@ -125,15 +126,15 @@ sph_status sph_read_torque_heat(sph_ctx* ctx, int body_id, double* torque_axis,
 
 /* Field ids for sph_read_fields (values as double, original id order). */
 enum {
-    SPH_FIELD_POS = 0,      /* n*3 */
-    SPH_FIELD_VEL = 1,      /* n*3; wall velocity for solids */
+    SPH_FIELD_POS = 0,      /* n*3; solids: at the current simulation time */
+    SPH_FIELD_VEL = 1,      /* n*3; solids: wall velocity at the current time */
     SPH_FIELD_RHO = 2,      /* n; rho0 for solids */
     SPH_FIELD_P = 3,        /* n; 0 for solids */
     SPH_FIELD_T = 4,        /* n */
     SPH_FIELD_DRHO = 5,     /* n; last continuity rate */
     SPH_FIELD_AVISC = 6,    /* n*3; viscous acceleration of the last advection step */
     SPH_FIELD_DTDT = 7,     /* n; conduction rate of the last advection step */
-    SPH_FIELD_NORMAL = 9    /* n*3; current wall normal (solids) */
+    SPH_FIELD_NORMAL = 9    /* n*3; wall normal at the current time (solids) */
 };
 
 /* Copy field `field` of all n particles (n must equal the particle count)
@@ -222,6 +223,73 @@ const char* sph_last_error(const sph_ctx* ctx);
  * cudaMallocAsync.  Errors: SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA. */
 sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], const double cellw[3],
                          const int ncell[3], int32_t* perm, int32_t* cell_start, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched cases (sweeps and serving).  A batch is one packed particle array
+ * on the device holding many independent cases (each built like a single
+ * case: sph_create + sph_set_material + sph_add_* + sph_set_rotation, never
+ * stepped).  One sph_batch_step advances every resident case by one
+ * advection step in a single CUDA graph launch; each case keeps its own step
+ * sizes, sub-step count, time, torque and heat, and its results do not depend
+ * on which other cases are resident (no cross-case sums; fixed-order
+ * per-case reductions).  Cases are admitted and retired between steps.
+ * ------------------------------------------------------------------------ */
+typedef struct sph_batch sph_batch;
+
+typedef struct {
+    int64_t max_particles; /* capacity of the packed array (all resident cases) */
+    int max_cases;         /* case slots */
+    int64_t max_cells;     /* capacity of the cell index space (sum of the cases' grids) */
+    int history_steps;     /* per-case ring of advection-step records (sph_batch_read_curve) */
+} sph_batch_config;
+
+enum { SPH_BATCH_RUNNING = 0, SPH_BATCH_DONE = 1, SPH_BATCH_UNSTABLE = -4 };
+
+/* Device bytes a batch of this configuration allocates (its HBM budget). */
+int64_t sph_batch_bytes(const sph_batch_config* cfg);
+
+/* Allocate a batch (all device memory up front).  Errors: SPH_EINVAL,
+ * SPH_ENOMEM (message in sph_last_error(NULL)), SPH_ECUDA. */
+sph_status sph_batch_create(const sph_batch_config* cfg, void* cuda_stream, sph_batch** out);
+sph_status sph_batch_destroy(sph_batch* b);
+const char* sph_batch_last_error(const sph_batch* b);
+
+/* Copy a staged case (never stepped; one fluid material) into the batch; it
+ * runs n_steps advection steps (0 = until retired).  *slot receives its
+ * slot id.  The staged context may be destroyed afterwards.  The case joins
+ * at the next sph_batch_step.  Errors: SPH_ENOMEM (no free slot, particle,
+ * cell or id capacity: the caller queues the request), SPH_EINVAL, SPH_ESTATE. */
+sph_status sph_batch_admit(sph_batch* b, sph_ctx* staged, int64_t n_steps, int* slot);
+
+/* Advance every running case n advection steps (finished cases stay
+ * resident, unchanged, until retired).  Errors: SPH_ECUDA. */
+sph_status sph_batch_step(sph_batch* b, int n_advection_steps);
+
+/* Steps done, simulated time and state (SPH_BATCH_*) of a resident case. */
+sph_status sph_batch_poll(sph_batch* b, int slot, int64_t* steps_done, double* sim_time, int* state);
+
+/* As sph_read_torque_heat, for a resident case. */
+sph_status sph_batch_read_torque_heat(sph_batch* b, int slot, int body_id, double* torque_axis,
+                                      double* torque_time_avg, double* heat_into_fluid, double* mean_fluid_T);
+
+/* The last n (<= max_steps, <= history_steps) advection-step records of a
+ * case, oldest first, 8 doubles each: time, torque of body 0, its running
+ * time average, heat into fluid, mean fluid temperature, dt_ad, sub-steps,
+ * max speed.  out: host double[8 * max_steps]. */
+sph_status sph_batch_read_curve(sph_batch* b, int slot, double* out, int64_t max_steps, int64_t* n_out);
+
+/* As sph_read_fields, for a resident case (n = its particle count). */
+sph_status sph_batch_read_fields(sph_batch* b, int slot, int field, void* host_dst, int64_t n);
+
+/* Remove a case; its particles, cells and ids are freed at the next step. */
+sph_status sph_batch_retire(sph_batch* b, int slot);
+
+/* Resident particles and cases, and kernels launched per advection step. */
+sph_status sph_batch_info(sph_batch* b, int64_t* n_particles, int* n_cases, int* kernels_per_step);
+
+sph_status sph_batch_set_tuning(sph_batch* b, int key, int value);
+sph_status sph_batch_profile(sph_batch* b, int enable);
+sph_status sph_batch_profile_read(sph_batch* b, double* ms, int64_t* launches, int reset);
 
 /* Allocation-free variant of sph_cell_sort, for callers that cannot let a
  * library allocate device memory: a process whose free HBM is already held by

@@ -1,9 +1,18 @@
-// sph_engine.cu -- host side of the C ABI (include/sph.h): validation,
-// device allocation, upload, CUDA-graph capture of one advection step, and
-// read-back.  The whole advection step (neighbour search, all passes, the
-// acoustic sub-step loop and the reductions) is one CUDA graph launch with no
-// host synchronisation; the sub-step count is data dependent and is handled
-// on the device (sub-steps past the end of the advection step are no-ops).
+// sph_engine.cu -- host side of the C ABI (include/sph.h).
+//
+// One Engine owns the device arrays of a packed particle array holding any
+// number of resident cases (a single-case context is an Engine with one
+// case).  A case occupies a contiguous segment of the array after every cell
+// sort, its own range of the cell index space and of the particle id space,
+// and one slot of the per-case parameter/state tables.  Admission appends the
+// case's particles and re-sorts; retirement marks the case dead so the next
+// sort carries its particles past the live ones, where they are dropped.
+//
+// The whole advection step (neighbour search, all passes, the acoustic
+// sub-step loop and the reductions) of all resident cases is one CUDA graph
+// launch with no host synchronisation; each case's data-dependent sub-step
+// count is handled on the device (its sub-step slots past the end of its
+// advection step are no-ops).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -21,68 +30,56 @@ void set_grid_cap(int sms);
 // message of the last failed call that has no context (sph_last_error(NULL))
 static thread_local std::string g_stateless_err;
 void set_stateless_error(const char* msg) { g_stateless_err = msg; }
-}
+}  // namespace sph
 
 using namespace sph;
 
-struct sph_ctx {
-    sph_config cfg{};
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;  // private stream used only to capture the step graph
-    std::string err;
-    sph_material mats[MAX_MAT]{};
-    bool mat_set[MAX_MAT]{};
-    struct {
-        double c[3], a[3], omega;
-        bool set;
-    } bodies[MAX_BODY]{};
-    // host staging, id order
-    std::vector<double> pos, vel, nrm, T, rho;
-    std::vector<int> kind, mat, body;
-    int64_t n_fluid = 0, n_solid = 0;
-    bool started = false;
-    // device
-    Bufs B{};
-    int parity = 0;  // index of the buffers holding the current state
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    std::vector<void*> allocs;
-    double* d_field = nullptr;
-    int kcap = 0;
-    int ncell[3]{};
-    double cellw[3]{};
-    double sigma0 = 0.0;
-    CaseState st_h{};
-    // profiling: CUDA events recorded between kernel groups inside the graph
-    bool prof = false;
-    std::vector<cudaEvent_t> ev;
-    std::vector<int> ev_class, ev_sub;  // per interval: group class and sub-step index (-1: not a sub-step)
-    double prof_ms[SPH_PROF_NCLASS]{};
-    int64_t prof_cnt[SPH_PROF_NCLASS]{};
-};
+namespace {
 
-static sph_status fail(sph_ctx* c, sph_status s, const char* fmt, ...) {
-    if (c) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        c->err = buf;
-    }
-    return s;
+std::string vformat(const char* fmt, va_list ap) {
+    char buf[512];
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    return buf;
 }
 
-#define CUDA_OR_FAIL(ctx, call)                                                                 \
-    do {                                                                                        \
-        cudaError_t e__ = (call);                                                               \
-        if (e__ != cudaSuccess)                                                                 \
-            return fail(ctx, SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, \
-                        __LINE__);                                                              \
-    } while (0)
+// First-fit allocator of [start, start+len) ranges in [0, cap).
+struct RangeAlloc {
+    std::vector<std::pair<int64_t, int64_t>> free_;  // (start, len), sorted by start
+    void reset(int64_t cap) { free_.assign(1, {0, cap}); }
+    bool alloc(int64_t len, int64_t* start) {
+        if (len == 0) {
+            *start = 0;
+            return true;
+        }
+        for (size_t k = 0; k < free_.size(); ++k)
+            if (free_[k].second >= len) {
+                *start = free_[k].first;
+                free_[k].first += len;
+                free_[k].second -= len;
+                if (free_[k].second == 0) free_.erase(free_.begin() + (long)k);
+                return true;
+            }
+        return false;
+    }
+    void release(int64_t start, int64_t len) {
+        if (len == 0) return;
+        auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(start, (int64_t)0));
+        it = free_.insert(it, {start, len});
+        size_t k = (size_t)(it - free_.begin());
+        if (k + 1 < free_.size() && free_[k].first + free_[k].second == free_[k + 1].first) {
+            free_[k].second += free_[k + 1].second;
+            free_.erase(free_.begin() + (long)k + 1);
+        }
+        if (k > 0 && free_[k - 1].first + free_[k - 1].second == free_[k].first) {
+            free_[k - 1].second += free_[k].second;
+            free_.erase(free_.begin() + (long)k);
+        }
+    }
+};
 
 // Kernel sum over the exact cubic lattice (spacing dx) including the centre:
 // the reference value sum W0 of Eq. (14).  Wendland C2, support 2h.
-static double lattice_sigma0(double dx, double h) {
+double lattice_sigma0(double dx, double h) {
     const double a = 21.0 / (16.0 * M_PI * h * h * h);
     const int m = (int)std::ceil(2.0 * h / dx) + 1;
     double s = 0.0;
@@ -97,146 +94,199 @@ static double lattice_sigma0(double dx, double h) {
     return s;
 }
 
+struct HostCase {
+    bool used = false, retiring = false, pending = false;
+    int64_t n = 0, n_fluid = 0, n_solid = 0;
+    int64_t id_base = 0, cell_base = 0, ncells = 0;
+    int kcap = 0;
+    int ncell[3] = {0, 0, 0};
+    double cellw[3] = {0, 0, 0};
+    int64_t steps_req = 0;
+};
+
+// device bytes per particle slot and per cell of an engine
+constexpr int64_t kBytesPerParticle =
+    3 * 8 * 2 /*X,Y*/ + 3 * 8 /*RP*/ + 16 * 2 /*V*/ + 4 * 2 /*DR*/ + 8 * 2 /*T64*/ + 4 * 2 /*ID*/ + 4 * 2 /*TAG*/ +
+    4 /*T32*/ + 16 /*SNAP*/ + 4 /*CELLK*/ + 16 /*AV*/ + 16 /*NRM*/ + 16 /*RN*/ + 4 * 2 /*TORQ*/ + 4 * 4 /*sort*/ +
+    4 * NB_CAP /*NB*/ + 4 /*NBC*/ + 4 /*OVFL*/ + 16 /*VH*/ + 3 * 8 /*field*/ + 1 /*PART*/;
+constexpr int64_t kBytesPerCell = 4 * 2 + 1;
+
+}  // namespace
+
+struct Engine {
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to capture the step graph
+    std::string err;
+    int64_t n_cap = 0, cells_cap = 0;
+    int c_cap = 0, hist_cap = 0;
+    bool allocated = false;
+    Bufs B{};
+    int parity = 0;  // index of the buffers holding the current state
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_dirty = true;
+    int kcap_max = 0;
+    std::vector<void*> allocs;
+    double* d_field = nullptr;
+    std::vector<HostCase> cases;
+    std::vector<CaseState> st_h;
+    RangeAlloc ids, cells;
+    bool need_prepare = false;
+    // profiling: CUDA events recorded between kernel groups inside the graph
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_class, ev_sub;  // per interval: group class and sub-step index (-1: not a sub-step)
+    double prof_ms[SPH_PROF_NCLASS]{};
+    int64_t prof_cnt[SPH_PROF_NCLASS]{};
+
+    sph_status fail(sph_status s, const char* fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        err = vformat(fmt, ap);
+        va_end(ap);
+        return s;
+    }
+    ~Engine() {
+        for (int p = 0; p < 2; ++p)
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+        if (allocated) cudaStreamSynchronize(stream);
+        for (auto e : ev) cudaEventDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+#define E_CUDA(E, call)                                                                                      \
+    do {                                                                                                     \
+        cudaError_t e__ = (call);                                                                            \
+        if (e__ != cudaSuccess)                                                                              \
+            return (E).fail(SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, __LINE__); \
+    } while (0)
+
+struct sph_ctx {
+    sph_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    sph_material mats[MAX_MAT]{};
+    bool mat_set[MAX_MAT]{};
+    struct {
+        double c[3], a[3], omega;
+        bool set;
+    } bodies[MAX_BODY]{};
+    // host staging, id order
+    std::vector<double> pos, vel, nrm, T, rho;
+    std::vector<int> kind, mat, body;
+    int64_t n_fluid = 0, n_solid = 0;
+    int ncell[3]{};
+    double cellw[3]{};
+    double sigma0 = 0.0;
+    int kcap = 0;
+    int tune_batch = 8;
+    bool started = false;   // stepped as a single case
+    bool admitted = false;  // handed to a batch
+    Engine* eng = nullptr;
+};
+
+struct sph_batch {
+    Engine eng;
+};
+
+static sph_status fail(sph_ctx* c, sph_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        c->err = vformat(fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+// ----------------------------------------------------------------- engine ---
 template <class T>
-static cudaError_t dalloc(sph_ctx* c, T** p, size_t count) {
+static cudaError_t dalloc(Engine& E, T** p, size_t count) {
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
     if (e != cudaSuccess) return e;
-    c->allocs.push_back(q);
+    E.allocs.push_back(q);
     *p = (T*)q;
-    return cudaMemsetAsync(q, 0, sizeof(T) * (count ? count : 1), c->stream);
+    return cudaMemsetAsync(q, 0, sizeof(T) * (count ? count : 1), E.stream);
 }
 
-extern "C" {
-
-const char* sph_last_error(const sph_ctx* ctx) { return ctx ? ctx->err.c_str() : sph::g_stateless_err.c_str(); }
-
-sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
-    if (!cfg || !out) return SPH_EINVAL;
-    *out = nullptr;
-    const double h = cfg->h_over_dx * cfg->dx;
-    if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) ||
-        !(cfg->cfl_ad > 0) || !(cfg->cfl_ac > 0))
-        return SPH_EINVAL;
-    sph_ctx* c = new sph_ctx();
-    c->cfg = *cfg;
-    c->stream = (cudaStream_t)stream;
-    const double R = 2.0 * h;
-    int64_t total = 1;
+static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cells_cap, int hist_cap) {
+    if (n_cap < 1 || n_cap > (int64_t)MAX_PARTICLES - 1 || c_cap < 1 || c_cap > (1 << 20) || cells_cap < 1 ||
+        cells_cap > ((int64_t)1 << 30) || hist_cap < 0)
+        return E.fail(SPH_EINVAL, "engine capacity out of range");
+    int dev = 0, sms = 148;
+    E_CUDA(E, cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    set_grid_cap(sms);
+    E.n_cap = n_cap;
+    E.c_cap = c_cap;
+    E.cells_cap = cells_cap;
+    E.hist_cap = hist_cap;
+    Bufs& B = E.B;
+    const int64_t n = n_cap;
+    B.n = 0;
+    B.ncases = c_cap;
+    B.ncells = (int)cells_cap;
+    B.max_chunks = (int)((n + RED_CHUNK - 1) / RED_CHUNK) + c_cap + 1;
+    B.hist_cap = hist_cap;
+    cudaError_t e = cudaSuccess;
+#define AL(p, cnt) \
+    if (e == cudaSuccess) e = dalloc(E, &(p), (size_t)(cnt))
+    AL(B.cases, c_cap);
+    AL(B.st, c_cap);
     for (int a = 0; a < 3; ++a) {
-        if (!(cfg->extent[a] > 0)) {
-            delete c;
-            return SPH_EINVAL;
-        }
-        int64_t n = (int64_t)std::floor(cfg->extent[a] / R);
-        if (n < 1) n = 1;
-        if ((cfg->periodic_mask & (1 << a)) && n < 3) {
-            delete c;
-            return SPH_EINVAL;
-        }
-        c->ncell[a] = (int)n;
-        c->cellw[a] = cfg->extent[a] / (double)n;
-        total *= n;
+        AL(B.X[a], n);
+        AL(B.Y[a], n);
+        AL(B.RP[a], n);
     }
-    if (total > (int64_t)1 << 30) {
-        delete c;
-        return SPH_EINVAL;
+    for (int p = 0; p < 2; ++p) {
+        AL(B.V[p], n);
+        AL(B.DR[p], n);
+        AL(B.T64[p], n);
+        AL(B.ID[p], n);
+        AL(B.TAG[p], n);
     }
-    c->kcap = cfg->max_substeps > 0
-                  ? cfg->max_substeps
-                  : (int)std::ceil(cfg->cfl_ad / cfg->cfl_ac * (cfg->c0 / cfg->u_ref + 1.0)) + 2;
-    c->sigma0 = lattice_sigma0(cfg->dx, h);
-    c->B.tune_batch = 8;
-    *out = c;
+    AL(B.T32, n);
+    AL(B.SNAP, n);
+    AL(B.CELLK, n);
+    AL(B.AV, n);
+    AL(B.NRM, n);
+    AL(B.RN, n);
+    AL(B.TORQ, n);
+    AL(B.TORQV, n);
+    AL(B.KEYS, n);
+    AL(B.RANK, n);
+    AL(B.TMP, n);
+    AL(B.PERM, n);
+    AL(B.CNT, cells_cap + 1);
+    AL(B.CSTART, cells_cap + 2);
+    AL(B.SCANBLK, scan_blocks((int)cells_cap + 1) + 1);
+    AL(B.PART, (size_t)3 * B.max_chunks);
+    AL(B.CHUNK_CASE, B.max_chunks);
+    AL(B.HIST, (size_t)8 * (hist_cap > 0 ? hist_cap : 1) * c_cap);
+    AL(E.d_field, (size_t)3 * n);
+    AL(B.NB, (size_t)NB_CAP * n);
+    AL(B.NBC, n);
+    AL(B.OVFL, n);
+    AL(B.novf, 1);
+    AL(B.VH, n);
+#undef AL
+    if (e != cudaSuccess)
+        return E.fail(e == cudaErrorMemoryAllocation ? SPH_ENOMEM : SPH_ECUDA, "device allocation: %s",
+                      cudaGetErrorString(e));
+    B.nb_stride = (int)n;
+    if (B.tune_batch == 0) B.tune_batch = 8;
+    E.cases.assign(c_cap, HostCase{});
+    E.st_h.assign(c_cap, CaseState{});
+    E.ids.reset(n_cap);
+    E.cells.reset(cells_cap);
+    E.allocated = true;
     return SPH_OK;
 }
 
-sph_status sph_destroy(sph_ctx* c) {
-    if (!c) return SPH_OK;
-    for (int p = 0; p < 2; ++p)
-        if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    else cudaDeviceSynchronize();
-    for (auto e : c->ev) cudaEventDestroy(e);
-    if (c->cap) cudaStreamDestroy(c->cap);
-    for (void* p : c->allocs) cudaFree(p);
-    delete c;
-    return SPH_OK;
-}
-
-sph_status sph_set_material(sph_ctx* c, int id, const sph_material* m) {
-    if (!c) return SPH_EINVAL;
-    if (c->started) return fail(c, SPH_ESTATE, "materials are fixed after the first step");
-    if (id < 0 || id >= MAX_MAT || !m) return fail(c, SPH_EINVAL, "material id %d out of range 0..%d", id, MAX_MAT - 1);
-    if (!(m->rho0 > 0) || !(m->cp > 0) || m->k < 0 || m->mu < 0)
-        return fail(c, SPH_EINVAL, "material %d: rho0, cp must be > 0 and k, mu >= 0", id);
-    c->mats[id] = *m;
-    c->mat_set[id] = true;
-    return SPH_OK;
-}
-
-static sph_status add_common(sph_ctx* c, int kind, int body, int mat, int64_t n, const double* pos,
-                             const double* vel, const double* nrm, const double* T, const double* rho,
-                             int64_t* first_id) {
-    if (!c) return SPH_EINVAL;
-    if (c->started) return fail(c, SPH_ESTATE, "particles can only be added before the first step");
-    if (n < 0 || (n > 0 && !pos)) return fail(c, SPH_EINVAL, "n < 0 or pos is NULL");
-    if (mat < 0 || mat >= MAX_MAT || !c->mat_set[mat]) return fail(c, SPH_EINVAL, "material %d not set", mat);
-    if (kind == 1 && (body < -1 || body >= MAX_BODY)) return fail(c, SPH_EINVAL, "body id %d out of range", body);
-    if (kind == 1 && n > 0 && !nrm) return fail(c, SPH_EINVAL, "solid particles need normals");
-    const int64_t n0 = (int64_t)c->kind.size();
-    if (n0 + n > (int64_t)MAX_PARTICLES - 1) return fail(c, SPH_EINVAL, "more than 2^26 - 1 particles");
-    const sph_material& M = c->mats[mat];
-    for (int64_t q = 0; q < 3 * n; ++q)
-        if (!std::isfinite(pos[q])) return fail(c, SPH_EINVAL, "non-finite position");
-    if (first_id) *first_id = n0;
-    for (int64_t q = 0; q < n; ++q) {
-        for (int a = 0; a < 3; ++a) {
-            double p = pos[3 * q + a];
-            c->pos.push_back(p);
-            c->vel.push_back(vel ? vel[3 * q + a] : 0.0);
-            c->nrm.push_back(nrm ? nrm[3 * q + a] : 0.0);
-        }
-        c->T.push_back(T ? T[q] : M.T_init);
-        c->rho.push_back(rho && std::isfinite(rho[q]) ? rho[q] : M.rho0);
-        c->kind.push_back(kind);
-        c->mat.push_back(mat);
-        c->body.push_back(kind == 0 ? -1 : body);
-    }
-    if (kind == 0) c->n_fluid += n;
-    else c->n_solid += n;
-    return SPH_OK;
-}
-
-sph_status sph_add_fluid(sph_ctx* c, int mat, int64_t n, const double* pos, const double* vel, const double* T,
-                         const double* rho, int64_t* first_id) {
-    return add_common(c, 0, -1, mat, n, pos, vel, nullptr, T, rho, first_id);
-}
-
-sph_status sph_add_solid(sph_ctx* c, int body, int mat, int64_t n, const double* pos, const double* normal,
-                         const double* T, int64_t* first_id) {
-    return add_common(c, 1, body, mat, n, pos, nullptr, normal, T, nullptr, first_id);
-}
-
-sph_status sph_set_rotation(sph_ctx* c, int b, const double center[3], const double axis[3], double omega) {
-    if (!c) return SPH_EINVAL;
-    if (c->started) return fail(c, SPH_ESTATE, "rotation is fixed after the first step");
-    if (b < 0 || b >= MAX_BODY || !center || !axis) return fail(c, SPH_EINVAL, "body id %d out of range", b);
-    const double L = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
-    if (std::fabs(L - 1.0) > 1e-9 || !std::isfinite(omega)) return fail(c, SPH_EINVAL, "axis must be a unit vector");
-    for (int a = 0; a < 3; ++a) {
-        c->bodies[b].c[a] = center[a];
-        c->bodies[b].a[a] = axis[a];
-    }
-    c->bodies[b].omega = omega;
-    c->bodies[b].set = true;
-    return SPH_OK;
-}
-
-}  // extern "C"
-
-// ------------------------------------------------------------------ upload --
-static sph_status build_case(sph_ctx* c, CaseDev& C) {
+// Per-case parameter table entry from a staged context.
+static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     const sph_config& F = c->cfg;
     memset(&C, 0, sizeof C);
     const double h = F.h_over_dx * F.dx;
@@ -249,7 +299,7 @@ static sph_status build_case(sph_ctx* c, CaseDev& C) {
         C.ncell[a] = c->ncell[a];
         C.g[a] = (float)F.gravity[a];
     }
-    C.cell_base = 0;
+    C.cell_base = (int)H.cell_base;
     C.ncells = c->ncell[0] * c->ncell[1] * c->ncell[2];
     C.periodic = F.periodic_mask;
     C.R2 = R2;
@@ -288,8 +338,8 @@ static sph_status build_case(sph_ctx* c, CaseDev& C) {
     C.nu_max = nu;
     C.T_ref = Tref;
     for (int m = 0; m < MAX_MAT; ++m) {
-        const sph_material& M = c->mats[m];
         if (!c->mat_set[m]) continue;
+        const sph_material& M = c->mats[m];
         C.mat[m].rho0 = (float)M.rho0;
         C.mat[m].mass = (float)(M.rho0 * F.dx * F.dx * F.dx);
         C.mat[m].mu = (float)M.mu;
@@ -301,8 +351,6 @@ static sph_status build_case(sph_ctx* c, CaseDev& C) {
     int nb = 0;
     for (int b = 0; b < MAX_BODY; ++b) {
         BodyDev& Bd = C.body[b];
-        Bd.id_lo = 0;
-        Bd.id_hi = 0;
         if (!c->bodies[b].set) continue;
         nb = b + 1;
         Bd.set = 1;
@@ -311,168 +359,81 @@ static sph_status build_case(sph_ctx* c, CaseDev& C) {
             Bd.axis[a] = c->bodies[b].a[a];
         }
         Bd.omega = c->bodies[b].omega;
-        int lo = -1, hi = -1;
+        int64_t lo = -1, hi = -1;
         for (size_t i = 0; i < c->kind.size(); ++i)
             if (c->kind[i] == 1 && c->body[i] == b) {
-                if (lo < 0) lo = (int)i;
-                hi = (int)i + 1;
+                if (lo < 0) lo = (int64_t)i;
+                hi = (int64_t)i + 1;
             }
-        Bd.id_lo = lo < 0 ? 0 : lo;
-        Bd.id_hi = hi < 0 ? 0 : hi;
+        Bd.id_lo = (int)(H.id_base + (lo < 0 ? 0 : lo));
+        Bd.id_hi = (int)(H.id_base + (hi < 0 ? 0 : hi));
     }
     C.n_body = nb;
-    return SPH_OK;
 }
 
-// Event k+1 closes interval k; intervals carry a group class (sph.h
-// SPH_PROF_*) and the acoustic sub-step index they belong to.
-static cudaError_t mark(sph_ctx* c, int cls, int sub) {
-    if (!c->prof) return cudaSuccess;
-    const size_t k = c->ev_class.size() + 1;
-    if (k >= c->ev.size()) return cudaErrorInvalidValue;
-    c->ev_class.push_back(cls);
-    c->ev_sub.push_back(sub);
-    return cudaEventRecordWithFlags(c->ev[k], c->cap, cudaEventRecordExternal);
+static bool single_fluid_material(const sph_ctx* c) {
+    int fm = -1;
+    for (size_t i = 0; i < c->kind.size(); ++i)
+        if (c->kind[i] == 0) {
+            if (fm < 0) fm = c->mat[i];
+            else if (c->mat[i] != fm) return false;
+        }
+    return true;
 }
 
-static sph_status capture(sph_ctx* c) {
-    for (int p = 0; p < 2; ++p) {
-        if (c->gexec[p]) {
-            cudaGraphExecDestroy(c->gexec[p]);
-            c->gexec[p] = nullptr;
-        }
-    }
-    // capture runs nothing; it needs a stream other than the legacy default one
-    if (!c->cap) CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    if (c->prof && c->ev.empty()) {
-        c->ev.resize(8 + 4 * (size_t)c->kcap + 8);
-        for (auto& e : c->ev) CUDA_OR_FAIL(c, cudaEventCreate(&e));
-    }
-    for (int p = 0; p < 2; ++p) {
-        cudaGraph_t g = nullptr;
-        c->ev_class.clear();
-        c->ev_sub.clear();
-        CUDA_OR_FAIL(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = c->prof ? cudaEventRecordWithFlags(c->ev[0], c->cap, cudaEventRecordExternal) : cudaSuccess;
-        if (e == cudaSuccess) e = launch_adv_begin(c->B, c->cap);
-        if (e == cudaSuccess) e = launch_sort(c->B, p, c->cap);
-        if (e == cudaSuccess) e = mark(c, SPH_PROF_SORT, -1);
-        if (e == cudaSuccess) e = launch_passD(c->B, p, c->cap);
-        if (e == cudaSuccess) e = mark(c, SPH_PROF_PASS_D, -1);
-        if (e == cudaSuccess) e = launch_passVT(c->B, p, c->cap);
-        if (e == cudaSuccess) e = mark(c, SPH_PROF_PASS_VT, -1);
-        for (int k = 0; k < c->kcap && e == cudaSuccess; ++k) {
-            e = launch_sub_begin(c->B, c->cap);
-            if (e == cudaSuccess) e = mark(c, SPH_PROF_CONTROL, k);
-            if (e == cudaSuccess) e = launch_passM(c->B, p, k == 0, c->cap);
-            if (e == cudaSuccess) e = mark(c, SPH_PROF_PASS_M, k);
-            if (e == cudaSuccess) e = launch_passC(c->B, p, c->cap);
-            if (e == cudaSuccess) e = mark(c, SPH_PROF_PASS_C, k);
-            if (e == cudaSuccess) e = launch_sub_end(c->B, c->cap);
-            if (e == cudaSuccess) e = mark(c, SPH_PROF_CONTROL, k);
-        }
-        if (e == cudaSuccess) e = launch_adv_end(c->B, p, c->cap);
-        if (e == cudaSuccess) e = mark(c, SPH_PROF_ADV_END, -1);
-        cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return fail(c, SPH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-        }
-        e = cudaGraphInstantiate(&c->gexec[p], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(c, SPH_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    }
-    return SPH_OK;
-}
-
-static sph_status upload(sph_ctx* c) {
+// Append a staged case's particles to the packed array (sorted in prepare()).
+static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, int* slot_out) {
     const int64_t n = (int64_t)c->kind.size();
-    if (n == 0) return fail(c, SPH_ESTATE, "no particles");
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    set_grid_cap(sms);
-    CaseDev C;
-    build_case(c, C);
-    Bufs& B = c->B;
-    B.n = (int)n;
-    B.ncases = 1;
-    B.ncells = C.ncells;
-    B.max_chunks = (int)((n + RED_CHUNK - 1) / RED_CHUNK) + B.ncases + 1;
-    B.hist_cap = 4096;
-    cudaError_t e = cudaSuccess;
-#define AL(p, cnt) \
-    if (e == cudaSuccess) e = dalloc(c, &(p), (size_t)(cnt))
-    AL(B.cases, 1);
-    AL(B.st, 1);
+    if (n == 0) return E.fail(SPH_EINVAL, "case has no particles");
+    int slot = -1;
+    for (int k = 0; k < E.c_cap; ++k)
+        if (!E.cases[k].used) {
+            slot = k;
+            break;
+        }
+    if (slot < 0) return E.fail(SPH_ENOMEM, "no free case slot (max_cases %d)", E.c_cap);
+    if ((int64_t)E.B.n + n > E.n_cap)
+        return E.fail(SPH_ENOMEM, "particle capacity exceeded (%lld resident + %lld > %lld)", (long long)E.B.n,
+                      (long long)n, (long long)E.n_cap);
+    const int64_t nc = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
+    HostCase H;
+    if (!E.cells.alloc(nc, &H.cell_base)) return E.fail(SPH_ENOMEM, "cell index capacity exceeded");
+    if (!E.ids.alloc(n, &H.id_base)) {
+        E.cells.release(H.cell_base, nc);
+        return E.fail(SPH_ENOMEM, "particle id capacity exceeded");
+    }
+    H.used = true;
+    H.pending = true;
+    H.n = n;
+    H.n_fluid = c->n_fluid;
+    H.n_solid = c->n_solid;
+    H.ncells = nc;
+    H.kcap = c->kcap;
+    H.steps_req = steps_req;
     for (int a = 0; a < 3; ++a) {
-        AL(B.X[a], n);
-        AL(B.Y[a], n);
-        AL(B.RP[a], n);
+        H.ncell[a] = c->ncell[a];
+        H.cellw[a] = c->cellw[a];
     }
-    for (int p = 0; p < 2; ++p) {
-        AL(B.V[p], n);
-        AL(B.DR[p], n);
-        AL(B.T64[p], n);
-        AL(B.ID[p], n);
-        AL(B.TAG[p], n);
-    }
-    AL(B.T32, n);
-    AL(B.SNAP, n);
-    AL(B.CELLK, n);
-    AL(B.AV, n);
-    AL(B.NRM, n);
-    AL(B.RN, n);
-    AL(B.TORQ, n);
-    AL(B.TORQV, n);
-    AL(B.KEYS, n);
-    AL(B.RANK, n);
-    AL(B.TMP, n);
-    AL(B.PERM, n);
-    AL(B.CNT, B.ncells);
-    AL(B.CSTART, (size_t)B.ncells + 1);
-    AL(B.SCANBLK, scan_blocks(B.ncells) + 1);
-    AL(B.PART, (size_t)3 * B.max_chunks);
-    AL(B.CHUNK_CASE, B.max_chunks);
-    AL(B.HIST, (size_t)8 * B.hist_cap * B.ncases);
-    AL(c->d_field, (size_t)3 * n);
-    AL(B.NB, (size_t)NB_CAP * n);
-    AL(B.NBC, n);
-    AL(B.OVFL, n);
-    AL(B.novf, 1);
-    AL(B.VH, n);
-    B.nb_stride = (int)n;
-    {
-        int fm = -1;
-        bool uni = true;
-        for (size_t i = 0; i < c->kind.size(); ++i)
-            if (c->kind[i] == 0) {
-                if (fm < 0) fm = c->mat[i];
-                else if (c->mat[i] != fm) uni = false;
-            }
-        B.uni_fluid = uni ? 1 : 0;
-    }
-#undef AL
-    if (e != cudaSuccess) return fail(c, e == cudaErrorMemoryAllocation ? SPH_ENOMEM : SPH_ECUDA,
-                                      "device allocation: %s", cudaGetErrorString(e));
-    // host images in id order
-    std::vector<double> xs[3], rp[3];
+    CaseDev C;
+    build_case(c, H, C);
+    CaseState S;
+    memset(&S, 0, sizeof S);
+    S.alive = 1;
+    S.running = 1;
+    S.init_pending = 1;
+    S.steps_req = steps_req;
+    // host images of the new particles (slot order = id order)
+    std::vector<double> xs[3];
     std::vector<float4> v(n), rn(n);
     std::vector<int> ids(n);
     std::vector<uint32_t> tags(n);
-    for (int a = 0; a < 3; ++a) {
-        xs[a].resize(n);
-        rp[a].resize(n);
-    }
+    for (int a = 0; a < 3; ++a) xs[a].resize(n);
     for (int64_t i = 0; i < n; ++i) {
         const int k = c->kind[i], m = c->mat[i], b = c->body[i];
         uint32_t kind = k == 0 ? KIND_FLUID : ((b >= 0 && c->bodies[b].set) ? KIND_ROT : KIND_STATIC);
-        tags[i] = make_tag((uint32_t)m, kind, kind == KIND_ROT ? (uint32_t)b : 0u, 0u);
-        ids[i] = (int)i;
-        for (int a = 0; a < 3; ++a) {
-            xs[a][i] = c->pos[3 * i + a];
-            rp[a][i] = c->pos[3 * i + a];
-        }
+        tags[i] = make_tag((uint32_t)m, kind, kind == KIND_ROT ? (uint32_t)b : 0u, (uint32_t)slot);
+        ids[i] = (int)(H.id_base + i);
+        for (int a = 0; a < 3; ++a) xs[a][i] = c->pos[3 * i + a];
         if (k == 0)
             v[i] = make_float4((float)c->vel[3 * i], (float)c->vel[3 * i + 1], (float)c->vel[3 * i + 2],
                                (float)(c->rho[i] - c->mats[m].rho0));
@@ -480,85 +441,223 @@ static sph_status upload(sph_ctx* c) {
             v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         rn[i] = make_float4((float)c->nrm[3 * i], (float)c->nrm[3 * i + 1], (float)c->nrm[3 * i + 2], 0.f);
     }
-    CaseState S;
-    memset(&S, 0, sizeof S);
-    cudaStream_t s = c->stream;
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.cases, &C, sizeof C, cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+    Bufs& B = E.B;
+    const int p = E.parity;
+    const int64_t at = B.n;
+    const int64_t idb = H.id_base;
+    cudaStream_t s = E.stream;
+    E_CUDA(E, cudaMemcpyAsync(B.cases + slot, &C, sizeof C, cudaMemcpyHostToDevice, s));
+    E_CUDA(E, cudaMemcpyAsync(B.st + slot, &S, sizeof S, cudaMemcpyHostToDevice, s));
     for (int a = 0; a < 3; ++a) {
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(B.X[a], xs[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(B.RP[a], rp[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        E_CUDA(E, cudaMemcpyAsync(B.X[a] + at, xs[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        E_CUDA(E, cudaMemcpyAsync(B.RP[a] + idb, xs[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     }
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.V[0], v.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.RN, rn.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.T64[0], c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.ID[0], ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(B.TAG[0], tags.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
-    // initial speed, rotation at t = 0, first cell sort, reference heat content
-    CUDA_OR_FAIL(c, launch_vmax_init(B, 0, s));
-    CUDA_OR_FAIL(c, launch_adv_begin(B, s));
-    CUDA_OR_FAIL(c, launch_sort(B, 0, s));
-    CUDA_OR_FAIL(c, launch_init_heat0(B, s));
+    E_CUDA(E, cudaMemcpyAsync(B.V[p] + at, v.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
+    E_CUDA(E, cudaMemsetAsync(B.DR[p] + at, 0, sizeof(float) * n, s));
+    E_CUDA(E, cudaMemcpyAsync(B.RN + idb, rn.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
+    E_CUDA(E, cudaMemsetAsync(B.TORQ + idb, 0, sizeof(float) * n, s));
+    E_CUDA(E, cudaMemsetAsync(B.TORQV + idb, 0, sizeof(float) * n, s));
+    E_CUDA(E, cudaMemcpyAsync(B.T64[p] + at, c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    E_CUDA(E, cudaMemcpyAsync(B.ID[p] + at, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    E_CUDA(E, cudaMemcpyAsync(B.TAG[p] + at, tags.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+    // the host images die at return: wait for the copies
+    E_CUDA(E, cudaStreamSynchronize(s));
+    B.n = (int)(at + n);
+    E.cases[slot] = H;
+    E.st_h[slot] = S;
+    E.need_prepare = true;
+    E.graph_dirty = true;
+    if (slot_out) *slot_out = slot;
+    return SPH_OK;
+}
+
+// Event k+1 closes interval k; intervals carry a group class (SPH_PROF_*)
+// and the acoustic sub-step index they belong to.
+static cudaError_t mark(Engine& E, int cls, int sub) {
+    if (!E.prof) return cudaSuccess;
+    const size_t k = E.ev_class.size() + 1;
+    if (k >= E.ev.size()) return cudaErrorInvalidValue;
+    E.ev_class.push_back(cls);
+    E.ev_sub.push_back(sub);
+    return cudaEventRecordWithFlags(E.ev[k], E.cap, cudaEventRecordExternal);
+}
+
+static sph_status capture(Engine& E) {
+    for (int p = 0; p < 2; ++p)
+        if (E.gexec[p]) {
+            cudaGraphExecDestroy(E.gexec[p]);
+            E.gexec[p] = nullptr;
+        }
+    // capture runs nothing; it needs a stream other than the legacy default one
+    if (!E.cap) E_CUDA(E, cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking));
+    E.kcap_max = 0;
+    for (const HostCase& H : E.cases)
+        if (H.used) E.kcap_max = std::max(E.kcap_max, H.kcap);
+    const size_t nev = 8 + 4 * (size_t)E.kcap_max + 8;
+    if (E.prof && E.ev.size() < nev) {
+        for (auto e : E.ev) cudaEventDestroy(e);
+        E.ev.assign(nev, nullptr);
+        for (auto& e : E.ev) E_CUDA(E, cudaEventCreate(&e));
+    }
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        E.ev_class.clear();
+        E.ev_sub.clear();
+        E_CUDA(E, cudaStreamBeginCapture(E.cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = E.prof ? cudaEventRecordWithFlags(E.ev[0], E.cap, cudaEventRecordExternal) : cudaSuccess;
+        if (e == cudaSuccess) e = launch_adv_begin(E.B, E.cap);
+        if (e == cudaSuccess) e = launch_sort(E.B, p, E.cap);
+        if (e == cudaSuccess) e = mark(E, SPH_PROF_SORT, -1);
+        if (e == cudaSuccess) e = launch_passD(E.B, p, E.cap);
+        if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_D, -1);
+        if (e == cudaSuccess) e = launch_passVT(E.B, p, E.cap);
+        if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_VT, -1);
+        for (int k = 0; k < E.kcap_max && e == cudaSuccess; ++k) {
+            e = launch_sub_begin(E.B, E.cap);
+            if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
+            if (e == cudaSuccess) e = launch_passM(E.B, p, k == 0, E.cap);
+            if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_M, k);
+            if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap);
+            if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_C, k);
+            if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap);
+            if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
+        }
+        if (e == cudaSuccess) e = launch_adv_end(E.B, p, E.cap);
+        if (e == cudaSuccess) e = mark(E, SPH_PROF_ADV_END, -1);
+        cudaError_t e2 = cudaStreamEndCapture(E.cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return E.fail(SPH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&E.gexec[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return E.fail(SPH_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    E.graph_dirty = false;
+    return SPH_OK;
+}
+
+static sph_status pull_state(Engine& E) {
+    E_CUDA(E, cudaMemcpyAsync(E.st_h.data(), E.B.st, sizeof(CaseState) * E.c_cap, cudaMemcpyDeviceToHost, E.stream));
+    E_CUDA(E, cudaStreamSynchronize(E.stream));
+    return SPH_OK;
+}
+
+// One cell sort outside the graph (admission or compaction), leaving the
+// current state sorted and the work positions consistent with it.
+static sph_status resort(Engine& E) {
+    Bufs& B = E.B;
+    cudaStream_t s = E.stream;
+    E_CUDA(E, launch_vmax_init(B, E.parity, s));
+    E_CUDA(E, launch_adv_begin(B, s));  // rigid-body angles at each case's current time
+    E_CUDA(E, launch_sort(B, E.parity, s));
+    E.parity ^= 1;
     for (int a = 0; a < 3; ++a)
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(B.X[a], B.Y[a], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    c->parity = 1;
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
-    sph_status rs = capture(c);
-    if (rs != SPH_OK) return rs;
-    c->started = true;
-    // host staging is no longer needed
-    std::vector<double>().swap(c->vel);
-    std::vector<double>().swap(c->rho);
+        E_CUDA(E, cudaMemcpyAsync(B.X[a], B.Y[a], sizeof(double) * B.n, cudaMemcpyDeviceToDevice, s));
     return SPH_OK;
 }
 
-static sph_status pull_state(sph_ctx* c) {
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(&c->st_h, c->B.st, sizeof(CaseState), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    return SPH_OK;
+// Apply pending retirements and admissions before the next step.
+static sph_status prepare(Engine& E) {
+    if (!E.need_prepare) return SPH_OK;
+    Bufs& B = E.B;
+    bool retire = false;
+    for (const HostCase& H : E.cases) retire |= H.used && H.retiring;
+    if (retire) {
+        // dead cases are sorted past the live particles, which are then kept
+        int64_t live = 0;
+        static const int zero = 0;
+        for (int k = 0; k < E.c_cap; ++k) {
+            HostCase& H = E.cases[k];
+            if (!H.used) continue;
+            if (!H.retiring) {
+                live += H.n;
+                continue;
+            }
+            E_CUDA(E, cudaMemcpyAsync(&B.st[k].alive, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+            E_CUDA(E, cudaMemcpyAsync(&B.st[k].running, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+        }
+        sph_status r = resort(E);
+        if (r != SPH_OK) return r;
+        B.n = (int)live;
+        for (int k = 0; k < E.c_cap; ++k) {
+            HostCase& H = E.cases[k];
+            if (!H.used || !H.retiring) continue;
+            E.cells.release(H.cell_base, H.ncells);
+            E.ids.release(H.id_base, H.n);
+            H = HostCase{};
+        }
+    }
+    bool admit = false;
+    for (const HostCase& H : E.cases) admit |= H.used && H.pending;
+    if (admit && B.n > 0) {
+        sph_status r = resort(E);
+        if (r != SPH_OK) return r;
+        E_CUDA(E, launch_init_heat0(B, E.parity, E.stream));
+        for (HostCase& H : E.cases) H.pending = false;
+    }
+    E.need_prepare = false;
+    E.graph_dirty = true;
+    return pull_state(E);
 }
 
-extern "C" {
-
-sph_status sph_step(sph_ctx* c, int n_steps, double* t_out) {
-    if (!c) return SPH_EINVAL;
-    if (n_steps < 0) return fail(c, SPH_EINVAL, "n_steps < 0");
-    if (!c->started) {
-        sph_status s = upload(c);
-        if (s != SPH_OK) return s;
+static sph_status engine_step(Engine& E, int n_steps) {
+    sph_status r = prepare(E);
+    if (r != SPH_OK) return r;
+    if (E.B.n == 0) return SPH_OK;
+    if (E.graph_dirty) {
+        r = capture(E);
+        if (r != SPH_OK) return r;
     }
     for (int k = 0; k < n_steps; ++k) {
-        CUDA_OR_FAIL(c, cudaGraphLaunch(c->gexec[c->parity], c->stream));
-        c->parity ^= 1;
-        if (c->prof) {
-            sph_status s = pull_state(c);
-            if (s != SPH_OK) return s;
-            const int nsub = c->st_h.last_nsub;
-            for (size_t q = 0; q < c->ev_class.size(); ++q) {
+        E_CUDA(E, cudaGraphLaunch(E.gexec[E.parity], E.stream));
+        E.parity ^= 1;
+        if (E.prof) {
+            r = pull_state(E);
+            if (r != SPH_OK) return r;
+            int nsub = 0;
+            for (int c = 0; c < E.c_cap; ++c)
+                if (E.cases[c].used) nsub = std::max(nsub, E.st_h[c].last_nsub);
+            for (size_t q = 0; q < E.ev_class.size(); ++q) {
                 float ms = 0.f;
-                CUDA_OR_FAIL(c, cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]));
-                const int cls = (c->ev_sub[q] >= nsub) ? SPH_PROF_IDLE : c->ev_class[q];
-                c->prof_ms[cls] += ms;
-                c->prof_cnt[cls] += 1;
+                E_CUDA(E, cudaEventElapsedTime(&ms, E.ev[q], E.ev[q + 1]));
+                const int cls = (E.ev_sub[q] >= nsub) ? SPH_PROF_IDLE : E.ev_class[q];
+                E.prof_ms[cls] += ms;
+                E.prof_cnt[cls] += 1;
             }
         }
     }
-    sph_status s = pull_state(c);
-    if (s != SPH_OK) return s;
-    if (t_out) *t_out = c->st_h.t;
-    if (c->st_h.err)
-        return fail(c, SPH_EUNSTABLE, "unstable state (error bits 0x%x: 1 = NaN/Inf, 2 = fluid left the box)",
-                    c->st_h.err);
+    return pull_state(E);
+}
+
+static int engine_kernels_per_step(const Engine& E) {
+    int kc = 0;
+    for (const HostCase& H : E.cases)
+        if (H.used) kc = std::max(kc, H.kcap);
+    return kernels_per_advection_step(kc);
+}
+
+static sph_status read_fields(Engine& E, int slot, int field, void* dst, int64_t n) {
+    const HostCase& H = E.cases[slot];
+    if (!dst || n != H.n) return E.fail(SPH_EINVAL, "n must equal the case's particle count %lld", (long long)H.n);
+    int k;
+    switch (field) {
+    case SPH_FIELD_POS: case SPH_FIELD_VEL: case SPH_FIELD_AVISC: case SPH_FIELD_NORMAL: k = 3; break;
+    case SPH_FIELD_RHO: case SPH_FIELD_P: case SPH_FIELD_T: case SPH_FIELD_DRHO: case SPH_FIELD_DTDT: k = 1; break;
+    default: return E.fail(SPH_EINVAL, "unknown field %d", field);
+    }
+    E_CUDA(E, launch_gather_field(E.B, E.parity ^ 1, field, slot, (int)H.id_base, E.d_field, E.stream));
+    E_CUDA(E, cudaMemcpyAsync(dst, E.d_field, sizeof(double) * k * n, cudaMemcpyDeviceToHost, E.stream));
+    E_CUDA(E, cudaStreamSynchronize(E.stream));
     return SPH_OK;
 }
 
-sph_status sph_read_torque_heat(sph_ctx* c, int b, double* tq, double* tq_avg, double* heat, double* meanT) {
-    if (!c) return SPH_EINVAL;
-    if (!c->started) return fail(c, SPH_ESTATE, "no step taken yet");
-    if (b < 0 || b >= MAX_BODY) return fail(c, SPH_EINVAL, "body id %d out of range", b);
-    sph_status s = pull_state(c);
+static sph_status read_torque_heat(Engine& E, int slot, int b, double* tq, double* tq_avg, double* heat,
+                                   double* meanT) {
+    if (b < 0 || b >= MAX_BODY) return E.fail(SPH_EINVAL, "body id %d out of range", b);
+    sph_status s = pull_state(E);
     if (s != SPH_OK) return s;
-    const CaseState& S = c->st_h;
+    const CaseState& S = E.st_h[slot];
     if (tq) *tq = S.tq_inst[b];
     if (tq_avg) *tq_avg = S.time_int > 0 ? S.tq_int[b] / S.time_int : 0.0;
     if (heat) *heat = S.heat;
@@ -566,32 +665,205 @@ sph_status sph_read_torque_heat(sph_ctx* c, int b, double* tq, double* tq_avg, d
     return SPH_OK;
 }
 
-sph_status sph_read_fields(sph_ctx* c, int field, void* dst, int64_t n) {
-    if (!c) return SPH_EINVAL;
-    if (!c->started) return fail(c, SPH_ESTATE, "no step taken yet");
-    if (!dst || n != (int64_t)c->B.n) return fail(c, SPH_EINVAL, "n must equal the particle count %d", c->B.n);
-    int k;
-    switch (field) {
-    case SPH_FIELD_POS: case SPH_FIELD_VEL: case SPH_FIELD_AVISC: case SPH_FIELD_NORMAL: k = 3; break;
-    case SPH_FIELD_RHO: case SPH_FIELD_P: case SPH_FIELD_T: case SPH_FIELD_DRHO: case SPH_FIELD_DTDT: k = 1; break;
-    default: return fail(c, SPH_EINVAL, "unknown field %d", field);
+// ----------------------------------------------------- single-case C ABI ---
+extern "C" {
+
+const char* sph_last_error(const sph_ctx* ctx) {
+    if (!ctx) return sph::g_stateless_err.c_str();
+    return ctx->err.c_str();
+}
+
+sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
+    if (!cfg || !out) return SPH_EINVAL;
+    *out = nullptr;
+    const double h = cfg->h_over_dx * cfg->dx;
+    if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
+        !(cfg->cfl_ac > 0))
+        return SPH_EINVAL;
+    sph_ctx* c = new sph_ctx();
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)stream;
+    const double R = 2.0 * h;
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(cfg->extent[a] > 0)) {
+            delete c;
+            return SPH_EINVAL;
+        }
+        int64_t n = (int64_t)std::floor(cfg->extent[a] / R);
+        if (n < 1) n = 1;
+        if ((cfg->periodic_mask & (1 << a)) && n < 3) {
+            delete c;
+            return SPH_EINVAL;
+        }
+        c->ncell[a] = (int)n;
+        c->cellw[a] = cfg->extent[a] / (double)n;
+        total *= n;
     }
-    CUDA_OR_FAIL(c, launch_gather_field(c->B, c->parity ^ 1, field, c->d_field, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(dst, c->d_field, sizeof(double) * k * n, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    if (total > (int64_t)1 << 30) {
+        delete c;
+        return SPH_EINVAL;
+    }
+    c->kcap = cfg->max_substeps > 0 ? cfg->max_substeps
+                                    : (int)std::ceil(cfg->cfl_ad / cfg->cfl_ac * (cfg->c0 / cfg->u_ref + 1.0)) + 2;
+    c->sigma0 = lattice_sigma0(cfg->dx, h);
+    *out = c;
     return SPH_OK;
 }
 
-sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t cap, int64_t* total) {
+sph_status sph_destroy(sph_ctx* c) {
+    if (!c) return SPH_OK;
+    delete c->eng;
+    delete c;
+    return SPH_OK;
+}
+
+sph_status sph_set_material(sph_ctx* c, int id, const sph_material* m) {
     if (!c) return SPH_EINVAL;
-    if (!c->started) return fail(c, SPH_ESTATE, "no step taken yet");
+    if (c->started || c->admitted) return fail(c, SPH_ESTATE, "materials are fixed after the first step");
+    if (id < 0 || id >= MAX_MAT || !m) return fail(c, SPH_EINVAL, "material id %d out of range 0..%d", id, MAX_MAT - 1);
+    if (!(m->rho0 > 0) || !(m->cp > 0) || m->k < 0 || m->mu < 0)
+        return fail(c, SPH_EINVAL, "material %d: rho0, cp must be > 0 and k, mu >= 0", id);
+    c->mats[id] = *m;
+    c->mat_set[id] = true;
+    return SPH_OK;
+}
+
+static sph_status add_common(sph_ctx* c, int kind, int body, int mat, int64_t n, const double* pos,
+                             const double* vel, const double* nrm, const double* T, const double* rho,
+                             int64_t* first_id) {
+    if (!c) return SPH_EINVAL;
+    if (c->started || c->admitted) return fail(c, SPH_ESTATE, "particles can only be added before the first step");
+    if (n < 0 || (n > 0 && !pos)) return fail(c, SPH_EINVAL, "n < 0 or pos is NULL");
+    if (mat < 0 || mat >= MAX_MAT || !c->mat_set[mat]) return fail(c, SPH_EINVAL, "material %d not set", mat);
+    if (kind == 1 && (body < -1 || body >= MAX_BODY)) return fail(c, SPH_EINVAL, "body id %d out of range", body);
+    if (kind == 1 && n > 0 && !nrm) return fail(c, SPH_EINVAL, "solid particles need normals");
+    const int64_t n0 = (int64_t)c->kind.size();
+    if (n0 + n > (int64_t)MAX_PARTICLES - 1) return fail(c, SPH_EINVAL, "more than 2^26 - 1 particles");
+    const sph_material& M = c->mats[mat];
+    for (int64_t q = 0; q < 3 * n; ++q)
+        if (!std::isfinite(pos[q])) return fail(c, SPH_EINVAL, "non-finite position");
+    if (first_id) *first_id = n0;
+    for (int64_t q = 0; q < n; ++q) {
+        for (int a = 0; a < 3; ++a) {
+            c->pos.push_back(pos[3 * q + a]);
+            c->vel.push_back(vel ? vel[3 * q + a] : 0.0);
+            c->nrm.push_back(nrm ? nrm[3 * q + a] : 0.0);
+        }
+        c->T.push_back(T ? T[q] : M.T_init);
+        c->rho.push_back(rho && std::isfinite(rho[q]) ? rho[q] : M.rho0);
+        c->kind.push_back(kind);
+        c->mat.push_back(mat);
+        c->body.push_back(kind == 0 ? -1 : body);
+    }
+    if (kind == 0) c->n_fluid += n;
+    else c->n_solid += n;
+    return SPH_OK;
+}
+
+sph_status sph_add_fluid(sph_ctx* c, int mat, int64_t n, const double* pos, const double* vel, const double* T,
+                         const double* rho, int64_t* first_id) {
+    return add_common(c, 0, -1, mat, n, pos, vel, nullptr, T, rho, first_id);
+}
+
+sph_status sph_add_solid(sph_ctx* c, int body, int mat, int64_t n, const double* pos, const double* normal,
+                         const double* T, int64_t* first_id) {
+    return add_common(c, 1, body, mat, n, pos, nullptr, normal, T, nullptr, first_id);
+}
+
+sph_status sph_set_rotation(sph_ctx* c, int b, const double center[3], const double axis[3], double omega) {
+    if (!c) return SPH_EINVAL;
+    if (c->started || c->admitted) return fail(c, SPH_ESTATE, "rotation is fixed after the first step");
+    if (b < 0 || b >= MAX_BODY || !center || !axis) return fail(c, SPH_EINVAL, "body id %d out of range", b);
+    const double L = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    if (std::fabs(L - 1.0) > 1e-9 || !std::isfinite(omega)) return fail(c, SPH_EINVAL, "axis must be a unit vector");
+    for (int a = 0; a < 3; ++a) {
+        c->bodies[b].c[a] = center[a];
+        c->bodies[b].a[a] = axis[a];
+    }
+    c->bodies[b].omega = omega;
+    c->bodies[b].set = true;
+    return SPH_OK;
+}
+
+}  // extern "C"
+
+// A single-case context is an engine with capacity for exactly its particles.
+static sph_status single_engine(sph_ctx* c) {
+    if (c->started) return SPH_OK;
+    if (c->admitted) return fail(c, SPH_ESTATE, "this context was admitted to a batch");
+    if (c->kind.empty()) return fail(c, SPH_ESTATE, "no particles");
+    Engine* E = new Engine();
+    E->stream = c->stream;
+    E->B.tune_batch = c->tune_batch;
+    E->B.uni_fluid = single_fluid_material(c) ? 1 : 0;
+    const int64_t nc = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
+    sph_status r = engine_alloc(*E, (int64_t)c->kind.size(), 1, nc, 4096);
+    int slot = -1;
+    if (r == SPH_OK) r = engine_admit(*E, c, 0, &slot);
+    if (r == SPH_OK) r = prepare(*E);
+    if (r == SPH_OK) r = capture(*E);
+    if (r != SPH_OK) {
+        c->err = E->err;
+        delete E;
+        return r;
+    }
+    c->eng = E;
+    c->started = true;
+    std::vector<double>().swap(c->vel);
+    std::vector<double>().swap(c->rho);
+    return SPH_OK;
+}
+
+static sph_status relay(sph_ctx* c, sph_status s) {
+    if (s != SPH_OK && c->eng) c->err = c->eng->err;
+    return s;
+}
+
+#define STARTED_OR_STATE(c)                                                   \
+    do {                                                                      \
+        if (!(c)) return SPH_EINVAL;                                          \
+        if (!(c)->started) return fail((c), SPH_ESTATE, "no step taken yet"); \
+    } while (0)
+
+extern "C" {
+
+sph_status sph_step(sph_ctx* c, int n_steps, double* t_out) {
+    if (!c) return SPH_EINVAL;
+    if (n_steps < 0) return fail(c, SPH_EINVAL, "n_steps < 0");
+    sph_status s = single_engine(c);
+    if (s != SPH_OK) return s;
+    Engine& E = *c->eng;
+    s = engine_step(E, n_steps);
+    if (s != SPH_OK) return relay(c, s);
+    if (t_out) *t_out = E.st_h[0].t;
+    if (E.st_h[0].err)
+        return fail(c, SPH_EUNSTABLE, "unstable state (error bits 0x%x: 1 = NaN/Inf, 2 = fluid left the box)",
+                    E.st_h[0].err);
+    return SPH_OK;
+}
+
+sph_status sph_read_torque_heat(sph_ctx* c, int b, double* tq, double* tq_avg, double* heat, double* meanT) {
+    STARTED_OR_STATE(c);
+    return relay(c, read_torque_heat(*c->eng, 0, b, tq, tq_avg, heat, meanT));
+}
+
+sph_status sph_read_fields(sph_ctx* c, int field, void* dst, int64_t n) {
+    STARTED_OR_STATE(c);
+    return relay(c, read_fields(*c->eng, 0, field, dst, n));
+}
+
+sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t cap, int64_t* total) {
+    STARTED_OR_STATE(c);
     if (!counts) return fail(c, SPH_EINVAL, "counts is NULL");
-    const int64_t n = c->B.n;
+    Engine& E = *c->eng;
+    const int64_t n = E.cases[0].n;
+    const int idb = (int)E.cases[0].id_base;
     int64_t* d_cnt = nullptr;
-    CUDA_OR_FAIL(c, cudaMalloc(&d_cnt, sizeof(int64_t) * (n + 1)));
-    cudaError_t e = launch_neighbors(c->B, c->parity ^ 1, d_cnt, nullptr, nullptr, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (cudaMalloc(&d_cnt, sizeof(int64_t) * (n + 1)) != cudaSuccess) return fail(c, SPH_ENOMEM, "neighbour counts");
+    cudaError_t e = launch_neighbors(E.B, E.parity ^ 1, 0, idb, d_cnt, nullptr, nullptr, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
     if (e != cudaSuccess) {
         cudaFree(d_cnt);
         return fail(c, SPH_ECUDA, "neighbour count: %s", cudaGetErrorString(e));
@@ -609,10 +881,12 @@ sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t
     }
     int32_t* d_list = nullptr;
     e = cudaMalloc(&d_list, sizeof(int32_t) * (start[n] + 1));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cnt, start.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_neighbors(c->B, c->parity ^ 1, nullptr, d_cnt, d_list, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ids, d_list, sizeof(int32_t) * start[n], cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cnt, start.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, E.stream);
+    if (e == cudaSuccess) e = launch_neighbors(E.B, E.parity ^ 1, 0, idb, nullptr, d_cnt, d_list, E.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ids, d_list, sizeof(int32_t) * start[n], cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
     cudaFree(d_list);
     cudaFree(d_cnt);
     if (e != cudaSuccess) return fail(c, SPH_ECUDA, "neighbour list: %s", cudaGetErrorString(e));
@@ -621,13 +895,16 @@ sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t
 }
 
 sph_status sph_read_cell_order(sph_ctx* c, int64_t* perm, int64_t n) {
-    if (!c) return SPH_EINVAL;
-    if (!c->started) return fail(c, SPH_ESTATE, "no step taken yet");
-    if (!perm || n != (int64_t)c->B.n) return fail(c, SPH_EINVAL, "n must equal the particle count");
+    STARTED_OR_STATE(c);
+    Engine& E = *c->eng;
+    if (!perm || n != E.cases[0].n) return fail(c, SPH_EINVAL, "n must equal the particle count");
     std::vector<int> ids(n);
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(ids.data(), c->B.ID[c->parity], sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    for (int64_t k = 0; k < n; ++k) perm[k] = ids[k];
+    const int lo = E.st_h[0].seg_lo;
+    if (cudaMemcpyAsync(ids.data(), E.B.ID[E.parity] + lo, sizeof(int) * n, cudaMemcpyDeviceToHost, E.stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(E.stream) != cudaSuccess)
+        return fail(c, SPH_ECUDA, "cell order read-back failed");
+    for (int64_t k = 0; k < n; ++k) perm[k] = ids[k] - E.cases[0].id_base;
     return SPH_OK;
 }
 
@@ -643,28 +920,31 @@ sph_status sph_get_info(sph_ctx* c, sph_info* info) {
     }
     info->graph_launches = kernels_per_advection_step(c->kcap);
     if (c->started) {
-        sph_status s = pull_state(c);
-        if (s != SPH_OK) return s;
-        info->t = c->st_h.t;
-        info->adv_steps = c->st_h.adv_steps;
-        info->substeps = c->st_h.substeps;
-        info->last_dt_ad = c->st_h.last_dt_ad;
-        info->last_nsub = c->st_h.last_nsub;
-        info->error_bits = c->st_h.err;
+        Engine& E = *c->eng;
+        sph_status s = pull_state(E);
+        if (s != SPH_OK) return relay(c, s);
+        const CaseState& S = E.st_h[0];
+        info->t = S.t;
+        info->adv_steps = S.adv_steps;
+        info->substeps = S.substeps;
+        info->last_dt_ad = S.last_dt_ad;
+        info->last_nsub = S.last_nsub;
+        info->error_bits = S.err;
     }
     return SPH_OK;
 }
 
 sph_status sph_pair_stats(sph_ctx* c, int64_t* fluid_fluid, int64_t* fluid_wall) {
-    if (!c || !fluid_fluid || !fluid_wall) return SPH_EINVAL;
-    if (!c->started) return fail(c, SPH_ESTATE, "no step taken yet");
+    STARTED_OR_STATE(c);
+    if (!fluid_fluid || !fluid_wall) return SPH_EINVAL;
+    Engine& E = *c->eng;
     unsigned long long* d = nullptr;
     unsigned long long h[2] = {0, 0};
-    CUDA_OR_FAIL(c, cudaMalloc(&d, sizeof h));
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, c->stream);
-    if (e == cudaSuccess) e = launch_pair_stats(c->B, d, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (cudaMalloc(&d, sizeof h) != cudaSuccess) return fail(c, SPH_ENOMEM, "pair stats");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, E.stream);
+    if (e == cudaSuccess) e = launch_pair_stats(E.B, d, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
     cudaFree(d);
     if (e != cudaSuccess) return fail(c, SPH_ECUDA, "pair stats: %s", cudaGetErrorString(e));
     *fluid_fluid = (int64_t)h[0];
@@ -678,63 +958,88 @@ sph_status sph_set_tuning(sph_ctx* c, int key, int value) {
     case SPH_TUNE_LIST_BATCH:
         if (value != 1 && value != 2 && value != 4 && value != 8)
             return fail(c, SPH_EINVAL, "list batch must be 1, 2, 4 or 8");
-        c->B.tune_batch = value;
+        c->tune_batch = value;
         break;
     default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
     }
     if (!c->started) return SPH_OK;
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    return capture(c);
+    Engine& E = *c->eng;
+    E.B.tune_batch = c->tune_batch;
+    if (cudaStreamSynchronize(E.stream) != cudaSuccess) return fail(c, SPH_ECUDA, "sync failed");
+    return relay(c, capture(E));
 }
 
 sph_status sph_get_tuning(sph_ctx* c, int key, int* value) {
     if (!c || !value) return SPH_EINVAL;
     switch (key) {
-    case SPH_TUNE_LIST_BATCH: *value = c->B.tune_batch; return SPH_OK;
+    case SPH_TUNE_LIST_BATCH: *value = c->tune_batch; return SPH_OK;
     default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
     }
 }
 
-sph_status sph_profile(sph_ctx* c, int enable) {
-    if (!c) return SPH_EINVAL;
-    c->prof = enable != 0;
+static sph_status engine_profile(Engine& E, int enable) {
+    E.prof = enable != 0;
     for (int k = 0; k < SPH_PROF_NCLASS; ++k) {
-        c->prof_ms[k] = 0.0;
-        c->prof_cnt[k] = 0;
+        E.prof_ms[k] = 0.0;
+        E.prof_cnt[k] = 0;
     }
-    if (!c->started) return SPH_OK;
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    return capture(c);
+    E_CUDA(E, cudaStreamSynchronize(E.stream));
+    return capture(E);
+}
+
+static void engine_profile_read(Engine& E, double* ms, int64_t* launches, int reset) {
+    for (int k = 0; k < SPH_PROF_NCLASS; ++k) {
+        ms[k] = E.prof_ms[k];
+        launches[k] = E.prof_cnt[k];
+        if (reset) {
+            E.prof_ms[k] = 0.0;
+            E.prof_cnt[k] = 0;
+        }
+    }
+}
+
+sph_status sph_profile(sph_ctx* c, int enable) {
+    STARTED_OR_STATE(c);
+    return relay(c, engine_profile(*c->eng, enable));
 }
 
 sph_status sph_profile_read(sph_ctx* c, double* ms, int64_t* launches, int reset) {
     if (!c || !ms || !launches) return SPH_EINVAL;
-    for (int k = 0; k < SPH_PROF_NCLASS; ++k) {
-        ms[k] = c->prof_ms[k];
-        launches[k] = c->prof_cnt[k];
-        if (reset) {
-            c->prof_ms[k] = 0.0;
-            c->prof_cnt[k] = 0;
-        }
-    }
+    STARTED_OR_STATE(c);
+    engine_profile_read(*c->eng, ms, launches, reset);
     return SPH_OK;
 }
 
 sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], const double cellw[3],
                          const int ncell[3], int32_t* perm, int32_t* cell_start, void* stream) {
-    if (n < 0 || (n > 0 && (!pos || !perm)) || !origin || !cellw || !ncell || !cell_start) return SPH_EINVAL;
-    if (n > ((int64_t)1 << 31) - 1) return SPH_EINVAL;
+    if (n < 0 || (n > 0 && (!pos || !perm)) || !origin || !cellw || !ncell || !cell_start) {
+        sph::set_stateless_error("sph_cell_sort: null pointer or negative n");
+        return SPH_EINVAL;
+    }
+    if (n > ((int64_t)1 << 31) - 1) {
+        sph::set_stateless_error("sph_cell_sort: n >= 2^31");
+        return SPH_EINVAL;
+    }
     int64_t nc = 1;
     for (int a = 0; a < 3; ++a) {
-        if (ncell[a] < 1 || !(cellw[a] > 0)) return SPH_EINVAL;
+        if (ncell[a] < 1 || !(cellw[a] > 0)) {
+            sph::set_stateless_error("sph_cell_sort: ncell must be >= 1 and cellw > 0");
+            return SPH_EINVAL;
+        }
         nc *= ncell[a];
     }
-    if (nc > ((int64_t)1 << 30)) return SPH_EINVAL;
+    if (nc > ((int64_t)1 << 30)) {
+        sph::set_stateless_error("sph_cell_sort: more than 2^30 cells");
+        return SPH_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = scan_blocks((int)nc) + 1;
     const size_t bytes = sizeof(uint32_t) * ((size_t)3 * (n > 0 ? n : 1) + (size_t)nc + nb);
     void* scratch = nullptr;
-    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) return SPH_ENOMEM;
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        sph::set_stateless_error("sph_cell_sort: scratch allocation failed");
+        return SPH_ENOMEM;
+    }
     uint32_t* keys = (uint32_t*)scratch;
     uint32_t* rank = keys + (n > 0 ? n : 1);
     uint32_t* tmp = rank + (n > 0 ? n : 1);
@@ -743,7 +1048,158 @@ sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], c
     cudaError_t e = launch_cell_sort(pos, (int)n, origin, cellw, ncell, keys, rank, cnt, tmp, blk, perm,
                                      cell_start, s);
     cudaError_t e2 = cudaFreeAsync(scratch, s);
-    if (e != cudaSuccess || e2 != cudaSuccess) return SPH_ECUDA;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        sph::set_stateless_error("sph_cell_sort: kernel launch failed");
+        return SPH_ECUDA;
+    }
+    return SPH_OK;
+}
+
+// ----------------------------------------------------------- batch C ABI ---
+
+int64_t sph_batch_bytes(const sph_batch_config* cfg) {
+    if (!cfg) return -1;
+    return cfg->max_particles * kBytesPerParticle + cfg->max_cells * kBytesPerCell +
+           (int64_t)cfg->max_cases * (int64_t)(sizeof(CaseDev) + sizeof(CaseState) + 64 * (int64_t)cfg->history_steps);
+}
+
+sph_status sph_batch_create(const sph_batch_config* cfg, void* stream, sph_batch** out) {
+    if (!cfg || !out) return SPH_EINVAL;
+    *out = nullptr;
+    sph_batch* b = new sph_batch();
+    b->eng.stream = (cudaStream_t)stream;
+    b->eng.B.tune_batch = 8;
+    b->eng.B.uni_fluid = 1;  // batched cases carry a single fluid material
+    sph_status s = engine_alloc(b->eng, cfg->max_particles, cfg->max_cases, cfg->max_cells, cfg->history_steps);
+    if (s != SPH_OK) {
+        sph::set_stateless_error(b->eng.err.c_str());
+        delete b;
+        return s;
+    }
+    *out = b;
+    return SPH_OK;
+}
+
+sph_status sph_batch_destroy(sph_batch* b) {
+    delete b;
+    return SPH_OK;
+}
+
+const char* sph_batch_last_error(const sph_batch* b) { return b ? b->eng.err.c_str() : sph::g_stateless_err.c_str(); }
+
+sph_status sph_batch_admit(sph_batch* b, sph_ctx* staged, int64_t n_steps, int* slot) {
+    if (!b || !staged || n_steps < 0) return SPH_EINVAL;
+    Engine& E = b->eng;
+    if (staged->started || staged->admitted) return E.fail(SPH_ESTATE, "case was already stepped or admitted");
+    if (!single_fluid_material(staged)) return E.fail(SPH_EINVAL, "batched cases need a single fluid material");
+    sph_status s = engine_admit(E, staged, n_steps, slot);
+    if (s == SPH_OK) staged->admitted = true;
+    return s;
+}
+
+sph_status sph_batch_step(sph_batch* b, int n_steps) {
+    if (!b || n_steps < 0) return SPH_EINVAL;
+    return engine_step(b->eng, n_steps);
+}
+
+static sph_status batch_slot(sph_batch* b, int slot) {
+    if (!b) return SPH_EINVAL;
+    if (slot < 0 || slot >= b->eng.c_cap || !b->eng.cases[slot].used || b->eng.cases[slot].retiring)
+        return b->eng.fail(SPH_EINVAL, "slot %d is not a resident case", slot);
+    return SPH_OK;
+}
+
+sph_status sph_batch_poll(sph_batch* b, int slot, int64_t* steps_done, double* sim_time, int* state) {
+    sph_status s = batch_slot(b, slot);
+    if (s != SPH_OK) return s;
+    const CaseState& S = b->eng.st_h[slot];
+    if (steps_done) *steps_done = S.adv_steps;
+    if (sim_time) *sim_time = S.t;
+    if (state) *state = S.err ? SPH_BATCH_UNSTABLE : (S.running ? SPH_BATCH_RUNNING : SPH_BATCH_DONE);
+    return SPH_OK;
+}
+
+sph_status sph_batch_read_torque_heat(sph_batch* b, int slot, int body, double* tq, double* tq_avg, double* heat,
+                                      double* meanT) {
+    sph_status s = batch_slot(b, slot);
+    if (s != SPH_OK) return s;
+    return read_torque_heat(b->eng, slot, body, tq, tq_avg, heat, meanT);
+}
+
+sph_status sph_batch_read_curve(sph_batch* b, int slot, double* out, int64_t max_steps, int64_t* n_out) {
+    sph_status s = batch_slot(b, slot);
+    if (s != SPH_OK) return s;
+    Engine& E = b->eng;
+    if (!out || max_steps < 0) return E.fail(SPH_EINVAL, "out is NULL or max_steps < 0");
+    const int64_t done = E.st_h[slot].adv_steps;
+    const int64_t cap = E.hist_cap;
+    const int64_t n = std::min(done, std::min(cap, max_steps));
+    if (n > 0) {
+        std::vector<double> ring((size_t)8 * (size_t)cap);
+        E_CUDA(E, cudaMemcpyAsync(ring.data(), E.B.HIST + (size_t)slot * cap * 8, sizeof(double) * 8 * cap,
+                                  cudaMemcpyDeviceToHost, E.stream));
+        E_CUDA(E, cudaStreamSynchronize(E.stream));
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t step = done - n + k;  // 0-based advection step index
+            memcpy(out + 8 * k, ring.data() + 8 * (step % cap), sizeof(double) * 8);
+        }
+    }
+    if (n_out) *n_out = n;
+    return SPH_OK;
+}
+
+sph_status sph_batch_read_fields(sph_batch* b, int slot, int field, void* host_dst, int64_t n) {
+    sph_status s = batch_slot(b, slot);
+    if (s != SPH_OK) return s;
+    if (b->eng.need_prepare) return b->eng.fail(SPH_ESTATE, "step the batch after admitting or retiring");
+    return read_fields(b->eng, slot, field, host_dst, n);
+}
+
+sph_status sph_batch_retire(sph_batch* b, int slot) {
+    sph_status s = batch_slot(b, slot);
+    if (s != SPH_OK) return s;
+    Engine& E = b->eng;
+    HostCase& H = E.cases[slot];
+    if (H.pending) return E.fail(SPH_ESTATE, "step the batch once after admitting before retiring");
+    H.retiring = true;
+    E.need_prepare = true;
+    return SPH_OK;
+}
+
+sph_status sph_batch_info(sph_batch* b, int64_t* n_particles, int* n_cases, int* kernels_per_step) {
+    if (!b) return SPH_EINVAL;
+    Engine& E = b->eng;
+    int nc = 0;
+    int64_t np = 0;
+    for (const HostCase& H : E.cases)
+        if (H.used && !H.retiring) {
+            ++nc;
+            np += H.n;
+        }
+    if (n_particles) *n_particles = np;
+    if (n_cases) *n_cases = nc;
+    if (kernels_per_step) *kernels_per_step = engine_kernels_per_step(E);
+    return SPH_OK;
+}
+
+sph_status sph_batch_set_tuning(sph_batch* b, int key, int value) {
+    if (!b) return SPH_EINVAL;
+    Engine& E = b->eng;
+    if (key != SPH_TUNE_LIST_BATCH) return E.fail(SPH_EINVAL, "unknown tuning key %d", key);
+    if (value != 1 && value != 2 && value != 4 && value != 8) return E.fail(SPH_EINVAL, "list batch must be 1, 2, 4 or 8");
+    E.B.tune_batch = value;
+    E.graph_dirty = true;
+    return SPH_OK;
+}
+
+sph_status sph_batch_profile(sph_batch* b, int enable) {
+    if (!b) return SPH_EINVAL;
+    return engine_profile(b->eng, enable);
+}
+
+sph_status sph_batch_profile_read(sph_batch* b, double* ms, int64_t* launches, int reset) {
+    if (!b || !ms || !launches) return SPH_EINVAL;
+    engine_profile_read(b->eng, ms, launches, reset);
     return SPH_OK;
 }
 

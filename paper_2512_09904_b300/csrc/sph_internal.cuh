@@ -94,6 +94,11 @@ struct CaseState {
     int chunk_lo, nchunks;
     int last_nsub, pad;
     double last_dt_ad;
+    int alive;         // resident in the engine (dead: sorted out at the next step)
+    int running;       // advancing (cleared when the requested steps are done)
+    int init_pending;  // reference heat content still to be taken
+    int pad2;
+    long long steps_req;  // advection steps requested (0 = unlimited)
 };
 
 // ---------------------------------------------------------------- kernel ---

@@ -57,7 +57,7 @@ __global__ void k_adv_begin(Bufs B) {
     S.dt_ad = C.cfl_ad * a;
     S.tau = 0.0;
     S.nsub = 0;
-    S.active = 1;
+    S.active = (S.alive && S.running) ? 1 : 0;
     S.last = 0;
     for (int b = 0; b < MAX_BODY; ++b) {
         double th = C.body[b].omega * S.t;
@@ -170,6 +170,11 @@ __global__ void k_hash(Bufs B, int par) {
         const uint32_t tag = B.TAG[par][s];
         const int c = tag_case(tag);
         const CaseDev& C = B.cases[c];
+        if (!B.st[c].alive) {  // retired case: its particles go to the last bucket
+            B.KEYS[s] = (uint32_t)B.ncells;
+            B.RANK[s] = atomicAdd(&B.CNT[B.ncells], 1u);
+            continue;
+        }
         double p[3];
         const bool fluid = tag_kind(tag) == KIND_FLUID;
         if (fluid) {
@@ -184,7 +189,7 @@ __global__ void k_hash(Bufs B, int par) {
                     if (p[a] >= o + L) { p[a] -= L; moved = true; }
                     else if (p[a] < o) { p[a] += L; moved = true; }
                 }
-            if (moved) {
+            if (moved && B.st[c].running) {  // a finished case keeps its state untouched
                 B.X[0][s] = p[0];
                 B.X[1][s] = p[1];
                 B.X[2][s] = p[2];
@@ -194,7 +199,7 @@ __global__ void k_hash(Bufs B, int par) {
         }
         bool out = false;
         uint32_t key = cell_key(C, p, &out);
-        if (out && fluid) atomicOr(&B.st[c].err, ERR_ESCAPE);
+        if (out && fluid && B.st[c].running) atomicOr(&B.st[c].err, ERR_ESCAPE);
         B.KEYS[s] = key;
         B.RANK[s] = atomicAdd(&B.CNT[key], 1u);
     }
@@ -309,6 +314,13 @@ __global__ void k_reorder(Bufs B, int par) {
         const CaseDev& C = B.cases[c];
         const uint32_t key = B.KEYS[s];
         const bool fluid = tag_kind(tag) == KIND_FLUID;
+        if (key == (uint32_t)B.ncells) {  // retired case: carried to the end, then dropped
+            B.SNAP[d] = make_float4(0.f, 0.f, 0.f, __uint_as_float(tag));
+            B.CELLK[d] = key;
+            B.ID[out][d] = id;
+            B.TAG[out][d] = tag;
+            continue;
+        }
         double p[3];
         if (fluid) {
             p[0] = B.X[0][s];
@@ -370,6 +382,12 @@ __global__ void k_segments(Bufs B) {
     for (int c = 0; c < B.ncases; ++c) {
         const CaseDev& C = B.cases[c];
         CaseState& S = B.st[c];
+        if (!S.alive) {
+            S.seg_lo = S.seg_hi = 0;
+            S.chunk_lo = q;
+            S.nchunks = 0;
+            continue;
+        }
         S.seg_lo = (int)B.CSTART[C.cell_base];
         S.seg_hi = (int)B.CSTART[C.cell_base + C.ncells];
         int nch = (S.seg_hi - S.seg_lo + RED_CHUNK - 1) / RED_CHUNK;
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(128) k_passD(Bufs B, int par) {
     const uint32_t kind = tag_kind(tag);
     const CaseDev& C = B.cases[tag_case(tag)];
     const MatDev& Mi = C.mat[tag_mat(tag)];
-    if (kind == KIND_STATIC && Mi.fixed_T) {
+    if ((kind == KIND_STATIC && Mi.fixed_T) || !B.st[tag_case(tag)].active) {
         B.NBC[i] = 0u;
         return;
     }
@@ -609,11 +627,12 @@ __global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
     if (i >= B.n) return;
     const uint32_t cnt = B.NBC[i];
     if (!listed(cnt)) {
-        if (!(cnt & NB_HAS)) B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // fixed-temperature static wall
+        if (!(cnt & NB_HAS)) B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no pair sums: no heating
         return;                                                            // overflow: k_passVT_ovf
     }
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
+    if (!B.st[tag_case(tag)].active) return;
     const CaseDev& C = B.cases[tag_case(tag)];
     vt_particle<UNI>(B, par, i, si, tag, C, ListVis<BATCH>{C, B, i, si, cnt});
 }
@@ -753,6 +772,11 @@ __global__ void __launch_bounds__(128) k_passM(Bufs B, int par, int first) {
         if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
             const CaseDev& C = B.cases[tag_case(tag)];
             m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH>{C, B, i, si, cnt}, &c, &vb);
+        } else if (!S.active && first && tag_kind(tag) == KIND_FLUID) {
+            // a case that does not advance still needs its work positions in the new order
+            B.X[0][i] = B.Y[0][i];
+            B.X[1][i] = B.Y[1][i];
+            B.X[2][i] = B.Y[2][i];
         }
     }
     // per-case max speed for the next step sizes: warp-aggregated atomics
@@ -854,8 +878,10 @@ __global__ void k_T_update(Bufs B, int par) {
     const int cur = 1 - par;
     GSTRIDE_LOOP(i, B.n) {
         const uint32_t tag = B.TAG[cur][i];
+        const CaseState& S = B.st[tag_case(tag)];
+        if (!S.running || !S.alive) continue;
         const float r = B.AV[i].w;
-        if (r != 0.0f) B.T64[cur][i] += B.st[tag_case(tag)].tau * (double)r;
+        if (r != 0.0f) B.T64[cur][i] += S.tau * (double)r;
     }
 }
 
@@ -903,9 +929,12 @@ __global__ void k_reduce_cases(Bufs B, int init) {
         m += B.PART[3 * q + 2];
     }
     if (init) {
+        if (!S.init_pending) return;
         S.heat0 = a;
         S.heat = 0.0;
+        S.init_pending = 0;
     } else {
+        if (!S.running || !S.alive) return;
         S.heat = a - S.heat0;
     }
     S.sum_mcpT = a;
@@ -918,6 +947,7 @@ __global__ void k_adv_end_cases(Bufs B) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= B.ncases) return;
     CaseState& S = B.st[c];
+    if (!S.running || !S.alive) return;
     S.t += S.tau;
     S.adv_steps += 1;
     S.last_nsub = S.nsub;
@@ -933,28 +963,68 @@ __global__ void k_adv_end_cases(Bufs B) {
         h[6] = (double)S.nsub;
         h[7] = (double)__uint_as_float(S.vmax_bits);
     }
+    if (S.steps_req > 0 && S.adv_steps >= S.steps_req) S.running = 0;
 }
 
 // ------------------------------------------------------------- readback ---
-__global__ void k_gather_field(Bufs B, int par, int field, double* out) {
+// Solid particle at the case's current time: position, normal and velocity
+// from its reference geometry (rigid rotation by omega t about (c, axis)).
+__device__ void solid_now(const CaseDev& C, const CaseState& S, uint32_t tag, const Bufs& B, int id, double p[3],
+                          double n[3], double v[3]) {
+    p[0] = B.RP[0][id];
+    p[1] = B.RP[1][id];
+    p[2] = B.RP[2][id];
+    const float4 n0 = B.RN[id];
+    n[0] = n0.x;
+    n[1] = n0.y;
+    n[2] = n0.z;
+    v[0] = v[1] = v[2] = 0.0;
+    if (tag_kind(tag) != KIND_ROT) return;
+    const BodyDev& Bd = C.body[tag_body(tag)];
+    double sn, cs;
+    sincos(Bd.omega * S.t, &sn, &cs);
+    const double* a = Bd.axis;
+    double d[3] = {p[0] - Bd.c[0], p[1] - Bd.c[1], p[2] - Bd.c[2]};
+    double rd[3], rn[3];
+    for (int pass = 0; pass < 2; ++pass) {
+        const double* x = pass == 0 ? d : n;
+        double* y = pass == 0 ? rd : rn;
+        const double axx[3] = {a[1] * x[2] - a[2] * x[1], a[2] * x[0] - a[0] * x[2], a[0] * x[1] - a[1] * x[0]};
+        const double ax = a[0] * x[0] + a[1] * x[1] + a[2] * x[2];
+        for (int k = 0; k < 3; ++k) y[k] = cs * x[k] + sn * axx[k] + (1.0 - cs) * ax * a[k];
+    }
+    for (int k = 0; k < 3; ++k) {
+        p[k] = Bd.c[k] + rd[k];
+        n[k] = rn[k];
+    }
+    v[0] = Bd.omega * (a[1] * rd[2] - a[2] * rd[1]);
+    v[1] = Bd.omega * (a[2] * rd[0] - a[0] * rd[2]);
+    v[2] = Bd.omega * (a[0] * rd[1] - a[1] * rd[0]);
+}
+
+__global__ void k_gather_field(Bufs B, int par, int field, int cs, int id_base, double* out) {
     const int cur = 1 - par;
     GSTRIDE_LOOP(i, B.n) {
         const uint32_t tag = B.TAG[cur][i];
-        const int id = B.ID[cur][i];
+        if ((int)tag_case(tag) != cs) continue;
+        const int gid = B.ID[cur][i];
+        const int id = gid - id_base;
         const CaseDev& C = B.cases[tag_case(tag)];
         const bool fluid = tag_kind(tag) == KIND_FLUID;
         const float4 v = B.V[cur][i];
         const MatDev& M = C.mat[tag_mat(tag)];
+        double sp[3], sn[3], sv[3];
+        if (!fluid && (field == 0 || field == 1 || field == 9)) solid_now(C, B.st[cs], tag, B, gid, sp, sn, sv);
         switch (field) {
         case 0:
-            out[3 * (size_t)id + 0] = fluid ? B.X[0][i] : B.Y[0][i];
-            out[3 * (size_t)id + 1] = fluid ? B.X[1][i] : B.Y[1][i];
-            out[3 * (size_t)id + 2] = fluid ? B.X[2][i] : B.Y[2][i];
+            out[3 * (size_t)id + 0] = fluid ? B.X[0][i] : sp[0];
+            out[3 * (size_t)id + 1] = fluid ? B.X[1][i] : sp[1];
+            out[3 * (size_t)id + 2] = fluid ? B.X[2][i] : sp[2];
             break;
         case 1:
-            out[3 * (size_t)id + 0] = v.x;
-            out[3 * (size_t)id + 1] = v.y;
-            out[3 * (size_t)id + 2] = v.z;
+            out[3 * (size_t)id + 0] = fluid ? (double)v.x : sv[0];
+            out[3 * (size_t)id + 1] = fluid ? (double)v.y : sv[1];
+            out[3 * (size_t)id + 2] = fluid ? (double)v.z : sv[2];
             break;
         case 2: out[id] = fluid ? (double)M.rho0 + (double)v.w : (double)M.rho0; break;
         case 3: out[id] = fluid ? (double)C.c02 * (double)v.w : 0.0; break;
@@ -968,13 +1038,11 @@ __global__ void k_gather_field(Bufs B, int par, int field, double* out) {
             break;
         }
         case 7: out[id] = B.AV[i].w; break;
-        case 9: {
-            const float4 nn = B.NRM[i];
-            out[3 * (size_t)id + 0] = fluid ? 0.0 : nn.x;
-            out[3 * (size_t)id + 1] = fluid ? 0.0 : nn.y;
-            out[3 * (size_t)id + 2] = fluid ? 0.0 : nn.z;
+        case 9:
+            out[3 * (size_t)id + 0] = fluid ? 0.0 : sn[0];
+            out[3 * (size_t)id + 1] = fluid ? 0.0 : sn[1];
+            out[3 * (size_t)id + 2] = fluid ? 0.0 : sn[2];
             break;
-        }
         default: break;
         }
     }
@@ -990,24 +1058,27 @@ __device__ __forceinline__ void visit_any(const CaseDev& C, const Bufs& B, int i
     else CellVis{C, B, i, si}.template run<PART_ALL>(g);
 }
 
-__global__ void __launch_bounds__(128) k_nb_count(Bufs B, int par, int64_t* counts) {
+__global__ void __launch_bounds__(128) k_nb_count(Bufs B, int par, int cs, int id_base, int64_t* counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
-    const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
+    if ((int)tag_case(__float_as_uint(si.w)) != cs) return;
+    const CaseDev& C = B.cases[cs];
     int64_t k = 0;
     visit_any(C, B, i, si, [&](int) { ++k; });
-    counts[B.ID[1 - par][i]] = k;
+    counts[B.ID[1 - par][i] - id_base] = k;
 }
 
-__global__ void __launch_bounds__(128) k_nb_list(Bufs B, int par, const int64_t* start, int32_t* list) {
+__global__ void __launch_bounds__(128) k_nb_list(Bufs B, int par, int cs, int id_base, const int64_t* start,
+                                                 int32_t* list) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
-    const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
+    if ((int)tag_case(__float_as_uint(si.w)) != cs) return;
+    const CaseDev& C = B.cases[cs];
     const int* ID = B.ID[1 - par];
-    int64_t k = start[ID[i]];
-    visit_any(C, B, i, si, [&](int j) { list[k++] = ID[j]; });
+    int64_t k = start[ID[i] - id_base];
+    visit_any(C, B, i, si, [&](int j) { list[k++] = ID[j] - id_base; });
 }
 
 // directed neighbour pairs of fluid particles by partner kind: [fluid, wall]
@@ -1095,7 +1166,7 @@ cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s) {
 cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s) {
     const int g = grid_stride_grid(B.n, 256);
     k_hash<<<g, 256, 0, s>>>(B, par);
-    CK(launch_scan(B.CNT, B.CSTART, B.SCANBLK, B.ncells, s));
+    CK(launch_scan(B.CNT, B.CSTART, B.SCANBLK, B.ncells + 1, s));
     k_scatter<<<g, 256, 0, s>>>(B.n, B.KEYS, B.RANK, B.CSTART, B.TMP);
     k_order<<<g, 256, 0, s>>>(B.n, B.KEYS, B.CSTART, B.TMP, B.ID[par], B.PERM);
     k_reorder<<<g, 256, 0, s>>>(B, par);
@@ -1170,10 +1241,10 @@ cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_heat0(const Bufs& B, cudaStream_t s) {
-    // called right after an initial sort with parity 0 (current buffers = 1)
+cudaError_t launch_init_heat0(const Bufs& B, int cur, cudaStream_t s) {
+    // right after a cell sort: reference heat content of newly admitted cases
     int g = B.max_chunks < g_grid_cap ? B.max_chunks : g_grid_cap;
-    k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, 1);
+    k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, cur);
     k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B, 1);
     return cudaGetLastError();
 }
@@ -1192,15 +1263,16 @@ int kernels_per_advection_step(int kcap) {
     return 1 + 8 + 3 + 7 * kcap + 4;
 }
 
-cudaError_t launch_gather_field(const Bufs& B, int par, int field, double* out, cudaStream_t s) {
-    k_gather_field<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par, field, out);
+cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int id_base, double* out,
+                                cudaStream_t s) {
+    k_gather_field<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par, field, cs, id_base, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_neighbors(const Bufs& B, int par, int64_t* counts, const int64_t* start, int32_t* list,
-                             cudaStream_t s) {
-    if (!list) k_nb_count<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, counts);
-    else k_nb_list<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, start, list);
+cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_t* counts, const int64_t* start,
+                             int32_t* list, cudaStream_t s) {
+    if (!list) k_nb_count<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, cs, id_base, counts);
+    else k_nb_list<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par, cs, id_base, start, list);
     return cudaGetLastError();
 }
 

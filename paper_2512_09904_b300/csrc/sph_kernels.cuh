@@ -11,7 +11,7 @@ constexpr int SCAN_TILE = 2048;  // cells per scan tile
 struct Bufs {
     int n;             // particle slots in use
     int ncases;
-    int ncells;        // total cells over all cases
+    int ncells;        // cell index space of all cases; key ncells is the bucket of dead particles
     int max_chunks;
     int hist_cap;
     CaseDev* cases;
@@ -57,10 +57,11 @@ cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s);
 cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s);
-cudaError_t launch_init_heat0(const Bufs& B, cudaStream_t s);
-cudaError_t launch_gather_field(const Bufs& B, int par, int field, double* out, cudaStream_t s);
-cudaError_t launch_neighbors(const Bufs& B, int par, int64_t* counts_by_id, const int64_t* start_by_id,
-                             int32_t* list, cudaStream_t s);
+cudaError_t launch_init_heat0(const Bufs& B, int cur, cudaStream_t s);
+cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int id_base, double* out,
+                                cudaStream_t s);
+cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_t* counts_by_id,
+                             const int64_t* start_by_id, int32_t* list, cudaStream_t s);
 int kernels_per_advection_step(int kcap);
 cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
 

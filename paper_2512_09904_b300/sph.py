@@ -45,6 +45,14 @@ class sph_info(C.Structure):
                 ("cell_width", D * 3), ("error_bits", C.c_int), ("graph_launches", C.c_int)]
 
 
+class sph_batch_config(C.Structure):
+    _fields_ = [("max_particles", I64), ("max_cases", C.c_int), ("max_cells", I64), ("history_steps", C.c_int)]
+
+
+BATCH_RUNNING, BATCH_DONE, BATCH_UNSTABLE = 0, 1, -4
+CURVE_FIELDS = ("t", "torque", "torque_avg", "heat", "mean_T", "dt_ad", "nsub", "vmax")
+
+
 class SphError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -80,6 +88,23 @@ def lib():
         L.sph_profile.argtypes = [vp, C.c_int]
         L.sph_pair_stats.argtypes = [vp, PI64, PI64]
         L.sph_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        L.sph_batch_bytes.argtypes = [C.POINTER(sph_batch_config)]
+        L.sph_batch_bytes.restype = I64
+        L.sph_batch_create.argtypes = [C.POINTER(sph_batch_config), vp, C.POINTER(vp)]
+        L.sph_batch_destroy.argtypes = [vp]
+        L.sph_batch_last_error.argtypes = [vp]
+        L.sph_batch_last_error.restype = C.c_char_p
+        L.sph_batch_admit.argtypes = [vp, vp, I64, C.POINTER(C.c_int)]
+        L.sph_batch_step.argtypes = [vp, C.c_int]
+        L.sph_batch_poll.argtypes = [vp, C.c_int, PI64, PD, C.POINTER(C.c_int)]
+        L.sph_batch_read_torque_heat.argtypes = [vp, C.c_int, C.c_int, PD, PD, PD, PD]
+        L.sph_batch_read_curve.argtypes = [vp, C.c_int, PD, I64, PI64]
+        L.sph_batch_read_fields.argtypes = [vp, C.c_int, C.c_int, vp, I64]
+        L.sph_batch_retire.argtypes = [vp, C.c_int]
+        L.sph_batch_info.argtypes = [vp, PI64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sph_batch_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        L.sph_batch_profile.argtypes = [vp, C.c_int]
+        L.sph_batch_profile_read.argtypes = [vp, PD, PI64, C.c_int]
         L.sph_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.sph_cell_sort_noalloc.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile_read.argtypes = [vp, PD, PI64, C.c_int]
@@ -87,7 +112,10 @@ def lib():
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
                      "sph_profile", "sph_profile_read", "sph_pair_stats", "sph_cell_sort_noalloc",
-                     "sph_set_tuning", "sph_get_tuning"):
+                     "sph_set_tuning", "sph_get_tuning", "sph_batch_create", "sph_batch_destroy",
+                     "sph_batch_admit", "sph_batch_step", "sph_batch_poll", "sph_batch_read_torque_heat",
+                     "sph_batch_read_curve", "sph_batch_read_fields", "sph_batch_retire", "sph_batch_info",
+                     "sph_batch_set_tuning", "sph_batch_profile", "sph_batch_profile_read"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -259,7 +287,7 @@ class Context:
 
 def from_case(case, stream=None) -> Context:
     """Build a Context from a workloads.Case (ids: fluid blocks, then solids)."""
-    ctx = Context(case.config, stream)
+    ctx = Context(case.config, 0 if stream is None else stream)
     for mid, m in case.materials.items():
         ctx.sph_set_material(mid, m)
     for bid, b in case.bodies.items():
@@ -298,3 +326,112 @@ def sph_cell_sort_noalloc(pos_dev_ptr: int, n: int, origin, cellw, ncell, perm_d
                                  C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream))
     if rc != SPH_OK:
         raise SphError(rc, "sph_cell_sort_noalloc: " + L.sph_last_error(None).decode())
+
+
+class Batch:
+    """A sph_batch: many cases packed in one device array, stepped together."""
+
+    def __init__(self, max_particles, max_cases, max_cells, history_steps=2048, stream=None):
+        self._L = lib()
+        cfg = sph_batch_config(int(max_particles), int(max_cases), int(max_cells), int(history_steps))
+        self.bytes = int(self._L.sph_batch_bytes(C.byref(cfg)))
+        p = C.c_void_p()
+        self.stream = current_stream_handle() if stream is None else int(stream)
+        rc = self._L.sph_batch_create(C.byref(cfg), C.c_void_p(self.stream), C.byref(p))
+        if rc != SPH_OK:
+            raise SphError(rc, "sph_batch_create: " + self._L.sph_last_error(None).decode())
+        self._p = p
+        self.n_of = {}
+
+    @staticmethod
+    def bytes_for(max_particles, max_cases, max_cells, history_steps=2048):
+        cfg = sph_batch_config(int(max_particles), int(max_cases), int(max_cells), int(history_steps))
+        return int(lib().sph_batch_bytes(C.byref(cfg)))
+
+    def _check(self, rc, what):
+        if rc != SPH_OK:
+            raise SphError(rc, f"{what}: {self._L.sph_batch_last_error(self._p).decode()}")
+
+    def admit(self, case, n_steps=0):
+        """Stage a workloads.Case and admit it; returns the slot (raises
+        SphError with status SPH_ENOMEM when the batch is full)."""
+        staged = from_case(case, stream=self.stream)
+        slot = C.c_int()
+        try:
+            self._check(self._L.sph_batch_admit(self._p, staged._p, int(n_steps), C.byref(slot)), "sph_batch_admit")
+        finally:
+            staged.close()
+        self.n_of[slot.value] = case.n_total
+        return slot.value
+
+    def step(self, n=1):
+        self._check(self._L.sph_batch_step(self._p, int(n)), "sph_batch_step")
+
+    def poll(self, slot):
+        steps, t, st = C.c_int64(), C.c_double(), C.c_int()
+        self._check(self._L.sph_batch_poll(self._p, int(slot), C.byref(steps), C.byref(t), C.byref(st)),
+                    "sph_batch_poll")
+        return steps.value, t.value, st.value
+
+    def torque_heat(self, slot, body=0):
+        v = [C.c_double() for _ in range(4)]
+        self._check(self._L.sph_batch_read_torque_heat(self._p, int(slot), int(body), *[C.byref(x) for x in v]),
+                    "sph_batch_read_torque_heat")
+        return dict(torque=v[0].value, torque_avg=v[1].value, heat=v[2].value, mean_T=v[3].value)
+
+    def curve(self, slot, max_steps):
+        out = np.zeros(8 * max(int(max_steps), 1), np.float64)
+        n = C.c_int64()
+        self._check(self._L.sph_batch_read_curve(self._p, int(slot), _pd(out), int(max_steps), C.byref(n)),
+                    "sph_batch_read_curve")
+        return out[:8 * n.value].reshape(n.value, 8)
+
+    def fields(self, slot, name):
+        fid, k = FIELDS[name]
+        n = self.n_of[slot]
+        out = np.empty(n * k, np.float64)
+        self._check(self._L.sph_batch_read_fields(self._p, int(slot), fid, out.ctypes.data_as(C.c_void_p), n),
+                    "sph_batch_read_fields")
+        return out.reshape(n, 3) if k == 3 else out
+
+    def retire(self, slot):
+        self._check(self._L.sph_batch_retire(self._p, int(slot)), "sph_batch_retire")
+        self.n_of.pop(slot, None)
+
+    def info(self):
+        n, c, k = C.c_int64(), C.c_int(), C.c_int()
+        self._check(self._L.sph_batch_info(self._p, C.byref(n), C.byref(c), C.byref(k)), "sph_batch_info")
+        return dict(n_particles=n.value, n_cases=c.value, kernels_per_step=k.value)
+
+    def set_tuning(self, key, value):
+        self._check(self._L.sph_batch_set_tuning(self._p, int(TUNE[key]), int(value)), "sph_batch_set_tuning")
+
+    def profile(self, enable=True):
+        self._check(self._L.sph_batch_profile(self._p, int(bool(enable))), "sph_batch_profile")
+
+    def profile_read(self, reset=False):
+        ms = np.zeros(len(PROF_CLASSES), np.float64)
+        cnt = np.zeros(len(PROF_CLASSES), np.int64)
+        self._check(self._L.sph_batch_profile_read(self._p, _pd(ms), cnt.ctypes.data_as(PI64), int(bool(reset))),
+                    "sph_batch_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._L.sph_batch_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cells_of(case):
+    """Cells of a case's grid (width >= 2h per axis), for batch sizing."""
+    R = case.support_radius()
+    n = 1
+    for e in case.config["extent"]:
+        n *= max(1, int(np.floor(e / R)))
+    return n
