@@ -141,8 +141,9 @@ enum {
  * into host_dst (double, n or n*3 values).  Errors: SPH_EINVAL, SPH_ESTATE. */
 sph_status sph_read_fields(sph_ctx* ctx, int field, void* host_dst, int64_t n);
 
-/* Neighbour pairs of the current advection step's frozen snapshot (pair
- * membership 0 < |r_i - r_j|^2 < (2h)^2 decided exactly as in FP64).
+/* Neighbour pairs of the last advection step's frozen snapshot (pair
+ * membership 0 < |r_i - r_j|^2 < (2h)^2 decided exactly as in FP64).  After
+ * the first step: the pairs of the initial positions.
  * counts: host int64[n] (per id).  ids: host int32[cap] or NULL; receives,
  * for each id in order, its neighbour ids in ascending order.  *total gets the
  * number of entries.  Errors: SPH_EINVAL (cap too small), SPH_ESTATE. */
@@ -150,7 +151,8 @@ sph_status sph_read_neighbors(sph_ctx* ctx, int64_t* counts, int32_t* ids, int64
                               int64_t* total);
 
 /* Cell order of the last neighbour search: perm[k] = id at sorted position k
- * (sorted by cell index, x fastest, then id).  host int64[n]. */
+ * (sorted by cell index, x fastest, then id).  host int64[n].  Errors:
+ * SPH_ESTATE before the first step. */
 sph_status sph_read_cell_order(sph_ctx* ctx, int64_t* perm, int64_t n);
 
 typedef struct {

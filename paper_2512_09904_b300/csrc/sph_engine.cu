@@ -96,6 +96,7 @@ double lattice_sigma0(double dx, double h) {
 
 struct HostCase {
     bool used = false, retiring = false, pending = false;
+    bool dead = false;  // flagged dead on the device; compacted away by the next step's sort
     int64_t n = 0, n_fluid = 0, n_solid = 0;
     int64_t id_base = 0, cell_base = 0, ncells = 0;
     int kcap = 0;
@@ -131,6 +132,8 @@ struct Engine {
     std::vector<CaseState> st_h;
     RangeAlloc ids, cells;
     bool need_prepare = false;
+    int64_t graph_steps = 0;  // advection steps launched so far
+    int64_t graph_instantiations = 0, graph_updates = 0;
     // profiling: CUDA events recorded between kernel groups inside the graph
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -264,6 +267,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     AL(B.SCANBLK, scan_blocks((int)cells_cap + 1) + 1);
     AL(B.PART, (size_t)3 * B.max_chunks);
     AL(B.CHUNK_CASE, B.max_chunks);
+    AL(B.nchunks, 1);
     AL(B.HIST, (size_t)8 * (hist_cap > 0 ? hist_cap : 1) * c_cap);
     AL(E.d_field, (size_t)3 * n);
     AL(B.NB, (size_t)NB_CAP * n);
@@ -460,6 +464,9 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     E_CUDA(E, cudaMemcpyAsync(B.T64[p] + at, c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemcpyAsync(B.ID[p] + at, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemcpyAsync(B.TAG[p] + at, tags.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+    // reference heat content and initial max speed from the appended block
+    E_CUDA(E, launch_block_heat0(B, p, slot, (int)at, (int)n, B.PART, s));
+    E_CUDA(E, launch_vmax_init(B, p, (int)at, (int)(at + n), s));
     // the host images die at return: wait for the copies
     E_CUDA(E, cudaStreamSynchronize(s));
     B.n = (int)(at + n);
@@ -483,16 +490,15 @@ static cudaError_t mark(Engine& E, int cls, int sub) {
 }
 
 static sph_status capture(Engine& E) {
-    for (int p = 0; p < 2; ++p)
-        if (E.gexec[p]) {
-            cudaGraphExecDestroy(E.gexec[p]);
-            E.gexec[p] = nullptr;
-        }
     // capture runs nothing; it needs a stream other than the legacy default one
     if (!E.cap) E_CUDA(E, cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking));
     E.kcap_max = 0;
     for (const HostCase& H : E.cases)
         if (H.used) E.kcap_max = std::max(E.kcap_max, H.kcap);
+    // neighbour lists are rebuilt every step: lay them out for the resident
+    // particles, not the capacity, so one particle's slots stay close together
+    E.B.nb_stride = std::max(E.B.n, 1);
+    E.B.max_chunks_used = (int)((E.B.n + RED_CHUNK - 1) / RED_CHUNK) + E.c_cap + 1;
     const size_t nev = 8 + 4 * (size_t)E.kcap_max + 8;
     if (E.prof && E.ev.size() < nev) {
         for (auto e : E.ev) cudaEventDestroy(e);
@@ -529,9 +535,23 @@ static sph_status capture(Engine& E) {
             if (g) cudaGraphDestroy(g);
             return E.fail(SPH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
         }
+        // same kernels in the same order (only sizes and arguments changed):
+        // patch the executable graph in place instead of instantiating anew
+        if (E.gexec[p]) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(E.gexec[p], g, &info) == cudaSuccess) {
+                cudaGraphDestroy(g);
+                ++E.graph_updates;
+                continue;
+            }
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(E.gexec[p]);
+            E.gexec[p] = nullptr;
+        }
         e = cudaGraphInstantiate(&E.gexec[p], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return E.fail(SPH_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        ++E.graph_instantiations;
     }
     E.graph_dirty = false;
     return SPH_OK;
@@ -543,62 +563,58 @@ static sph_status pull_state(Engine& E) {
     return SPH_OK;
 }
 
-// One cell sort outside the graph (admission or compaction), leaving the
-// current state sorted and the work positions consistent with it.
-static sph_status resort(Engine& E) {
-    Bufs& B = E.B;
-    cudaStream_t s = E.stream;
-    E_CUDA(E, launch_vmax_init(B, E.parity, s));
-    E_CUDA(E, launch_adv_begin(B, s));  // rigid-body angles at each case's current time
-    E_CUDA(E, launch_sort(B, E.parity, s));
-    E.parity ^= 1;
-    for (int a = 0; a < 3; ++a)
-        E_CUDA(E, cudaMemcpyAsync(B.X[a], B.Y[a], sizeof(double) * B.n, cudaMemcpyDeviceToDevice, s));
-    return SPH_OK;
+// Cells scanned per sort: up to the highest allocated cell range (the dead
+// bucket sits just past it).
+static void set_cell_high_water(Engine& E) {
+    int64_t hw = 1;
+    for (const HostCase& H : E.cases)
+        if (H.used) hw = std::max(hw, H.cell_base + H.ncells);
+    E.B.ncells = (int)hw;
 }
 
-// Apply pending retirements and admissions before the next step.
+// Apply pending retirements and admissions before the next step.  Nothing
+// is re-sorted here: admitted particles sit unsorted past the resident ones
+// and retired cases are flagged dead; the next step's cell sort places the
+// former and carries the latter past all live particles, after which
+// finish_retirements() drops them.
 static sph_status prepare(Engine& E) {
     if (!E.need_prepare) return SPH_OK;
     Bufs& B = E.B;
-    bool retire = false;
-    for (const HostCase& H : E.cases) retire |= H.used && H.retiring;
-    if (retire) {
-        // dead cases are sorted past the live particles, which are then kept
-        int64_t live = 0;
-        static const int zero = 0;
-        for (int k = 0; k < E.c_cap; ++k) {
-            HostCase& H = E.cases[k];
-            if (!H.used) continue;
-            if (!H.retiring) {
-                live += H.n;
-                continue;
-            }
-            E_CUDA(E, cudaMemcpyAsync(&B.st[k].alive, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
-            E_CUDA(E, cudaMemcpyAsync(&B.st[k].running, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
-        }
-        sph_status r = resort(E);
-        if (r != SPH_OK) return r;
-        B.n = (int)live;
-        for (int k = 0; k < E.c_cap; ++k) {
-            HostCase& H = E.cases[k];
-            if (!H.used || !H.retiring) continue;
-            E.cells.release(H.cell_base, H.ncells);
-            E.ids.release(H.id_base, H.n);
-            H = HostCase{};
-        }
+    static const int zero = 0;
+    for (int k = 0; k < E.c_cap; ++k) {
+        HostCase& H = E.cases[k];
+        if (!H.used || !H.retiring || H.dead) continue;
+        E_CUDA(E, cudaMemcpyAsync(&B.st[k].alive, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+        E_CUDA(E, cudaMemcpyAsync(&B.st[k].running, &zero, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+        H.dead = true;
     }
-    bool admit = false;
-    for (const HostCase& H : E.cases) admit |= H.used && H.pending;
-    if (admit && B.n > 0) {
-        sph_status r = resort(E);
-        if (r != SPH_OK) return r;
-        E_CUDA(E, launch_init_heat0(B, E.parity, E.stream));
-        for (HostCase& H : E.cases) H.pending = false;
-    }
+    for (HostCase& H : E.cases) H.pending = false;
+    set_cell_high_water(E);  // covers dead and newly admitted cases
     E.need_prepare = false;
     E.graph_dirty = true;
     return pull_state(E);
+}
+
+// After a step whose sort has carried the dead cases' particles past the live
+// ones: shrink the particle count to the live ones and free their ranges.
+static void finish_retirements(Engine& E) {
+    int64_t live = 0;
+    bool any = false;
+    for (const HostCase& H : E.cases) {
+        if (!H.used) continue;
+        if (H.dead) any = true;
+        else live += H.n;
+    }
+    if (!any) return;
+    E.B.n = (int)live;
+    for (HostCase& H : E.cases) {
+        if (!H.used || !H.dead) continue;
+        E.cells.release(H.cell_base, H.ncells);
+        E.ids.release(H.id_base, H.n);
+        H = HostCase{};
+    }
+    set_cell_high_water(E);
+    E.graph_dirty = true;
 }
 
 static sph_status engine_step(Engine& E, int n_steps) {
@@ -610,8 +626,14 @@ static sph_status engine_step(Engine& E, int n_steps) {
         if (r != SPH_OK) return r;
     }
     for (int k = 0; k < n_steps; ++k) {
+        if (E.graph_dirty) {
+            r = capture(E);
+            if (r != SPH_OK) return r;
+        }
         E_CUDA(E, cudaGraphLaunch(E.gexec[E.parity], E.stream));
         E.parity ^= 1;
+        ++E.graph_steps;
+        finish_retirements(E);
         if (E.prof) {
             r = pull_state(E);
             if (r != SPH_OK) return r;
@@ -744,18 +766,21 @@ static sph_status add_common(sph_ctx* c, int kind, int body, int mat, int64_t n,
     for (int64_t q = 0; q < 3 * n; ++q)
         if (!std::isfinite(pos[q])) return fail(c, SPH_EINVAL, "non-finite position");
     if (first_id) *first_id = n0;
-    for (int64_t q = 0; q < n; ++q) {
-        for (int a = 0; a < 3; ++a) {
-            c->pos.push_back(pos[3 * q + a]);
-            c->vel.push_back(vel ? vel[3 * q + a] : 0.0);
-            c->nrm.push_back(nrm ? nrm[3 * q + a] : 0.0);
-        }
-        c->T.push_back(T ? T[q] : M.T_init);
-        c->rho.push_back(rho && std::isfinite(rho[q]) ? rho[q] : M.rho0);
-        c->kind.push_back(kind);
-        c->mat.push_back(mat);
-        c->body.push_back(kind == 0 ? -1 : body);
-    }
+    c->pos.insert(c->pos.end(), pos, pos + 3 * n);
+    if (vel) c->vel.insert(c->vel.end(), vel, vel + 3 * n);
+    else c->vel.resize(c->vel.size() + 3 * n, 0.0);
+    if (nrm) c->nrm.insert(c->nrm.end(), nrm, nrm + 3 * n);
+    else c->nrm.resize(c->nrm.size() + 3 * n, 0.0);
+    if (T) c->T.insert(c->T.end(), T, T + n);
+    else c->T.resize(c->T.size() + n, M.T_init);
+    const size_t r0 = c->rho.size();
+    c->rho.resize(r0 + n, M.rho0);
+    if (rho)
+        for (int64_t q = 0; q < n; ++q)
+            if (std::isfinite(rho[q])) c->rho[r0 + q] = rho[q];
+    c->kind.resize(c->kind.size() + n, kind);
+    c->mat.resize(c->mat.size() + n, mat);
+    c->body.resize(c->body.size() + n, kind == 0 ? -1 : body);
     if (kind == 0) c->n_fluid += n;
     else c->n_solid += n;
     return SPH_OK;
@@ -855,6 +880,7 @@ sph_status sph_read_fields(sph_ctx* c, int field, void* dst, int64_t n) {
 
 sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t cap, int64_t* total) {
     STARTED_OR_STATE(c);
+    if (c->eng->graph_steps == 0) return fail(c, SPH_ESTATE, "no neighbour search before the first step");
     if (!counts) return fail(c, SPH_EINVAL, "counts is NULL");
     Engine& E = *c->eng;
     const int64_t n = E.cases[0].n;
@@ -896,6 +922,7 @@ sph_status sph_read_neighbors(sph_ctx* c, int64_t* counts, int32_t* ids, int64_t
 
 sph_status sph_read_cell_order(sph_ctx* c, int64_t* perm, int64_t n) {
     STARTED_OR_STATE(c);
+    if (c->eng->graph_steps == 0) return fail(c, SPH_ESTATE, "no cell sort before the first step");
     Engine& E = *c->eng;
     if (!perm || n != E.cases[0].n) return fail(c, SPH_EINVAL, "n must equal the particle count");
     std::vector<int> ids(n);
@@ -936,6 +963,7 @@ sph_status sph_get_info(sph_ctx* c, sph_info* info) {
 
 sph_status sph_pair_stats(sph_ctx* c, int64_t* fluid_fluid, int64_t* fluid_wall) {
     STARTED_OR_STATE(c);
+    if (c->eng->graph_steps == 0) return fail(c, SPH_ESTATE, "no neighbour search before the first step");
     if (!fluid_fluid || !fluid_wall) return SPH_EINVAL;
     Engine& E = *c->eng;
     unsigned long long* d = nullptr;

@@ -31,13 +31,27 @@ static inline int grid_1to1(int n, int block) {
 #define GSTRIDE_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
 // --------------------------------------------------------------- control ---
-__global__ void k_vmax_init(Bufs B, int par) {
-    GSTRIDE_LOOP(i, B.n) {
-        uint32_t tag = B.TAG[par][i];
-        if (tag_kind(tag) != KIND_FLUID) continue;
-        float4 v = B.V[par][i];
-        float m = sqrtf(dot3f(v.x, v.y, v.z, v.x, v.y, v.z));
-        atomicMax(&B.st[tag_case(tag)].vmax_bits, __float_as_uint(m));
+// Initial max speed of the particles in slots [lo, hi) (a newly admitted
+// case): warp-aggregated atomics per case.
+__global__ void k_vmax_init(Bufs B, int par, int lo, int hi) {
+    const int stride = gridDim.x * blockDim.x;
+    const int span = hi - lo;
+    const int rounds = (span + stride - 1) / stride;
+    for (int k = 0; k < rounds; ++k) {
+        const int i = lo + k * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        int c = -1;
+        unsigned bits = 0u;
+        if (i < hi) {
+            const uint32_t tag = B.TAG[par][i];
+            if (tag_kind(tag) == KIND_FLUID) {
+                const float4 v = B.V[par][i];
+                c = (int)tag_case(tag);
+                bits = __float_as_uint(sqrtf(dot3f(v.x, v.y, v.z, v.x, v.y, v.z)));
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const unsigned m = __reduce_max_sync(peers, bits);
+        if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&B.st[c].vmax_bits, m);
     }
 }
 
@@ -287,10 +301,17 @@ __global__ void k_scatter(int n, const uint32_t* __restrict__ keys, const uint32
 }
 
 // Within a cell, order by particle id: rank = #{cell members with smaller id}.
+// Particles in the bucket `dead` (retired cases, dropped after this sort) keep
+// their arrival rank: their order does not matter and the bucket can be large.
 __global__ void k_order(int n, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cstart,
-                        const uint32_t* __restrict__ tmp, const int* __restrict__ ids, uint32_t* perm) {
+                        const uint32_t* __restrict__ tmp, const int* __restrict__ ids, uint32_t* perm,
+                        const uint32_t* __restrict__ rank, uint32_t dead) {
     GSTRIDE_LOOP(s, n) {
         const uint32_t key = keys[s];
+        if (key == dead) {
+            perm[cstart[key] + rank[s]] = (uint32_t)s;
+            continue;
+        }
         const uint32_t a = cstart[key], b = cstart[key + 1];
         const int my = ids ? ids[s] : s;
         uint32_t r = 0;
@@ -395,7 +416,7 @@ __global__ void k_segments(Bufs B) {
         S.nchunks = nch;
         for (int k = 0; k < nch && q < B.max_chunks; ++k) B.CHUNK_CASE[q++] = c;
     }
-    for (; q < B.max_chunks; ++q) B.CHUNK_CASE[q] = -1;
+    *B.nchunks = q;  // chunks in use this step
     *B.novf = 0;  // overflow list of this advection step's neighbour search
 }
 
@@ -888,9 +909,9 @@ __global__ void k_T_update(Bufs B, int par) {
 // fixed-order partial sums per chunk of a case segment (blockDim 256)
 __global__ void __launch_bounds__(256) k_reduce_chunks(Bufs B, int cur) {
     __shared__ double sh[256];
-    for (int q = blockIdx.x; q < B.max_chunks; q += gridDim.x) {
+    const int nq = *B.nchunks;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
         const int c = B.CHUNK_CASE[q];
-        if (c < 0) break;
         const CaseState& S = B.st[c];
         const CaseDev& C = B.cases[c];
         const int lo = S.seg_lo + (q - S.chunk_lo) * RED_CHUNK;
@@ -917,7 +938,7 @@ __global__ void __launch_bounds__(256) k_reduce_chunks(Bufs B, int cur) {
     }
 }
 
-__global__ void k_reduce_cases(Bufs B, int init) {
+__global__ void k_reduce_cases(Bufs B) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= B.ncases) return;
     CaseState& S = B.st[c];
@@ -928,15 +949,8 @@ __global__ void k_reduce_cases(Bufs B, int init) {
         b += B.PART[3 * q + 1];
         m += B.PART[3 * q + 2];
     }
-    if (init) {
-        if (!S.init_pending) return;
-        S.heat0 = a;
-        S.heat = 0.0;
-        S.init_pending = 0;
-    } else {
-        if (!S.running || !S.alive) return;
-        S.heat = a - S.heat0;
-    }
+    if (!S.running || !S.alive) return;
+    S.heat = a - S.heat0;
     S.sum_mcpT = a;
     S.sum_mT = b;
     S.sum_m = m;
@@ -1153,8 +1167,8 @@ static cudaError_t launch_scan(uint32_t* cnt, uint32_t* cstart, uint32_t* blk, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_vmax_init(const Bufs& B, int par, cudaStream_t s) {
-    k_vmax_init<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
+cudaError_t launch_vmax_init(const Bufs& B, int par, int lo, int hi, cudaStream_t s) {
+    k_vmax_init<<<grid_stride_grid(hi - lo, 256), 256, 0, s>>>(B, par, lo, hi);
     return cudaGetLastError();
 }
 
@@ -1168,7 +1182,7 @@ cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s) {
     k_hash<<<g, 256, 0, s>>>(B, par);
     CK(launch_scan(B.CNT, B.CSTART, B.SCANBLK, B.ncells + 1, s));
     k_scatter<<<g, 256, 0, s>>>(B.n, B.KEYS, B.RANK, B.CSTART, B.TMP);
-    k_order<<<g, 256, 0, s>>>(B.n, B.KEYS, B.CSTART, B.TMP, B.ID[par], B.PERM);
+    k_order<<<g, 256, 0, s>>>(B.n, B.KEYS, B.CSTART, B.TMP, B.ID[par], B.PERM, B.RANK, (uint32_t)B.ncells);
     k_reorder<<<g, 256, 0, s>>>(B, par);
     k_segments<<<1, 32, 0, s>>>(B);
     return cudaGetLastError();
@@ -1235,17 +1249,47 @@ cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s) {
 }
 
 cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s) {
-    int g = B.max_chunks < g_grid_cap ? B.max_chunks : g_grid_cap;
+    int g = B.max_chunks_used < g_grid_cap ? B.max_chunks_used : g_grid_cap;
     k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, 1 - par);
-    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B, 0);
+    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_heat0(const Bufs& B, int cur, cudaStream_t s) {
-    // right after a cell sort: reference heat content of newly admitted cases
-    int g = B.max_chunks < g_grid_cap ? B.max_chunks : g_grid_cap;
-    k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, cur);
-    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B, 1);
+// Reference heat content of a newly admitted case from its appended block of
+// slots [at, at+n) (id order), fixed-order: chunk partials, then their sum.
+__global__ void __launch_bounds__(256) k_block_heat_chunks(Bufs B, int cur, int at, int n, double* part) {
+    __shared__ double sh[256];
+    const int nch = (n + RED_CHUNK - 1) / RED_CHUNK;
+    for (int q = blockIdx.x; q < nch; q += gridDim.x) {
+        const int lo = at + q * RED_CHUNK, hi = min(lo + RED_CHUNK, at + n);
+        double a = 0.0;
+        for (int i = lo + threadIdx.x; i < hi; i += 256) {
+            const uint32_t tag = B.TAG[cur][i];
+            if (tag_kind(tag) != KIND_FLUID) continue;
+            const MatDev& M = B.cases[tag_case(tag)].mat[tag_mat(tag)];
+            a += (double)M.mass * (double)M.cp * B.T64[cur][i];
+        }
+        a = block_sum_256(a, sh);
+        if (threadIdx.x == 0) part[q] = a;
+    }
+}
+
+__global__ void k_block_heat_final(Bufs B, int slot, int n, const double* part) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nch = (n + RED_CHUNK - 1) / RED_CHUNK;
+    double a = 0.0;
+    for (int q = 0; q < nch; ++q) a += part[q];
+    CaseState& S = B.st[slot];
+    S.heat0 = a;
+    S.heat = 0.0;
+    S.init_pending = 0;
+}
+
+cudaError_t launch_block_heat0(const Bufs& B, int cur, int slot, int at, int n, double* part, cudaStream_t s) {
+    const int nch = (n + RED_CHUNK - 1) / RED_CHUNK;
+    int g = nch < g_grid_cap ? nch : g_grid_cap;
+    k_block_heat_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, cur, at, n, part);
+    k_block_heat_final<<<1, 32, 0, s>>>(B, slot, n, part);
     return cudaGetLastError();
 }
 
@@ -1287,7 +1331,7 @@ cudaError_t launch_cell_sort(const double* pos, int n, const double origin[3], c
     uint32_t* cs = reinterpret_cast<uint32_t*>(cell_start);
     CK(launch_scan(cnt, cs, scanblk, ncells, s));
     k_scatter<<<g, 256, 0, s>>>(n, keys, rank, cs, tmp);
-    k_order<<<g, 256, 0, s>>>(n, keys, cs, tmp, nullptr, reinterpret_cast<uint32_t*>(perm));
+    k_order<<<g, 256, 0, s>>>(n, keys, cs, tmp, nullptr, reinterpret_cast<uint32_t*>(perm), rank, 0xffffffffu);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,8 @@ struct Bufs {
     int n;             // particle slots in use
     int ncases;
     int ncells;        // cell index space of all cases; key ncells is the bucket of dead particles
-    int max_chunks;
+    int max_chunks;       // capacity of the chunk table
+    int max_chunks_used;  // chunks that the resident particles can need
     int hist_cap;
     CaseDev* cases;
     CaseState* st;
@@ -34,6 +35,7 @@ struct Bufs {
     uint32_t *KEYS, *RANK, *TMP, *PERM, *CNT, *CSTART, *SCANBLK;
     double* PART;
     int* CHUNK_CASE;
+    int* nchunks;     // chunks in use (written by the cell sort)
     double* HIST;
     uint32_t* NB;   // neighbour lists, NB_CAP slots of nb_stride entries
     uint32_t* NBC;  // per-slot list counts
@@ -46,7 +48,7 @@ struct Bufs {
 };
 
 // launchers (stream-ordered; all return the launch error)
-cudaError_t launch_vmax_init(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_vmax_init(const Bufs& B, int par, int lo, int hi, cudaStream_t s);
 cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s);
 cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s);  // hash..reorder + segments
 cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s);
@@ -57,7 +59,7 @@ cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s);
 cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s);
-cudaError_t launch_init_heat0(const Bufs& B, int cur, cudaStream_t s);
+cudaError_t launch_block_heat0(const Bufs& B, int cur, int slot, int at, int n, double* part, cudaStream_t s);
 cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int id_base, double* out,
                                 cudaStream_t s);
 cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_t* counts_by_id,

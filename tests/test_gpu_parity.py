@@ -44,25 +44,26 @@ NEIGHBOR_CASES = [
 
 @pytest.mark.parametrize("name,make", NEIGHBOR_CASES, ids=[c[0] for c in NEIGHBOR_CASES])
 def test_neighbor_sets_bit_exact(sph, oracle, name, make):
-    # step 0: the upload's cell sort, read through the 27-cell loop;
-    # step 1: the per-particle lists the passes of the first advection step
-    # use, built from the same snapshot (positions at t = 0)
+    # after the first advection step: the per-particle lists its passes used
+    # (and, for walls without pair sums, the 27-cell loop), all built from the
+    # snapshot of the initial positions
     case = make()
     f = W.flatten(case)
     R2 = case.support_radius() ** 2
     ref_counts, ref_lst = oracle.neighbors(f["pos"], R2, case.config["periodic_mask"], case.config["extent"])
     ctx = _ctx(sph, case)
-    for steps in (0, 1):
-        ctx.sph_step(steps)
-        counts, lst = ctx.sph_read_neighbors()
-        assert np.array_equal(counts, ref_counts), steps
-        assert np.array_equal(lst, ref_lst), steps
+    with pytest.raises(sph.SphError):
+        ctx.sph_read_neighbors()  # no neighbour search before the first step
+    ctx.sph_step(1)
+    counts, lst = ctx.sph_read_neighbors()
+    assert np.array_equal(counts, ref_counts)
+    assert np.array_equal(lst, ref_lst)
 
 
 @pytest.mark.parametrize("name,make", NEIGHBOR_CASES[:4], ids=[c[0] for c in NEIGHBOR_CASES[:4]])
 def test_cell_order_bit_exact(sph, oracle, name, make):
     case = make()
-    ctx = _ctx(sph, case)
+    ctx = _ctx(sph, case, steps=1)  # the first step sorts the initial positions
     info = ctx.sph_get_info()
     perm = ctx.sph_read_cell_order()
     f = W.flatten(case)
