@@ -85,7 +85,12 @@ void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR, doub
 /* One-sided wall Riemann problem (Eqs. 16-17, 19).  Left state is the fluid
  * (rho_f, U_L = -n.v_f, p_f); right state U_R = -U_L + 2 u_w,
  * P_R = p_f + rho_f g.r_fw, rho_R from the EoS.  Interface velocity from
- * Eq. (12) with these states; pressure from Eq. (19) with (p_w, rho_w) = (P_R, rho_R). */
+ * Eq. (12) with these states.
+ * READING: the interface pressure is Eq. (19)'s density-weighted mean with
+ * (p_w, rho_w) = (P_R, rho_R) plus the limiter term of Eq. (12) on the same
+ * one-sided states, beta = min(3 max(U_L - U_R, 0), c0).  Eq. (19) alone has no
+ * term that resists a particle approaching the wall, and with it fluid
+ * particles drift into walls at edges and corners. */
 void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_dot_rfw,
                       double rho0, double c0, double* UR, double* PR, double* rhoR,
                       double* Ustar, double* pstar) {
@@ -93,7 +98,10 @@ void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_
     *PR = p_f + rho_f * g_dot_rfw;
     *rhoR = rho0 + *PR / (c0 * c0);
     *Ustar = 0.5 * (UL + *UR) + (p_f - *PR) / (c0 * (rho_f + *rhoR));
-    *pstar = (rho_f * *PR + *rhoR * p_f) / (rho_f + *rhoR);
+    double dU = UL - *UR;
+    double beta = 3.0 * (dU > 0.0 ? dU : 0.0);
+    if (beta > c0) beta = c0;
+    *pstar = (rho_f * *PR + *rhoR * p_f) / (rho_f + *rhoR) + rho_f * *rhoR * beta * dU / (rho_f + *rhoR);
 }
 
 /* Eq. (25).  READING: |v|max is floored at u_ref = c0/10 (the anticipated

@@ -719,14 +719,19 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             ay = fmaf(coef, ry, ay);
             az = fmaf(coef, rz, az);
         });
-        vis.template run<PART_WALL>([&](int, float4, float rx, float ry, float rz, float r2) {
+        vis.template run<PART_WALL>([&](int j, float4, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
-            // one-sided wall problem: P_R = p_f + rho_f g.r_fw, r_fw = -r_ij
+            // one-sided wall problem: P_R = p_f + rho_f g.r_fw, r_fw = -r_ij;
+            // U_L - U_R = 2 (U_L - u_w) = -2 n.(v_f - v_w)
+            const float4 nw = __ldg(B.NRM + j);
+            const float4 vw = __ldg(VH + j);
             const float g_rfw = -dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
             const float PR = fmaf(rho_i, g_rfw, p_i);
             const float rhoR = fmaf(PR, C.inv_c02, Mi.rho0);
-            const float pstar = __fdividef(fmaf(rho_i, PR, rhoR * p_i), rho_i + rhoR);
+            const float dUw = -2.f * dot3f(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z);
+            const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
+            const float pstar = __fdividef(fmaf(rho_i, PR, rhoR * p_i) + rho_i * rhoR * beta * dUw, rho_i + rhoR);
             const float coef = C.vol * pstar * dW * inv_r;
             ax = fmaf(coef, rx, ax);
             ay = fmaf(coef, ry, ay);
@@ -757,6 +762,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
     Vout[i] = vi;
     if (kind != KIND_ROT) return;
     // rigid-body particle: pressure force of its fluid neighbours on it
+    const float4 nwi = B.NRM[i];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
@@ -769,7 +775,9 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         const float g_rfw = dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
         const float PR = fmaf(rho_j, g_rfw, p_j);
         const float rhoR = fmaf(PR, C.inv_c02, Mj.rho0);
-        const float pstar = __fdividef(fmaf(rho_j, PR, rhoR * p_j), rho_j + rhoR);
+        const float dUw = -2.f * dot3f(nwi.x, nwi.y, nwi.z, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z);
+        const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
+        const float pstar = __fdividef(fmaf(rho_j, PR, rhoR * p_j) + rho_j * rhoR * beta * dUw, rho_j + rhoR);
         // a_jw = -2 V_w / rho_j p* dW e_jw with e_jw = -r_ij / r; force on wall = -m_j a_jw
         const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * pstar * dW * inv_r;
         fx = fmaf(cf, rx, fx);

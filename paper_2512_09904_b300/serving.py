@@ -217,8 +217,9 @@ def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb
         out["speedup_cases_per_h"] = out["batched"]["cases_per_h"] / out["sequential"]["cases_per_h"]
         ok = [(a, s) for a, s in zip(results, res_s) if a["state"] != sph.BATCH_UNSTABLE]
         out["sequential"]["unstable"] = int(sum(1 for s in res_s if s["state"] == sph.BATCH_UNSTABLE))
-        out["max_abs_diff_torque_avg"] = max(abs(a["torque_avg"] - s["torque_avg"]) for a, s in ok)
-        out["max_abs_diff_heat"] = max(abs(a["heat"] - s["heat"]) for a, s in ok)
+        out["state_mismatches"] = int(sum(1 for a, s in zip(results, res_s) if a["state"] != s["state"]))
+        out["max_abs_diff_torque_avg"] = max((abs(a["torque_avg"] - s["torque_avg"]) for a, s in ok), default=None)
+        out["max_abs_diff_heat"] = max((abs(a["heat"] - s["heat"]) for a, s in ok), default=None)
     out["unstable_requests"] = [dict(i=i, **{k: trace[i][k] for k in ("omega", "depth_frac", "mu", "n_fluid", "dx")})
                                 for i, r in enumerate(results) if r["state"] == sph.BATCH_UNSTABLE]
     return out

@@ -180,6 +180,18 @@ def test_wall_riemann_still_wall(oracle):
     assert s["UR"] == pytest.approx(-0.3, abs=1e-15) and s["Ustar"] == pytest.approx(0.2, abs=1e-15)
 
 
+def test_wall_riemann_impact_gives_water_hammer_pressure(oracle):
+    # a fluid at pressure 0 hitting a still rigid wall at speed U > c0/6 (limiter
+    # saturated): the interface pressure is the Joukowsky value rho c0 U
+    rho, c0, U = 900.0, 10.0, 3.0
+    s = oracle.wall_riemann(rho, U, 0.0, 0.0, 0.0, rho, c0)
+    assert s["pstar"] == pytest.approx(rho * c0 * U, rel=1e-14)
+    assert s["Ustar"] == pytest.approx(0.0, abs=1e-15)  # no penetration
+    # receding from the wall: no dissipation, the mean pressure only
+    s = oracle.wall_riemann(rho, -U, 40.0, 0.0, 0.0, rho, c0)
+    assert s["pstar"] == pytest.approx(40.0, rel=1e-13)
+
+
 def test_wall_riemann_hydrostatic_extrapolation(oracle):
     rho, g, dz, c0 = 870.0, 9.81, 1e-3, 10.0
     s = oracle.wall_riemann(rho, 0.0, 100.0, 0.0, g * dz, rho, c0)
