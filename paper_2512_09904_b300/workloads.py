@@ -6,7 +6,8 @@ arithmetic, so both the CUDA path and the CPU oracle can take its output as
 their common input.
 
 Workload shapes follow the paper: a lubricant bath churned by a rigid spur
-gear (Sec. 4, Tables 5-7: shaft speeds 150-600 rad/s, fill depth, viscosity),
+gear (Sec. 4, Table 5: shaft speeds 150-600 rad/s, fill depth, viscosity;
+Table 6: lubricant and gear properties),
 a still oil tank, a thermal dam break, and the two-material slab of the heat
 conduction validation (Sec. 3.2, Table 3).  No CAD, dataset or measured curve
 of the paper is used: every geometry here is analytic.
@@ -199,7 +200,7 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     """Steel spur gear (pitch radius 50 mm, 24 teeth, face 20 mm, axis along y)
     in a closed sump 0.16x0.06x0.14 m scaled by `scale` per axis, filled to
     `depth_frac` x tip diameter above the gear's lowest point.  Lubricant and
-    gear properties follow the paper's property table (Table 7).
+    gear properties follow the paper's property table (Table 6).
     """
     from scipy import ndimage
 

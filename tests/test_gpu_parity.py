@@ -94,11 +94,14 @@ TOL = 1e-5  # relative tolerance of FP32 pair arithmetic against FP64
 
 
 def _scales(case):
+    # per-field floors of the relative error: lattice spacing, reference
+    # speed, the density excess of the dynamic pressure rho0 U^2 through the
+    # EoS (rho0 (U/c0)^2), and the case's temperature range
     cfg = case.config
     rho0 = max(m["rho0"] for m in case.materials.values())
     Ts = [m["T_init"] for m in case.materials.values()]
     dT = max(max(Ts) - min(Ts), 1.0)
-    return dict(pos=cfg["dx"], vel=cfg["u_ref"], drho_rel=rho0 * cfg["u_ref"] / cfg["c0"], T=dT)
+    return dict(pos=cfg["dx"], vel=cfg["u_ref"], drho_rel=rho0 * (cfg["u_ref"] / cfg["c0"]) ** 2, T=dT)
 
 
 def _compare(sph_ctx, sim, case, fluid_only=True):
