@@ -39,13 +39,15 @@ FLOP_C = dict(ff=40, fw=56)   # pass C
 # is served from L1/L2): pass M reads snapshot 16, state 16, rate 4, viscous
 # acceleration 16, cell 4, position 24 and writes state 16, position 24;
 # pass C reads snapshot 16, state 16, cell 4 and writes state 16, rate 4.
+# Both also read each particle's neighbour list once: 4 B per directed pair.
 BYTES_M, BYTES_C = 120, 56
+BYTES_PER_LIST_ENTRY = 4
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dx", type=float, default=1e-3)
@@ -70,7 +72,7 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler (every 200 ms) around the timed region."""
+    """nvidia-smi sampler (every 100 ms) around the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -81,7 +83,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -230,7 +232,7 @@ def main():
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     peak_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
     achieved = flops / avg_s / 1e12
-    bytes_launch = case.n_fluid * (BYTES_M if dom == "pass_M" else BYTES_C)
+    bytes_launch = case.n_fluid * (BYTES_M if dom == "pass_M" else BYTES_C) + BYTES_PER_LIST_ENTRY * (ff + fw)
     hbm_gbs = bytes_launch / avg_s / 1e9
     total_prof = sum(v[0] for v in prof.values())
     roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
