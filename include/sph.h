@@ -59,6 +59,10 @@ typedef struct {
     int free_surface;            /* 1: re-initialise rho = max(rho, rho0 sumW/sumW0), Eq. (14); 0: Eq. (15) */
     int periodic_mask;           /* bit a set: axis a is periodic */
     int max_substeps;            /* cap on acoustic sub-steps per advection step; 0 = ceil(cfl_ad/cfl_ac (c0/u_ref + 1)) + 2 */
+    int pair_precision;          /* 0: FP32 pair arithmetic, FP64 positions, temperatures and
+                                    reductions (default); 1: FP64 pair arithmetic and particle
+                                    state throughout (the plain FP64 method, for small cases;
+                                    not admissible to a batch).  Other values: SPH_EINVAL. */
 } sph_config;
 
 /* Material table entry (Sec. 2.6 and the paper's property tables). */

@@ -258,6 +258,18 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     AL(B.RN, n);
     AL(B.TORQ, n);
     AL(B.TORQV, n);
+    if (B.fp64) {
+        for (int p = 0; p < 2; ++p) {
+            AL(B.V64[p], n);
+            AL(B.DR64[p], n);
+        }
+        AL(B.VH64, n);
+        AL(B.AV64, n);
+        AL(B.NRM64, n);
+        AL(B.RN64, n);
+        AL(B.TORQ64, n);
+        AL(B.TORQV64, n);
+    }
     AL(B.KEYS, n);
     AL(B.RANK, n);
     AL(B.TMP, n);
@@ -325,6 +337,16 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.inv_c02 = (float)(1.0 / (F.c0 * F.c0));
     C.h64 = h;
     C.c0_64 = F.c0;
+    C.kw64 = alpha;
+    C.kdw64 = -5.0 * alpha / h;
+    C.w0_64 = alpha;
+    C.inv_sigma0_64 = 1.0 / c->sigma0;
+    C.vol64 = F.dx * F.dx * F.dx;
+    C.c02_64 = F.c0 * F.c0;
+    C.inv_c0_64 = 1.0 / F.c0;
+    C.inv_c02_64 = 1.0 / (F.c0 * F.c0);
+    for (int a = 0; a < 3; ++a) C.g64[a] = F.gravity[a];
+    C.fp64 = F.pair_precision == 1 ? 1 : 0;
     C.u_ref = F.u_ref;
     C.cfl_ad = F.cfl_ad;
     C.cfl_ac = F.cfl_ac;
@@ -351,6 +373,12 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.mat[m].cp = (float)M.cp;
         C.mat[m].inv_rho0_cp = (float)(1.0 / (M.rho0 * M.cp));
         C.mat[m].fixed_T = M.fixed_T;
+        C.mat64[m].rho0 = M.rho0;
+        C.mat64[m].mass = M.rho0 * F.dx * F.dx * F.dx;
+        C.mat64[m].mu = M.mu;
+        C.mat64[m].k = M.k;
+        C.mat64[m].cp = M.cp;
+        C.mat64[m].inv_rho0_cp = 1.0 / (M.rho0 * M.cp);
     }
     int nb = 0;
     for (int b = 0; b < MAX_BODY; ++b) {
@@ -462,6 +490,23 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     E_CUDA(E, cudaMemsetAsync(B.TORQ + idb, 0, sizeof(float) * n, s));
     E_CUDA(E, cudaMemsetAsync(B.TORQV + idb, 0, sizeof(float) * n, s));
     E_CUDA(E, cudaMemcpyAsync(B.T64[p] + at, c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    std::vector<double4_32a> v64, rn64;
+    if (B.fp64) {
+        v64.resize(n);
+        rn64.resize(n);
+        for (int64_t i = 0; i < n; ++i) {
+            const bool fl = c->kind[i] == 0;
+            v64[i] = fl ? make_double4_32a(c->vel[3 * i], c->vel[3 * i + 1], c->vel[3 * i + 2],
+                                       c->rho[i] - c->mats[c->mat[i]].rho0)
+                        : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            rn64[i] = make_double4_32a(c->nrm[3 * i], c->nrm[3 * i + 1], c->nrm[3 * i + 2], 0.0);
+        }
+        E_CUDA(E, cudaMemcpyAsync(B.V64[p] + at, v64.data(), sizeof(double4_32a) * n, cudaMemcpyHostToDevice, s));
+        E_CUDA(E, cudaMemsetAsync(B.DR64[p] + at, 0, sizeof(double) * n, s));
+        E_CUDA(E, cudaMemcpyAsync(B.RN64 + idb, rn64.data(), sizeof(double4_32a) * n, cudaMemcpyHostToDevice, s));
+        E_CUDA(E, cudaMemsetAsync(B.TORQ64 + idb, 0, sizeof(double) * n, s));
+        E_CUDA(E, cudaMemsetAsync(B.TORQV64 + idb, 0, sizeof(double) * n, s));
+    }
     E_CUDA(E, cudaMemcpyAsync(B.ID[p] + at, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemcpyAsync(B.TAG[p] + at, tags.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
     // reference heat content and initial max speed from the appended block
@@ -656,7 +701,7 @@ static int engine_kernels_per_step(const Engine& E) {
     int kc = 0;
     for (const HostCase& H : E.cases)
         if (H.used) kc = std::max(kc, H.kcap);
-    return kernels_per_advection_step(kc);
+    return kernels_per_advection_step(kc, E.B.fp64 != 0);
 }
 
 static sph_status read_fields(Engine& E, int slot, int field, void* dst, int64_t n) {
@@ -700,7 +745,7 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     *out = nullptr;
     const double h = cfg->h_over_dx * cfg->dx;
     if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
-        !(cfg->cfl_ac > 0))
+        !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1))
         return SPH_EINVAL;
     sph_ctx* c = new sph_ctx();
     c->cfg = *cfg;
@@ -822,6 +867,7 @@ static sph_status single_engine(sph_ctx* c) {
     E->stream = c->stream;
     E->B.tune_batch = c->tune_batch;
     E->B.uni_fluid = single_fluid_material(c) ? 1 : 0;
+    E->B.fp64 = c->cfg.pair_precision == 1 ? 1 : 0;
     const int64_t nc = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
     sph_status r = engine_alloc(*E, (int64_t)c->kind.size(), 1, nc, 4096);
     int slot = -1;
@@ -945,7 +991,7 @@ sph_status sph_get_info(sph_ctx* c, sph_info* info) {
         info->ncell[a] = c->ncell[a];
         info->cell_width[a] = c->cellw[a];
     }
-    info->graph_launches = kernels_per_advection_step(c->kcap);
+    info->graph_launches = kernels_per_advection_step(c->kcap, c->cfg.pair_precision == 1);
     if (c->started) {
         Engine& E = *c->eng;
         sph_status s = pull_state(E);
@@ -1120,6 +1166,7 @@ sph_status sph_batch_admit(sph_batch* b, sph_ctx* staged, int64_t n_steps, int* 
     Engine& E = b->eng;
     if (staged->started || staged->admitted) return E.fail(SPH_ESTATE, "case was already stepped or admitted");
     if (!single_fluid_material(staged)) return E.fail(SPH_EINVAL, "batched cases need a single fluid material");
+    if (staged->cfg.pair_precision != 0) return E.fail(SPH_EINVAL, "batched cases use FP32 pair arithmetic");
     sph_status s = engine_admit(E, staged, n_steps, slot);
     if (s == SPH_OK) staged->admitted = true;
     return s;

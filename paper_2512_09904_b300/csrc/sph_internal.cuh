@@ -52,6 +52,11 @@ struct MatDev {
     int fixed_T, pad;
 };
 
+// The same material in FP64 (pair arithmetic in FP64).
+struct MatDev64 {
+    double rho0, mass, mu, k, cp, inv_rho0_cp;
+};
+
 struct BodyDev {
     double c[3], axis[3], omega;
     int id_lo, id_hi;   // id range holding the body's particles
@@ -72,8 +77,11 @@ struct CaseDev {
     float g[3];
     double h64, c0_64, u_ref, cfl_ad, cfl_ac, nu_max;
     double T_ref;
-    int free_surface, kcap, n_body, pad;
+    // FP64 copies of the constants above (pair arithmetic in FP64)
+    double kw64, kdw64, w0_64, inv_sigma0_64, vol64, c02_64, inv_c0_64, inv_c02_64, g64[3];
+    int free_surface, kcap, n_body, fp64;
     MatDev mat[MAX_MAT];
+    MatDev64 mat64[MAX_MAT];
     BodyDev body[MAX_BODY];
 };
 
@@ -99,6 +107,7 @@ struct CaseState {
     int init_pending;  // reference heat content still to be taken
     int pad2;
     long long steps_req;  // advection steps requested (0 = unlimited)
+    unsigned long long vmax64_bits;  // FP64 pair arithmetic: bits of the (non-negative) max speed
 };
 
 // ---------------------------------------------------------------- kernel ---

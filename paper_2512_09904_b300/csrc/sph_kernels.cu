@@ -44,9 +44,15 @@ __global__ void k_vmax_init(Bufs B, int par, int lo, int hi) {
         if (i < hi) {
             const uint32_t tag = B.TAG[par][i];
             if (tag_kind(tag) == KIND_FLUID) {
-                const float4 v = B.V[par][i];
                 c = (int)tag_case(tag);
-                bits = __float_as_uint(sqrtf(dot3f(v.x, v.y, v.z, v.x, v.y, v.z)));
+                if (B.fp64) {
+                    const double4_32a v = B.V64[par][i];
+                    const double sp = sqrt(v.x * v.x + v.y * v.y + v.z * v.z);
+                    atomicMax(&B.st[c].vmax64_bits, (unsigned long long)__double_as_longlong(sp));
+                } else {
+                    const float4 v = B.V[par][i];
+                    bits = __float_as_uint(sqrtf(dot3f(v.x, v.y, v.z, v.x, v.y, v.z)));
+                }
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, c);
@@ -61,7 +67,7 @@ __global__ void k_adv_begin(Bufs B) {
     if (c >= B.ncases) return;
     const CaseDev& C = B.cases[c];
     CaseState& S = B.st[c];
-    double vmax = (double)__uint_as_float(S.vmax_bits);
+    double vmax = C.fp64 ? __longlong_as_double((long long)S.vmax64_bits) : (double)__uint_as_float(S.vmax_bits);
     double U = vmax > C.u_ref ? vmax : C.u_ref;
     double a = C.h64 / U;
     if (C.nu_max > 0.0) {
@@ -94,7 +100,7 @@ __global__ void k_sub_begin(Bufs B) {
         S.hdtf = 0.0f;
         return;
     }
-    double vmax = (double)__uint_as_float(S.vmax_bits);
+    double vmax = C.fp64 ? __longlong_as_double((long long)S.vmax64_bits) : (double)__uint_as_float(S.vmax_bits);
     double dt_ac = C.cfl_ac * C.h64 / (C.c0_64 + vmax);
     double rem = S.dt_ad - S.tau;
     int reach = rem <= dt_ac;
@@ -105,6 +111,7 @@ __global__ void k_sub_begin(Bufs B) {
     S.dtf = (float)dt;
     S.hdtf = (float)(0.5 * dt);
     S.vmax_bits = 0u;
+    S.vmax64_bits = 0ull;
 }
 
 // fixed-order block reduction of doubles (blockDim = 256)
@@ -138,8 +145,8 @@ __global__ void __launch_bounds__(256) k_sub_end(Bufs B) {
         if (!Bd.set) continue;
         double acc = 0.0, accv = 0.0;
         for (int id = Bd.id_lo + threadIdx.x; id < Bd.id_hi; id += 256) {
-            acc += (double)B.TORQ[id];
-            if (first) accv += (double)B.TORQV[id];
+            acc += C.fp64 ? B.TORQ64[id] : (double)B.TORQ[id];
+            if (first) accv += C.fp64 ? B.TORQV64[id] : (double)B.TORQV[id];
         }
         double tq = block_sum_256(acc, sh);
         double tqv = first ? block_sum_256(accv, sh) : 0.0;
@@ -324,6 +331,9 @@ __global__ void k_order(int n, const uint32_t* __restrict__ keys, const uint32_t
     }
 }
 
+__device__ void solid_at(const CaseDev& C, const CaseState& S, uint32_t tag, const Bufs& B, int id, double p[3],
+                         double n[3], double v[3]);
+
 // Gather every per-particle field into cell order; build the frozen snapshot.
 __global__ void k_reorder(Bufs B, int par) {
     const int in = par, out = 1 - par;
@@ -361,8 +371,19 @@ __global__ void k_reorder(Bufs B, int par) {
         B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
         B.CELLK[d] = key;
         if (fluid) {
-            B.V[out][d] = B.V[in][s];
-            B.DR[out][d] = B.DR[in][s];
+            if (C.fp64) {
+                B.V64[out][d] = B.V64[in][s];
+                B.DR64[out][d] = B.DR64[in][s];
+            } else {
+                B.V[out][d] = B.V[in][s];
+                B.DR[out][d] = B.DR[in][s];
+            }
+        } else if (C.fp64) {
+            double sp[3], sn[3], sv[3];
+            solid_at(C, B.st[c], tag, B, id, sp, sn, sv);
+            B.V64[out][d] = make_double4_32a(sv[0], sv[1], sv[2], 0.0);
+            B.DR64[out][d] = 0.0;
+            B.NRM64[d] = make_double4_32a(sn[0], sn[1], sn[2], 0.0);
         } else {
             float4 n0 = B.RN[id];
             float vw[3] = {0.f, 0.f, 0.f};
@@ -909,8 +930,8 @@ __global__ void k_T_update(Bufs B, int par) {
         const uint32_t tag = B.TAG[cur][i];
         const CaseState& S = B.st[tag_case(tag)];
         if (!S.running || !S.alive) continue;
-        const float r = B.AV[i].w;
-        if (r != 0.0f) B.T64[cur][i] += S.tau * (double)r;
+        const double r = B.cases[tag_case(tag)].fp64 ? B.AV64[i].w : (double)B.AV[i].w;
+        if (r != 0.0) B.T64[cur][i] += S.tau * r;
     }
 }
 
@@ -983,28 +1004,34 @@ __global__ void k_adv_end_cases(Bufs B) {
         h[4] = S.mean_T;
         h[5] = S.dt_ad;
         h[6] = (double)S.nsub;
-        h[7] = (double)__uint_as_float(S.vmax_bits);
+        h[7] = B.cases[c].fp64 ? __longlong_as_double((long long)S.vmax64_bits) : (double)__uint_as_float(S.vmax_bits);
     }
     if (S.steps_req > 0 && S.adv_steps >= S.steps_req) S.running = 0;
 }
 
 // ------------------------------------------------------------- readback ---
-// Solid particle at the case's current time: position, normal and velocity
-// from its reference geometry (rigid rotation by omega t about (c, axis)).
-__device__ void solid_now(const CaseDev& C, const CaseState& S, uint32_t tag, const Bufs& B, int id, double p[3],
-                          double n[3], double v[3]) {
+// Solid particle rotated by (cos, sin) of its body's angle: position, normal
+// and velocity from its reference geometry (rigid rotation about (c, axis),
+// Rodrigues' formula in FP64).
+__device__ void solid_rotated(const CaseDev& C, uint32_t tag, const Bufs& B, int id, double cs, double sn,
+                              double p[3], double n[3], double v[3]) {
     p[0] = B.RP[0][id];
     p[1] = B.RP[1][id];
     p[2] = B.RP[2][id];
-    const float4 n0 = B.RN[id];
-    n[0] = n0.x;
-    n[1] = n0.y;
-    n[2] = n0.z;
+    if (C.fp64) {
+        const double4_32a n0 = B.RN64[id];
+        n[0] = n0.x;
+        n[1] = n0.y;
+        n[2] = n0.z;
+    } else {
+        const float4 n0 = B.RN[id];
+        n[0] = n0.x;
+        n[1] = n0.y;
+        n[2] = n0.z;
+    }
     v[0] = v[1] = v[2] = 0.0;
     if (tag_kind(tag) != KIND_ROT) return;
     const BodyDev& Bd = C.body[tag_body(tag)];
-    double sn, cs;
-    sincos(Bd.omega * S.t, &sn, &cs);
     const double* a = Bd.axis;
     double d[3] = {p[0] - Bd.c[0], p[1] - Bd.c[1], p[2] - Bd.c[2]};
     double rd[3], rn[3];
@@ -1024,6 +1051,21 @@ __device__ void solid_now(const CaseDev& C, const CaseState& S, uint32_t tag, co
     v[2] = Bd.omega * (a[0] * rd[1] - a[1] * rd[0]);
 }
 
+// ... at the case's current time
+__device__ void solid_now(const CaseDev& C, const CaseState& S, uint32_t tag, const Bufs& B, int id, double p[3],
+                          double n[3], double v[3]) {
+    double sn = 0.0, cs = 1.0;
+    if (tag_kind(tag) == KIND_ROT) sincos(C.body[tag_body(tag)].omega * S.t, &sn, &cs);
+    solid_rotated(C, tag, B, id, cs, sn, p, n, v);
+}
+
+// ... at the angle of the current advection step
+__device__ void solid_at(const CaseDev& C, const CaseState& S, uint32_t tag, const Bufs& B, int id, double p[3],
+                         double n[3], double v[3]) {
+    const int b = tag_body(tag);
+    solid_rotated(C, tag, B, id, S.cs[b], S.sn[b], p, n, v);
+}
+
 __global__ void k_gather_field(Bufs B, int par, int field, int cs, int id_base, double* out) {
     const int cur = 1 - par;
     GSTRIDE_LOOP(i, B.n) {
@@ -1033,8 +1075,10 @@ __global__ void k_gather_field(Bufs B, int par, int field, int cs, int id_base, 
         const int id = gid - id_base;
         const CaseDev& C = B.cases[tag_case(tag)];
         const bool fluid = tag_kind(tag) == KIND_FLUID;
-        const float4 v = B.V[cur][i];
-        const MatDev& M = C.mat[tag_mat(tag)];
+        const float4 vf = B.V[cur][i];
+        const double4_32a v = C.fp64 ? B.V64[cur][i] : make_double4_32a(vf.x, vf.y, vf.z, vf.w);
+        const double rho0 = C.fp64 ? C.mat64[tag_mat(tag)].rho0 : (double)C.mat[tag_mat(tag)].rho0;
+        const double c02 = C.fp64 ? C.c02_64 : (double)C.c02;
         double sp[3], sn[3], sv[3];
         if (!fluid && (field == 0 || field == 1 || field == 9)) solid_now(C, B.st[cs], tag, B, gid, sp, sn, sv);
         switch (field) {
@@ -1044,22 +1088,23 @@ __global__ void k_gather_field(Bufs B, int par, int field, int cs, int id_base, 
             out[3 * (size_t)id + 2] = fluid ? B.X[2][i] : sp[2];
             break;
         case 1:
-            out[3 * (size_t)id + 0] = fluid ? (double)v.x : sv[0];
-            out[3 * (size_t)id + 1] = fluid ? (double)v.y : sv[1];
-            out[3 * (size_t)id + 2] = fluid ? (double)v.z : sv[2];
+            out[3 * (size_t)id + 0] = fluid ? v.x : sv[0];
+            out[3 * (size_t)id + 1] = fluid ? v.y : sv[1];
+            out[3 * (size_t)id + 2] = fluid ? v.z : sv[2];
             break;
-        case 2: out[id] = fluid ? (double)M.rho0 + (double)v.w : (double)M.rho0; break;
-        case 3: out[id] = fluid ? (double)C.c02 * (double)v.w : 0.0; break;
+        case 2: out[id] = fluid ? rho0 + v.w : rho0; break;
+        case 3: out[id] = fluid ? c02 * v.w : 0.0; break;
         case 4: out[id] = B.T64[cur][i]; break;
-        case 5: out[id] = fluid ? (double)B.DR[cur][i] : 0.0; break;
+        case 5: out[id] = fluid ? (C.fp64 ? B.DR64[cur][i] : (double)B.DR[cur][i]) : 0.0; break;
         case 6: {
-            const float4 a = B.AV[i];
+            const float4 af = B.AV[i];
+            const double4_32a a = C.fp64 ? B.AV64[i] : make_double4_32a(af.x, af.y, af.z, af.w);
             out[3 * (size_t)id + 0] = fluid ? a.x : 0.0;
             out[3 * (size_t)id + 1] = fluid ? a.y : 0.0;
             out[3 * (size_t)id + 2] = fluid ? a.z : 0.0;
             break;
         }
-        case 7: out[id] = B.AV[i].w; break;
+        case 7: out[id] = C.fp64 ? B.AV64[i].w : (double)B.AV[i].w; break;
         case 9:
             out[3 * (size_t)id + 0] = fluid ? 0.0 : sn[0];
             out[3 * (size_t)id + 1] = fluid ? 0.0 : sn[1];
@@ -1197,6 +1242,7 @@ cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s) {
 }
 
 cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
+    if (B.fp64) return launch_passD64(B, par, s);
     k_passD<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
     return cudaGetLastError();
 }
@@ -1212,6 +1258,7 @@ static const int kOvfGrid = 32;
     }
 
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
+    if (B.fp64) return launch_passVT64(B, par, s);
     if (B.uni_fluid) {
         DISPATCH_BATCH(k_passVT, true, grid_1to1(B.n, 128), 128, s, B, par);
         k_passVT_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
@@ -1228,6 +1275,7 @@ cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s) {
 }
 
 cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
+    if (B.fp64) return launch_passM64(B, par, first, s);
     k_halfkick<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
     const int f = first ? 1 : 0;
     if (B.uni_fluid) {
@@ -1241,6 +1289,7 @@ cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
 }
 
 cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
+    if (B.fp64) return launch_passC64(B, par, s);
     if (B.uni_fluid) {
         DISPATCH_BATCH(k_passC, true, grid_1to1(B.n, 128), 128, s, B, par);
         k_passC_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
@@ -1308,11 +1357,11 @@ cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int kernels_per_advection_step(int kcap) {
+int kernels_per_advection_step(int kcap, bool fp64) {
     // adv_begin + sort(hash, 3 scan, scatter, order, reorder, segments)
     // + D + VT(+ovf) + kcap * (sub_begin, halfkick, M(+ovf), C(+ovf), sub_end)
-    // + T_update + 2 reduce + adv_end
-    return 1 + 8 + 3 + 7 * kcap + 4;
+    // + T_update + 2 reduce + adv_end; the FP64 passes have no overflow kernels
+    return fp64 ? 1 + 8 + 2 + 5 * kcap + 4 : 1 + 8 + 3 + 7 * kcap + 4;
 }
 
 cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int id_base, double* out,

@@ -45,6 +45,17 @@ struct Bufs {
     float4* VH;     // (v, half-kicked drho) input of pass M
     int uni_fluid;  // every case has a single fluid material
     int tune_batch; // list entries loaded together per thread in the pair passes (1, 2, 4, 8)
+    // FP64 pair arithmetic (fp64 = 1): particle state in FP64 beside the
+    // FP32 arrays above, which then only carry tags, snapshot offsets and lists
+    int fp64;
+    double4_32a* V64[2];  // (vx, vy, vz, rho - rho0)
+    double* DR64[2];
+    double4_32a* VH64;
+    double4_32a* AV64;    // (viscous acceleration, dT/dt)
+    double4_32a* NRM64;   // wall normals at the advection step, slot order
+    double4_32a* RN64;    // reference normals, by id
+    double* TORQ64;   // per-id pressure torque
+    double* TORQV64;  // per-id viscous torque
 };
 
 // launchers (stream-ordered; all return the launch error)
@@ -64,8 +75,14 @@ cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int i
                                 cudaStream_t s);
 cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_t* counts_by_id,
                              const int64_t* start_by_id, int32_t* list, cudaStream_t s);
-int kernels_per_advection_step(int kcap);
+int kernels_per_advection_step(int kcap, bool fp64);
 cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
+
+// FP64 pair passes (sph_kernels64.cu)
+cudaError_t launch_passD64(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_passVT64(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_passM64(const Bufs& B, int par, bool first, cudaStream_t s);
+cudaError_t launch_passC64(const Bufs& B, int par, cudaStream_t s);
 
 // stateless cell sort (positions AoS)
 cudaError_t launch_cell_sort(const double* pos, int n, const double origin[3], const double cellw[3],

@@ -66,6 +66,11 @@ def test_create_validates_config(sphlib):
     bad = dict(cfg, periodic_mask=1, extent=[2.5 * R, cfg["extent"][1], cfg["extent"][2]])
     with pytest.raises(sphlib.SphError):
         sphlib.Context(bad, stream=0)
+    # pair precision: 0 (FP32 pairs) or 1 (FP64 throughout)
+    sphlib.Context(dict(cfg, pair_precision=1), stream=0).close()
+    with pytest.raises(sphlib.SphError) as e:
+        sphlib.Context(dict(cfg, pair_precision=2), stream=0)
+    assert e.value.status == sphlib.SPH_EINVAL
 
 
 def test_add_validates_arguments(sphlib):

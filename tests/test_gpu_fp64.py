@@ -1,0 +1,143 @@
+"""The plain FP64 method (sph_config.pair_precision = 1) against the FP64 oracle.
+
+Same neighbour lists as the FP32 path; pair geometry, pair sums and particle
+state in FP64.  What remains between the two is the order of the pair sums
+(list order on the GPU, ascending id in the oracle), a few ulp per sum, so the
+field tolerance is 1e-12 of the field scale instead of the FP32 path's 1e-5.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_09904_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2512_09904_b300 import build
+    build.build()
+    from paper_2512_09904_b300 import sph as S
+    return S
+
+
+def _fp64(case):
+    case.config = dict(case.config, pair_precision=1)
+    return case
+
+
+def _scales(case):
+    cfg = case.config
+    rho0 = max(m["rho0"] for m in case.materials.values())
+    Ts = [m["T_init"] for m in case.materials.values()]
+    return dict(pos=cfg["dx"], vel=cfg["u_ref"], drho_rel=rho0 * (cfg["u_ref"] / cfg["c0"]) ** 2,
+                T=max(max(Ts) - min(Ts), 1.0))
+
+
+def _errors(ctx, sim, case):
+    f = W.flatten(case)
+    sel = f["kind"] == 0
+    rho0 = np.array([case.materials[m]["rho0"] for m in f["mat"]])
+    sc = _scales(case)
+    out = {}
+    for k in ("pos", "vel", "T"):
+        g, r = ctx.sph_read_fields(k)[sel], sim.field(k)[sel]
+        out[k] = float(np.max(np.abs(g - r) / np.maximum(np.abs(r), sc[k])))
+    g = ctx.sph_read_fields("rho")[sel] - rho0[sel]
+    r = sim.field("rho")[sel] - rho0[sel]
+    out["drho_rel"] = float(np.max(np.abs(g - r) / np.maximum(np.abs(r), sc["drho_rel"])))
+    return out
+
+
+CASES = [
+    ("still_tank_small", lambda: W.still_tank(nx=12, ny=12, nz=8, wall_h=12), 3),
+    ("periodic_box", lambda: W.periodic_box(n=12), 3),
+    ("rotating_cylinder", lambda: W.rotating_cylinder(), 3),
+    ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
+]
+
+
+@pytest.mark.parametrize("name,make,steps", CASES, ids=[c[0] for c in CASES])
+def test_fp64_field_parity(sph, oracle, name, make, steps):
+    case = _fp64(make())
+    ctx = sph.from_case(case, stream=0)
+    sim = oracle.OracleSim(case)
+    for k in range(steps):
+        ctx.sph_step(1)
+        sim.step(1)
+        gi, oi = ctx.sph_get_info(), sim.time()
+        assert gi["last_nsub"] == oi["nsub"]
+        assert gi["t"] == pytest.approx(oi["t"], rel=1e-12)
+        err = _errors(ctx, sim, case)
+        print(name, k + 1, err)
+        for f, e in err.items():
+            assert e <= TOL64, (name, k + 1, f, e)
+    ctx.close()
+
+
+def test_fp64_torque_heat(sph, oracle):
+    case = _fp64(W.rotating_cylinder())
+    ctx = sph.from_case(case, stream=0)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(20)
+    sim.step(20)
+    g, r = ctx.sph_read_torque_heat(0), sim.torque_heat(0)
+    print(g, r)
+    assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=1e-9)
+    # heat = sum(m cp T) - its initial value: a small difference of two large
+    # fixed-order sums, so its error is bounded against the sum itself
+    f = W.flatten(case)
+    fl = f["kind"] == 0
+    m = np.array([case.materials[k]["rho0"] * case.config["dx"] ** 3 * case.materials[k]["cp"] for k in f["mat"]])
+    total = float((m[fl] * ctx.sph_read_fields("T")[fl]).sum())
+    assert abs(g["heat"] - r["heat"]) <= 1e-11 * total
+    assert g["mean_T"] == pytest.approx(r["mean_T"], rel=1e-12)
+    ctx.close()
+
+
+def test_fp64_and_fp32_paths_agree(sph):
+    # the FP32 fast path stays within its tolerance of the FP64 path
+    case = W.rotating_cylinder()
+    c32 = sph.from_case(case, stream=0)
+    c64 = sph.from_case(_fp64(W.rotating_cylinder()), stream=0)
+    c32.sph_step(3)
+    c64.sph_step(3)
+    sel = W.flatten(case)["kind"] == 0
+    for k, s in (("pos", case.config["dx"]), ("vel", case.config["u_ref"])):
+        a, b = c32.sph_read_fields(k)[sel], c64.sph_read_fields(k)[sel]
+        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), s)) <= 3e-5, k
+    c32.close()
+    c64.close()
+
+
+def test_fp64_case_is_not_admitted_to_a_batch(sph):
+    case = _fp64(W.still_tank(nx=6, ny=6, nz=4, wall_h=6))
+    b = sph.Batch(10000, 2, 10000, history_steps=4)
+    with pytest.raises(sph.SphError) as e:
+        b.admit(case, 2)
+    assert e.value.status == sph.SPH_EINVAL
+    b.close()
+
+
+@pytest.mark.slow
+def test_fp64_still_tank_full_200_steps(sph, oracle):
+    # the full still-tank case (32 x 32 x 16 oil lattice in a 3-layer steel
+    # tank, bottom held at 80 C), 200 advection steps in FP64 on both sides
+    case = _fp64(W.still_tank())
+    ctx = sph.from_case(case, stream=0)
+    sim = oracle.OracleSim(case)
+    for _ in range(4):
+        ctx.sph_step(50)
+        sim.step(50)
+        assert ctx.sph_get_info()["adv_steps"] == sim.time()["adv_steps"]
+    err = _errors(ctx, sim, case)
+    print("still_tank 200", err, ctx.sph_get_info()["t"], sim.time()["t"])
+    assert ctx.sph_get_info()["t"] == pytest.approx(sim.time()["t"], rel=1e-12)
+    for f, e in err.items():
+        assert e <= 1e-11, (f, e)
+    ctx.close()
