@@ -196,16 +196,18 @@ def _gear_inside(px, pz, r_p, z_teeth, pa):
 
 def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, jitter=0.01,
               layers=3, gear_layers=3, rho0=968.1, k_oil=0.15, cp_oil=2000.0, T_oil=298.15,
-              T_gear=318.15, g=9.81):
+              T_gear=318.15, g=9.81, gear=None):
     """Steel spur gear (pitch radius 50 mm, 24 teeth, face 20 mm, axis along y)
     in a closed sump 0.16x0.06x0.14 m scaled by `scale` per axis, filled to
     `depth_frac` x tip diameter above the gear's lowest point.  Lubricant and
-    gear properties follow the paper's property table (Table 6).
+    gear properties follow the paper's property table (Table 6).  `gear`
+    overrides r_pitch / teeth / face (a geometrically similar smaller case).
     """
     from scipy import ndimage
 
     rng = np.random.default_rng(seed)
-    r_p, z_t, b = GEAR["r_pitch"], GEAR["teeth"], GEAR["face"]
+    G = dict(GEAR, **(gear or {}))
+    r_p, z_t, b = G["r_pitch"], G["teeth"], G["face"]
     m = 2.0 * r_p / z_t
     r_a = r_p + m
     L = np.array([0.16, 0.06, 0.14]) * scale
@@ -222,7 +224,7 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     shape = tuple(hi - lo)
     gi = _grid(tuple(lo), tuple(hi))
     gp = (gi + 0.5) * dx
-    inside = _gear_inside(gp[:, 0] - c[0], gp[:, 2] - c[2], r_p, z_t, GEAR["pressure_angle_deg"])
+    inside = _gear_inside(gp[:, 0] - c[0], gp[:, 2] - c[2], r_p, z_t, G["pressure_angle_deg"])
     inside &= np.abs(gp[:, 1] - c[1]) <= b / 2
     vol = inside.reshape(shape[2], shape[1], shape[0])  # (k, j, i)
     depth_in = ndimage.distance_transform_edt(vol)
@@ -239,7 +241,7 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     fpos0 = (fidx + 0.5) * dx
     fpos0 = fpos0[fpos0[:, 2] < z_fill]
     rel = fpos0 - c
-    in_gear = _gear_inside(rel[:, 0], rel[:, 2], r_p, z_t, GEAR["pressure_angle_deg"]) & (np.abs(rel[:, 1]) <= b / 2)
+    in_gear = _gear_inside(rel[:, 0], rel[:, 2], r_p, z_t, G["pressure_angle_deg"]) & (np.abs(rel[:, 1]) <= b / 2)
     fpos0 = fpos0[~in_gear]
     fpos = fpos0 + _jitter(rng, len(fpos0), dx, jitter)
     u_tip = omega * r_a
@@ -269,6 +271,14 @@ def gear_bath_dx_for(n_fluid_target, depth_frac=0.5, scale=1.5):
     z_fill = (L[2] / 2 - r_a) + depth_frac * 2.0 * r_a
     v = L[0] * L[1] * z_fill - math.pi * r_p * r_p * b * min(max(depth_frac, 0.0), 1.0)
     return float((v / n_fluid_target) ** (1.0 / 3.0))
+
+
+def mini_gear_bath(omega=300.0, dx=1.5e-3, depth_frac=0.5, mu=0.1, seed=9):
+    """The gear bath shrunk by 5 (pitch radius 10 mm, 24 teeth of module
+    0.83 mm, face 4 mm, sump 48x18x42 mm) at a coarse lattice: a case small
+    enough for the O(N^2) oracle over 1000 advection steps."""
+    return gear_bath(dx=dx, omega=omega, depth_frac=depth_frac, mu=mu, scale=0.3, seed=seed,
+                     gear=dict(r_pitch=GEAR["r_pitch"] / 5, face=GEAR["face"] / 5))
 
 
 # --------------------------------------------------------------------------
