@@ -35,12 +35,20 @@ UNIT = "oil particle-substeps/s"
 # kernels (distance, kernel derivative, Riemann state, accumulation; FMA = 2):
 FLOP_M = dict(ff=53, fw=43)   # pass M: fluid-fluid, fluid-wall
 FLOP_C = dict(ff=40, fw=56)   # pass C
+FLOP_VT = dict(ff=29, fw=25)  # pass VT (viscous + conduction terms)
+# pass D: 8 per candidate (3 differences, r^2 with 1 mul + 2 FMA) and 11 per
+# partner found (sqrt, q, (1 - q/2)^4 (1 + 2q), sum)
+FLOP_D = dict(cand=8, pair=11)
 # HBM bytes per oil particle per launch (own state in and out; neighbour data
 # is served from L1/L2): pass M reads snapshot 16, state 16, rate 4, viscous
 # acceleration 16, cell 4, position 24 and writes state 16, position 24;
 # pass C reads snapshot 16, state 16, cell 4 and writes state 16, rate 4.
 # Both also read each particle's neighbour list once: 4 B per directed pair.
 BYTES_M, BYTES_C = 120, 56
+# pass VT reads snapshot 16, state 16, temperature 4, cell 4 and writes the
+# held accelerations 16; pass D reads snapshot 16, cell 4, FP64 position 24,
+# state 16 and writes state 16, list count 4.
+BYTES_VT, BYTES_D = 56, 80
 BYTES_PER_LIST_ENTRY = 4
 
 
@@ -55,6 +63,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--list-batch", type=int, default=0, help="override the list-batch kernel variant")
+    ap.add_argument("--tpp", type=int, default=0, help="override threads per particle of the pair passes")
+    ap.add_argument("--block", type=int, default=0, help="override the pair-pass block size")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner (default variants)")
     return ap.parse_args()
 
 
@@ -181,9 +192,21 @@ def main():
     case = workload(args.dx, args.omega)
     stream = torch.cuda.current_stream()
     ctx = sph.from_case(case, stream=stream.cuda_stream)
-    if args.list_batch:
-        ctx.sph_set_tuning("list_batch", args.list_batch)
+    tune = None
+    if not args.no_autotune:
+        # pick the pair-pass variant on a scratch copy of the workload, so the
+        # timed case starts from the same state either way
+        tctx = sph.from_case(case, stream=stream.cuda_stream)
+        tctx.sph_step(1)
+        tune = tctx.sph_autotune(steps_per_trial=2)
+        tctx.close()
+        del tctx
+        for key in ("list_batch", "tpp", "block"):
+            ctx.sph_set_tuning(key, tune[key])
     ctx.sph_step(1)                     # upload + first advection step
+    for key, val in (("list_batch", args.list_batch), ("tpp", args.tpp), ("block", args.block)):
+        if val:
+            ctx.sph_set_tuning(key, val)
     ctx.sph_profile(True)               # event records between kernel groups
     ctx.sph_step(max(args.warmup, 3) - 1)
     info0 = ctx.sph_get_info()
@@ -208,6 +231,8 @@ def main():
     substeps = info1["substeps"] - info0["substeps"]
     units = case.n_fluid * substeps
     ff, fw = ctx.sph_pair_stats()
+    search = ctx.sph_search_stats()
+    ctx_tuning = {k: ctx.sph_get_tuning(k) for k in ("list_batch", "tpp", "block")}
     th = ctx.sph_read_torque_heat(0)
     ctx.close()
     del ctx
@@ -224,22 +249,30 @@ def main():
 
     # roofline of the dominant kernel (largest share of device time)
     peaks, src = measured_peaks()
-    dom = max(("pass_M", "pass_C"), key=lambda k: prof[k][0])
+    dom = max(("pass_D", "pass_VT", "pass_M", "pass_C"), key=lambda k: prof[k][0])
     dms, dcnt = prof[dom]
     avg_s = dms / max(dcnt, 1) * 1e-3
-    fl = FLOP_M if dom == "pass_M" else FLOP_C
-    flops = ff * fl["ff"] + fw * fl["fw"]
+    if dom == "pass_D":
+        flops = search["candidates"] * FLOP_D["cand"] + search["partners"] * FLOP_D["pair"]
+    else:
+        fl = dict(pass_M=FLOP_M, pass_C=FLOP_C, pass_VT=FLOP_VT)[dom]
+        flops = ff * fl["ff"] + fw * fl["fw"]
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     peak_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
     achieved = flops / avg_s / 1e12
-    bytes_launch = case.n_fluid * (BYTES_M if dom == "pass_M" else BYTES_C) + BYTES_PER_LIST_ENTRY * (ff + fw)
+    # HBM bytes per launch: own state in and out plus one pass over the lists
+    # (pass D writes them; VT reads them like M and C)
+    per_particle = dict(pass_M=BYTES_M, pass_C=BYTES_C, pass_VT=BYTES_VT, pass_D=BYTES_D)[dom]
+    n_part = search["searched"] if dom in ("pass_D", "pass_VT") else case.n_fluid
+    n_list = search["partners"] if dom in ("pass_D", "pass_VT") else ff + fw
+    bytes_launch = n_part * per_particle + BYTES_PER_LIST_ENTRY * n_list
     hbm_gbs = bytes_launch / avg_s / 1e9
     total_prof = sum(v[0] for v in prof.values())
     roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max from {src} peaks file)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
-                "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw,
+                "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
                 "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": hbm_gbs / peaks.get("hbm_gbs", 6505.9), "bytes_per_launch": bytes_launch},
                 "share": {k: round(v[0] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
@@ -252,7 +285,9 @@ def main():
                       "pair_arith": "f32", "integration_and_reductions": "f64",
                       "l2": "inputs larger than L2 (~0.7 GB resident state)",
                       "parallelism": f"replicas x{world}", "torque_avg_Nm": th["torque_avg"],
-                      "heat_J": th["heat"]},
+                      "heat_J": th["heat"],
+                      "pair_variant": {k: ctx_tuning[k] for k in ("list_batch", "tpp", "block")},
+                      "autotune": tune},
            "roofline": roofline,
            "gpu_launches": int(info1["graph_launches"]) * args.steps,
            "clocks": clk}

@@ -179,16 +179,47 @@ sph_status sph_get_info(sph_ctx* ctx, sph_info* info);
  * Errors: SPH_ESTATE (no step yet), SPH_ECUDA. */
 sph_status sph_pair_stats(sph_ctx* ctx, int64_t* fluid_fluid, int64_t* fluid_wall);
 
-/* Kernel-variant knobs (performance only: results do not depend on them). */
+/* Work of the current snapshot's neighbour search (pass D): particles
+ * searched, candidates tested (sum of their 27-cell populations) and
+ * partners found.  Used to turn pass-D times into search rates.
+ * Errors: SPH_ESTATE (no step yet), SPH_EINVAL (NULL output), SPH_ECUDA. */
+sph_status sph_search_stats(sph_ctx* ctx, int64_t* searched, int64_t* candidates, int64_t* partners);
+
+/* Kernel-variant knobs of the pair passes (performance only).  List batch
+ * and block size leave every result bitwise unchanged; two threads per
+ * particle add each particle's pair terms in two interleaved halves, which
+ * changes FP32 rounding only. */
 enum {
-    SPH_TUNE_LIST_BATCH = 0  /* neighbour-list entries each thread loads together in the
-                                pair passes: 1, 2, 4 or 8 (default) */
+    SPH_TUNE_LIST_BATCH = 0, /* neighbour-list entries each thread loads together: 1, 2, 4 or 8 (default) */
+    SPH_TUNE_TPP = 1,        /* threads per particle in passes VT, M, C: 1 (default; 32 particles
+                                per warp) or 2 (16 particles per warp) */
+    SPH_TUNE_BLOCK = 2       /* threads per block of the pair passes: 64, 128 (default) or 256 */
 };
 
 /* Select a kernel variant; re-captures the step graph if the context has
  * started.  Errors: SPH_EINVAL (unknown key or value), SPH_ECUDA. */
 sph_status sph_set_tuning(sph_ctx* ctx, int key, int value);
 sph_status sph_get_tuning(sph_ctx* ctx, int key, int* value);
+
+/* Autotuner result: the variant now in force and the model time it won on,
+ * ms per advection step = (D + VT) per step + substeps_ref x (M + C) per
+ * sub-step, measured with device events. */
+typedef struct {
+    int list_batch, tpp, block; /* chosen variant (set on return) */
+    double ms_step_start;       /* model time of the variant in force before tuning */
+    double ms_step_chosen;      /* model time of the chosen variant */
+    double substeps_ref;        /* sub-steps per advection step of the first trial */
+    int trials;                 /* variants timed */
+    int64_t steps;              /* advection steps advanced while tuning */
+} sph_tune_report;
+
+/* Time the pair-pass variants on this context's own workload and keep the
+ * fastest (coordinate descent: list batch, then threads per particle, then
+ * block size; 1 + steps_per_trial real advection steps per variant, the
+ * simulation advances by report->steps).  report: host, may be NULL.
+ * Errors: SPH_EINVAL (steps_per_trial < 1), SPH_ESTATE (no particles, or
+ * the case has finished), SPH_EUNSTABLE, SPH_ECUDA. */
+sph_status sph_autotune(sph_ctx* ctx, int steps_per_trial, sph_tune_report* report);
 
 /* Device-time profile of the advection step, by kernel group. */
 enum {
@@ -294,6 +325,9 @@ sph_status sph_batch_retire(sph_batch* b, int slot);
 sph_status sph_batch_info(sph_batch* b, int64_t* n_particles, int* n_cases, int* kernels_per_step);
 
 sph_status sph_batch_set_tuning(sph_batch* b, int key, int value);
+
+/* sph_autotune for the resident cases of a batch (one variant for all). */
+sph_status sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tune_report* report);
 sph_status sph_batch_profile(sph_batch* b, int enable);
 sph_status sph_batch_profile_read(sph_batch* b, double* ms, int64_t* launches, int reset);
 

@@ -183,7 +183,7 @@ struct sph_ctx {
     double cellw[3]{};
     double sigma0 = 0.0;
     int kcap = 0;
-    int tune_batch = 8;
+    int tune_batch = 8, tune_tpp = 1, tune_block = 128;
     bool started = false;   // stepped as a single case
     bool admitted = false;  // handed to a batch
     Engine* eng = nullptr;
@@ -293,6 +293,8 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
                       cudaGetErrorString(e));
     B.nb_stride = (int)n;
     if (B.tune_batch == 0) B.tune_batch = 8;
+    if (B.tune_tpp == 0) B.tune_tpp = 1;
+    if (B.tune_block == 0) B.tune_block = 128;
     E.cases.assign(c_cap, HostCase{});
     E.st_h.assign(c_cap, CaseState{});
     E.ids.reset(n_cap);
@@ -866,6 +868,8 @@ static sph_status single_engine(sph_ctx* c) {
     Engine* E = new Engine();
     E->stream = c->stream;
     E->B.tune_batch = c->tune_batch;
+    E->B.tune_tpp = c->tune_tpp;
+    E->B.tune_block = c->tune_block;
     E->B.uni_fluid = single_fluid_material(c) ? 1 : 0;
     E->B.fp64 = c->cfg.pair_precision == 1 ? 1 : 0;
     const int64_t nc = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
@@ -1026,19 +1030,50 @@ sph_status sph_pair_stats(sph_ctx* c, int64_t* fluid_fluid, int64_t* fluid_wall)
     return SPH_OK;
 }
 
-sph_status sph_set_tuning(sph_ctx* c, int key, int value) {
-    if (!c) return SPH_EINVAL;
+sph_status sph_search_stats(sph_ctx* c, int64_t* searched, int64_t* candidates, int64_t* partners) {
+    STARTED_OR_STATE(c);
+    if (c->eng->graph_steps == 0) return fail(c, SPH_ESTATE, "no neighbour search before the first step");
+    if (!searched || !candidates || !partners) return SPH_EINVAL;
+    Engine& E = *c->eng;
+    unsigned long long* d = nullptr;
+    unsigned long long h[3] = {0, 0, 0};
+    if (cudaMalloc(&d, sizeof h) != cudaSuccess) return fail(c, SPH_ENOMEM, "search stats");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, E.stream);
+    if (e == cudaSuccess) e = launch_search_stats(E.B, d, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(c, SPH_ECUDA, "search stats: %s", cudaGetErrorString(e));
+    *searched = (int64_t)h[0];
+    *candidates = (int64_t)h[1];
+    *partners = (int64_t)h[2];
+    return SPH_OK;
+}
+
+// Kernel-variant knobs: validation and the engine field each one sets.
+static const char* tuning_check(int key, int value) {
     switch (key) {
     case SPH_TUNE_LIST_BATCH:
-        if (value != 1 && value != 2 && value != 4 && value != 8)
-            return fail(c, SPH_EINVAL, "list batch must be 1, 2, 4 or 8");
-        c->tune_batch = value;
-        break;
-    default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
+        return (value == 1 || value == 2 || value == 4 || value == 8) ? nullptr : "list batch must be 1, 2, 4 or 8";
+    case SPH_TUNE_TPP: return (value == 1 || value == 2) ? nullptr : "threads per particle must be 1 or 2";
+    case SPH_TUNE_BLOCK:
+        return (value == 64 || value == 128 || value == 256) ? nullptr : "block size must be 64, 128 or 256";
+    default: return "unknown tuning key";
     }
+}
+
+static int* tuning_field(Bufs& B, int key) {
+    return key == SPH_TUNE_LIST_BATCH ? &B.tune_batch : key == SPH_TUNE_TPP ? &B.tune_tpp : &B.tune_block;
+}
+
+sph_status sph_set_tuning(sph_ctx* c, int key, int value) {
+    if (!c) return SPH_EINVAL;
+    if (const char* m = tuning_check(key, value)) return fail(c, SPH_EINVAL, "%s (key %d, value %d)", m, key, value);
+    int* f = key == SPH_TUNE_LIST_BATCH ? &c->tune_batch : key == SPH_TUNE_TPP ? &c->tune_tpp : &c->tune_block;
+    *f = value;
     if (!c->started) return SPH_OK;
     Engine& E = *c->eng;
-    E.B.tune_batch = c->tune_batch;
+    *tuning_field(E.B, key) = value;
     if (cudaStreamSynchronize(E.stream) != cudaSuccess) return fail(c, SPH_ECUDA, "sync failed");
     return relay(c, capture(E));
 }
@@ -1047,6 +1082,8 @@ sph_status sph_get_tuning(sph_ctx* c, int key, int* value) {
     if (!c || !value) return SPH_EINVAL;
     switch (key) {
     case SPH_TUNE_LIST_BATCH: *value = c->tune_batch; return SPH_OK;
+    case SPH_TUNE_TPP: *value = c->tune_tpp; return SPH_OK;
+    case SPH_TUNE_BLOCK: *value = c->tune_block; return SPH_OK;
     default: return fail(c, SPH_EINVAL, "unknown tuning key %d", key);
     }
 }
@@ -1070,6 +1107,87 @@ static void engine_profile_read(Engine& E, double* ms, int64_t* launches, int re
             E.prof_cnt[k] = 0;
         }
     }
+}
+
+// Autotuner: coordinate descent over the pair-pass variants (list batch,
+// threads per particle, block size), each timed over real advection steps
+// with the profiling events: score = (D + VT) per advection step + the
+// reference number of sub-steps x (M + C) per sub-step, so trials at
+// different sub-step counts compare fairly.  The first step after each
+// re-capture is not timed.
+static sph_status engine_autotune(Engine& E, int steps_per_trial, sph_tune_report* rep) {
+    if (steps_per_trial < 1) return E.fail(SPH_EINVAL, "steps per trial must be >= 1");
+    const bool prof0 = E.prof;
+    double nsub_ref = -1.0;
+    int64_t steps = 0;
+    int trials = 0;
+    auto score = [&](double* out) -> sph_status {
+        sph_status r = engine_profile(E, 1);
+        if (r == SPH_OK) r = engine_step(E, 1);
+        if (r != SPH_OK) return r;
+        double ms[SPH_PROF_NCLASS];
+        int64_t cnt[SPH_PROF_NCLASS];
+        engine_profile_read(E, ms, cnt, 1);
+        r = engine_step(E, steps_per_trial);
+        if (r != SPH_OK) return r;
+        engine_profile_read(E, ms, cnt, 1);
+        steps += 1 + steps_per_trial;
+        ++trials;
+        if (cnt[SPH_PROF_PASS_M] == 0 || cnt[SPH_PROF_PASS_C] == 0)
+            return E.fail(SPH_ESTATE, "no running case to time");
+        if (nsub_ref < 0.0) nsub_ref = (double)cnt[SPH_PROF_PASS_M] / steps_per_trial;
+        *out = (ms[SPH_PROF_PASS_D] + ms[SPH_PROF_PASS_VT]) / steps_per_trial +
+               nsub_ref * (ms[SPH_PROF_PASS_M] / cnt[SPH_PROF_PASS_M] + ms[SPH_PROF_PASS_C] / cnt[SPH_PROF_PASS_C]);
+        return SPH_OK;
+    };
+    static const int keys[3] = {SPH_TUNE_LIST_BATCH, SPH_TUNE_TPP, SPH_TUNE_BLOCK};
+    static const int vals[3][4] = {{8, 4, 2, 1}, {1, 2, 0, 0}, {128, 64, 256, 0}};
+    int best[3];
+    for (int k = 0; k < 3; ++k) best[k] = *tuning_field(E.B, keys[k]);
+    double s_start = 0.0, s_best = 0.0;
+    sph_status r = score(&s_start);
+    s_best = s_start;
+    for (int k = 0; k < 3 && r == SPH_OK; ++k) {
+        for (int v = 0; v < 4 && r == SPH_OK; ++v) {
+            const int val = vals[k][v];
+            if (val == 0 || val == best[k]) continue;
+            for (int q = 0; q < 3; ++q) *tuning_field(E.B, keys[q]) = best[q];
+            *tuning_field(E.B, keys[k]) = val;
+            double sc = 0.0;
+            r = score(&sc);
+            if (r == SPH_OK && sc < s_best) {
+                s_best = sc;
+                best[k] = val;
+            }
+        }
+    }
+    for (int q = 0; q < 3; ++q) *tuning_field(E.B, keys[q]) = best[q];
+    const sph_status r2 = engine_profile(E, prof0 ? 1 : 0);
+    if (r != SPH_OK) return r;
+    if (rep) {
+        rep->list_batch = best[0];
+        rep->tpp = best[1];
+        rep->block = best[2];
+        rep->ms_step_start = s_start;
+        rep->ms_step_chosen = s_best;
+        rep->substeps_ref = nsub_ref;
+        rep->trials = trials;
+        rep->steps = steps;
+    }
+    return r2;
+}
+
+sph_status sph_autotune(sph_ctx* c, int steps_per_trial, sph_tune_report* report) {
+    if (!c) return SPH_EINVAL;
+    sph_status r = single_engine(c);
+    if (r != SPH_OK) return r;
+    sph_tune_report rep{};
+    r = relay(c, engine_autotune(*c->eng, steps_per_trial, &rep));
+    c->tune_batch = c->eng->B.tune_batch;
+    c->tune_tpp = c->eng->B.tune_tpp;
+    c->tune_block = c->eng->B.tune_block;
+    if (report) *report = rep;
+    return r;
 }
 
 sph_status sph_profile(sph_ctx* c, int enable) {
@@ -1260,11 +1378,18 @@ sph_status sph_batch_info(sph_batch* b, int64_t* n_particles, int* n_cases, int*
 sph_status sph_batch_set_tuning(sph_batch* b, int key, int value) {
     if (!b) return SPH_EINVAL;
     Engine& E = b->eng;
-    if (key != SPH_TUNE_LIST_BATCH) return E.fail(SPH_EINVAL, "unknown tuning key %d", key);
-    if (value != 1 && value != 2 && value != 4 && value != 8) return E.fail(SPH_EINVAL, "list batch must be 1, 2, 4 or 8");
-    E.B.tune_batch = value;
+    if (const char* m = tuning_check(key, value)) return E.fail(SPH_EINVAL, "%s (key %d, value %d)", m, key, value);
+    *tuning_field(E.B, key) = value;
     E.graph_dirty = true;
     return SPH_OK;
+}
+
+sph_status sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tune_report* report) {
+    if (!b) return SPH_EINVAL;
+    sph_tune_report rep{};
+    const sph_status r = engine_autotune(b->eng, steps_per_trial, &rep);
+    if (report) *report = rep;
+    return r;
 }
 
 sph_status sph_batch_profile(sph_batch* b, int enable) {

@@ -449,21 +449,22 @@ constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
 // Walk `cnt` list slots starting at slot k0 with step ks (+1 fluid part,
 // -1 wall part); geometry from the snapshot offsets and the packed cell code.
 // The list entries of a batch are loaded together so that BATCH independent
-// loads of the (DRAM-resident) list stream are in flight per thread.
-template <int BATCH, class F>
+// loads of the (DRAM-resident) list stream are in flight per thread.  With
+// TPP threads per particle, thread `sub` takes list slots sub, sub + TPP, ...
+template <int BATCH, int TPP, class F>
 __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i, float4 si, int k0, int ks,
-                                          int cnt, F&& f) {
+                                          int cnt, int sub, F&& f) {
     const size_t stride = (size_t)B.nb_stride;
     const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
     const ptrdiff_t step = ks * (ptrdiff_t)stride;
     const float sx = si.x + C.cellwf[0], sy = si.y + C.cellwf[1], sz = si.z + C.cellwf[2];
-    for (int q0 = 0; q0 < cnt; q0 += BATCH) {
+    for (int q0 = sub; q0 < cnt; q0 += TPP * BATCH) {
         uint32_t e[BATCH];
 #pragma unroll
-        for (int u = 0; u < BATCH; ++u) e[u] = (q0 + u < cnt) ? __ldg(nb + (q0 + u) * step) : 0u;
+        for (int u = 0; u < BATCH; ++u) e[u] = (q0 + TPP * u < cnt) ? __ldg(nb + (q0 + TPP * u) * step) : 0u;
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
-            if (q0 + u < cnt) {
+            if (q0 + TPP * u < cnt) {
                 const int j = (int)(e[u] & NB_JMASK);
                 const uint32_t d = e[u] >> 26;
                 const float4 sj = __ldg(B.SNAP + j);
@@ -478,19 +479,28 @@ __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i
     }
 }
 
-// Neighbours of a particle from its list (the common case) ...
-template <int BATCH>
+// Neighbours of a particle from its list (the common case), walked by TPP
+// adjacent threads; sum() adds the threads' partial sums (the same value on
+// each) and lead() marks the thread that stores the particle's results.
+template <int BATCH, int TPP = 1>
 struct ListVis {
     const CaseDev& C;
     const Bufs& B;
     int i;
     float4 si;
     uint32_t cnt;
+    int sub = 0;
     template <int PART, class F>
     __device__ __forceinline__ void run(F&& f) const {
-        if (PART & PART_FLUID) list_walk<BATCH>(C, B, i, si, 0, 1, (int)(cnt & 255u), f);
-        if (PART & PART_WALL) list_walk<BATCH>(C, B, i, si, NB_CAP - 1, -1, (int)((cnt >> 8) & 255u), f);
+        if (PART & PART_FLUID) list_walk<BATCH, TPP>(C, B, i, si, 0, 1, (int)(cnt & 255u), sub, f);
+        if (PART & PART_WALL) list_walk<BATCH, TPP>(C, B, i, si, NB_CAP - 1, -1, (int)((cnt >> 8) & 255u), sub, f);
     }
+    __device__ __forceinline__ float sum(float x) const {
+        // the two threads of the particle (adjacent lanes) wait for each other here
+        if (TPP == 2) x += __shfl_xor_sync(3u << ((threadIdx.x & 31u) & ~1u), x, 1);
+        return x;
+    }
+    __device__ __forceinline__ bool lead() const { return sub == 0; }
 };
 
 // ... or, for a particle whose partners did not fit its list, from the
@@ -500,6 +510,8 @@ struct CellVis {
     const Bufs& B;
     int i;
     float4 si;
+    __device__ __forceinline__ float sum(float x) const { return x; }
+    __device__ __forceinline__ bool lead() const { return true; }
     template <int PART, class F>
     __device__ __forceinline__ void run(F&& f) const {
         for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i],
@@ -518,7 +530,7 @@ __device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && 
 // their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
 // runs over all partners (fluid and wall) plus the particle itself.  Static
 // walls of fixed temperature have no pair sums of their own and get no list.
-__global__ void __launch_bounds__(128) k_passD(Bufs B, int par) {
+__global__ void __launch_bounds__(256) k_passD(Bufs B, int par) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
@@ -621,8 +633,12 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
             const float K = 2.f * harmonic2(Mi.k, Mj.k);
             dT = fmaf(C.vol * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
         });
+        ax = vis.sum(ax);
+        ay = vis.sum(ay);
+        az = vis.sum(az);
+        dT = vis.sum(dT);
         const float inv_rho = 1.0f / rho_i;
-        B.AV[i] = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, dT * inv_rho / Mi.cp);
+        if (vis.lead()) B.AV[i] = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, dT * inv_rho / Mi.cp);
         return;
     }
     const bool thermal = !Mi.fixed_T;
@@ -656,6 +672,11 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
             fz = fmaf(cf, vj.z - vw.z, fz);
         }
     });
+    dT = vis.sum(dT);
+    fx = vis.sum(fx);
+    fy = vis.sum(fy);
+    fz = vis.sum(fz);
+    if (!vis.lead()) return;
     B.AV[i] = make_float4(0.f, 0.f, 0.f, thermal ? dT * Mi.inv_rho0_cp : 0.f);
     if (rot) {
         const BodyDev& Bd = C.body[tag_body(tag)];
@@ -663,20 +684,21 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     }
 }
 
-template <bool UNI, int BATCH>
-__global__ void __launch_bounds__(128) k_passVT(Bufs B, int par) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool UNI, int BATCH, int TPP>
+__global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TPP, sub = g % TPP;
     if (i >= B.n) return;
     const uint32_t cnt = B.NBC[i];
     if (!listed(cnt)) {
-        if (!(cnt & NB_HAS)) B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no pair sums: no heating
+        if (!(cnt & NB_HAS) && sub == 0) B.AV[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no pair sums: no heating
         return;                                                            // overflow: k_passVT_ovf
     }
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
     if (!B.st[tag_case(tag)].active) return;
     const CaseDev& C = B.cases[tag_case(tag)];
-    vt_particle<UNI>(B, par, i, si, tag, C, ListVis<BATCH>{C, B, i, si, cnt});
+    vt_particle<UNI>(B, par, i, si, tag, C, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
 }
 
 template <bool UNI>
@@ -758,11 +780,18 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             ay = fmaf(coef, ry, ay);
             az = fmaf(coef, rz, az);
         });
+        ax = vis.sum(ax);
+        ay = vis.sum(ay);
+        az = vis.sum(az);
         const float k = -2.f / rho_i;
         const float4 av = B.AV[i];
         const float nvx = vi.x + dt * (k * ax + av.x + C.g[0]);
         const float nvy = vi.y + dt * (k * ay + av.y + C.g[1]);
         const float nvz = vi.z + dt * (k * az + av.z + C.g[2]);
+        const float sp = sqrtf(dot3f(nvx, nvy, nvz, nvx, nvy, nvz));
+        *case_out = (int)tag_case(tag);
+        *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
+        if (!vis.lead()) return;
         Vout[i] = make_float4(nvx, nvy, nvz, dh_i);
         const double hd = (double)hdt;
         const double* Xs[3] = {first ? B.Y[0] : B.X[0], first ? B.Y[1] : B.X[1], first ? B.Y[2] : B.X[2]};
@@ -774,13 +803,10 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             x = x + hd * (double)vn[a];
             B.X[a][i] = x;
         }
-        const float sp = sqrtf(dot3f(nvx, nvy, nvz, nvx, nvy, nvz));
         if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[tag_case(tag)].err, ERR_NAN);
-        *case_out = (int)tag_case(tag);
-        *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
         return;
     }
-    Vout[i] = vi;
+    if (vis.lead()) Vout[i] = vi;
     if (kind != KIND_ROT) return;
     // rigid-body particle: pressure force of its fluid neighbours on it
     const float4 nwi = B.NRM[i];
@@ -805,13 +831,18 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         fy = fmaf(cf, ry, fy);
         fz = fmaf(cf, rz, fz);
     });
+    fx = vis.sum(fx);
+    fy = vis.sum(fy);
+    fz = vis.sum(fz);
+    if (!vis.lead()) return;
     const BodyDev& Bd = C.body[tag_body(tag)];
     B.TORQ[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
 }
 
-template <bool UNI, int BATCH>
-__global__ void __launch_bounds__(128) k_passM(Bufs B, int par, int first) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool UNI, int BATCH, int TPP>
+__global__ void __launch_bounds__(256) k_passM(Bufs B, int par, int first) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TPP, sub = g % TPP;
     int c = -1;
     unsigned vb = 0u;
     if (i < B.n) {
@@ -821,8 +852,8 @@ __global__ void __launch_bounds__(128) k_passM(Bufs B, int par, int first) {
         const CaseState& S = B.st[tag_case(tag)];
         if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
             const CaseDev& C = B.cases[tag_case(tag)];
-            m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH>{C, B, i, si, cnt}, &c, &vb);
-        } else if (!S.active && first && tag_kind(tag) == KIND_FLUID) {
+            m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub}, &c, &vb);
+        } else if (!S.active && first && tag_kind(tag) == KIND_FLUID && sub == 0) {
             // a case that does not advance still needs its work positions in the new order
             B.X[0][i] = B.Y[0][i];
             B.X[1][i] = B.Y[1][i];
@@ -860,7 +891,7 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
     float4* Vout = B.V[1 - par];
     const float4 vi = Vin[i];
     if (tag_kind(tag) != KIND_FLUID) {
-        Vout[i] = vi;
+        if (vis.lead()) Vout[i] = vi;
         return;
     }
     const MatDev& Mi = C.mat[tag_mat(tag)];
@@ -891,14 +922,17 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
                          __fdividef(rho_i * g_rfw * C.inv_c0, rho_i + rhoR);
         d = fmaf(C.vol * du * dot3f(nw.x, nw.y, nw.z, rx, ry, rz) * inv_r, dW, d);
     });
+    d = vis.sum(d);
+    if (!vis.lead()) return;
     const float drho = 2.f * rho_i * d;
     Vout[i] = make_float4(vi.x, vi.y, vi.z, fmaf(S.hdtf, drho, vi.w));
     B.DR[1 - par][i] = drho;
 }
 
-template <bool UNI, int BATCH>
-__global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool UNI, int BATCH, int TPP>
+__global__ void __launch_bounds__(256) k_passC(Bufs B, int par) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TPP, sub = g % TPP;
     if (i >= B.n) return;
     const uint32_t cnt = B.NBC[i];
     if ((cnt & NB_HAS) && (cnt & NB_OVF)) return;  // k_passC_ovf
@@ -907,7 +941,7 @@ __global__ void __launch_bounds__(128) k_passC(Bufs B, int par) {
     const CaseState& S = B.st[tag_case(tag)];
     if (!S.active) return;
     const CaseDev& C = B.cases[tag_case(tag)];
-    c_particle<UNI>(B, par, i, si, tag, C, S, ListVis<BATCH>{C, B, i, si, cnt});
+    c_particle<UNI>(B, par, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
 }
 
 template <bool UNI>
@@ -1121,7 +1155,7 @@ template <class F>
 __device__ __forceinline__ void visit_any(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
     const uint32_t cnt = B.NBC[i];
     auto g = [&](int j, float4, float, float, float, float) { f(j); };
-    if (listed(cnt)) ListVis<1>{C, B, i, si, cnt}.template run<PART_ALL>(g);
+    if (listed(cnt)) ListVis<1, 1>{C, B, i, si, cnt}.template run<PART_ALL>(g);
     else CellVis{C, B, i, si}.template run<PART_ALL>(g);
 }
 
@@ -1175,6 +1209,61 @@ __global__ void __launch_bounds__(128) k_pair_stats(Bufs B, unsigned long long* 
         atomicAdd(out + 0, ff);
         atomicAdd(out + 1, fw);
     }
+}
+
+// Neighbour-search work of pass D: [particles searched, candidates tested
+// (27-cell populations), partners found], over the particles with a search.
+__global__ void __launch_bounds__(128) k_search_stats(Bufs B, unsigned long long* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long ns = 0, cand = 0, pairs = 0;
+    if (i < B.n && (B.NBC[i] & NB_HAS)) {
+        const float4 si = B.SNAP[i];
+        const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
+        ns = 1;
+        const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
+        const int cl = (int)B.CELLK[i] - C.cell_base;
+        const int cx = cl % nx, cy = (cl / nx) % ny, cz = cl / (nx * ny);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || x >= nx) {
+                        if (!(C.periodic & 1)) continue;
+                        x = (x + nx) % nx;
+                    }
+                    if (y < 0 || y >= ny) {
+                        if (!(C.periodic & 2)) continue;
+                        y = (y + ny) % ny;
+                    }
+                    if (z < 0 || z >= nz) {
+                        if (!(C.periodic & 4)) continue;
+                        z = (z + nz) % nz;
+                    }
+                    const int k = C.cell_base + (z * ny + y) * nx + x;
+                    cand += B.CSTART[k + 1] - B.CSTART[k];
+                }
+        const uint32_t cnt = B.NBC[i];
+        if (listed(cnt)) {
+            pairs = (cnt & 255u) + ((cnt >> 8) & 255u);
+        } else {
+            CellVis{C, B, i, si}.template run<PART_ALL>([&](int, float4, float, float, float, float) { ++pairs; });
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ns += __shfl_down_sync(0xffffffffu, ns, o);
+        cand += __shfl_down_sync(0xffffffffu, cand, o);
+        pairs += __shfl_down_sync(0xffffffffu, pairs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, ns);
+        atomicAdd(out + 1, cand);
+        atomicAdd(out + 2, pairs);
+    }
+}
+
+cudaError_t launch_search_stats(const Bufs& B, unsigned long long* out, cudaStream_t s) {
+    k_search_stats<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s) {
@@ -1241,29 +1330,45 @@ cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+static const int kOvfGrid = 32;
+
+static inline int pair_block(const Bufs& B) {
+    return (B.tune_block == 64 || B.tune_block == 256) ? B.tune_block : 128;
+}
+
 cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
     if (B.fp64) return launch_passD64(B, par, s);
-    k_passD<<<grid_1to1(B.n, 128), 128, 0, s>>>(B, par);
+    k_passD<<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
     return cudaGetLastError();
 }
 
-static const int kOvfGrid = 32;
 
-#define DISPATCH_BATCH(KERNEL, UNI, GRID, BLOCK, S, ...)                               \
-    switch (B.tune_batch) {                                                            \
-    case 1: KERNEL<UNI, 1><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
-    case 2: KERNEL<UNI, 2><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
-    case 4: KERNEL<UNI, 4><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                 \
-    default: KERNEL<UNI, 8><<<GRID, BLOCK, 0, S>>>(__VA_ARGS__); break;                \
-    }
+// Pair-pass variant: list entries loaded together (B.tune_batch), threads per
+// particle (B.tune_tpp) and block size (B.tune_block).
+#define DISPATCH_PASS(KERNEL, UNI, S, ...)                                                          \
+    do {                                                                                           \
+        const int tpp_ = B.tune_tpp == 2 ? 2 : 1;                                                  \
+        const int blk_ = pair_block(B);                                                            \
+        const int grd_ = grid_1to1(B.n * tpp_, blk_);                                              \
+        switch (B.tune_batch * 4 + tpp_) {                                                         \
+        case 1 * 4 + 1: KERNEL<UNI, 1, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 2 * 4 + 1: KERNEL<UNI, 2, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 4 * 4 + 1: KERNEL<UNI, 4, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 1 * 4 + 2: KERNEL<UNI, 1, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 2 * 4 + 2: KERNEL<UNI, 2, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 4 * 4 + 2: KERNEL<UNI, 4, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        case 8 * 4 + 2: KERNEL<UNI, 8, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
+        default: KERNEL<UNI, 8, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;                     \
+        }                                                                                          \
+    } while (0)
 
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
     if (B.fp64) return launch_passVT64(B, par, s);
     if (B.uni_fluid) {
-        DISPATCH_BATCH(k_passVT, true, grid_1to1(B.n, 128), 128, s, B, par);
+        DISPATCH_PASS(k_passVT, true, s, B, par);
         k_passVT_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
     } else {
-        DISPATCH_BATCH(k_passVT, false, grid_1to1(B.n, 128), 128, s, B, par);
+        DISPATCH_PASS(k_passVT, false, s, B, par);
         k_passVT_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par);
     }
     return cudaGetLastError();
@@ -1279,10 +1384,10 @@ cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
     k_halfkick<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
     const int f = first ? 1 : 0;
     if (B.uni_fluid) {
-        DISPATCH_BATCH(k_passM, true, grid_1to1(B.n, 128), 128, s, B, par, f);
+        DISPATCH_PASS(k_passM, true, s, B, par, f);
         k_passM_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par, f);
     } else {
-        DISPATCH_BATCH(k_passM, false, grid_1to1(B.n, 128), 128, s, B, par, f);
+        DISPATCH_PASS(k_passM, false, s, B, par, f);
         k_passM_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par, f);
     }
     return cudaGetLastError();
@@ -1291,10 +1396,10 @@ cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
 cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
     if (B.fp64) return launch_passC64(B, par, s);
     if (B.uni_fluid) {
-        DISPATCH_BATCH(k_passC, true, grid_1to1(B.n, 128), 128, s, B, par);
+        DISPATCH_PASS(k_passC, true, s, B, par);
         k_passC_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
     } else {
-        DISPATCH_BATCH(k_passC, false, grid_1to1(B.n, 128), 128, s, B, par);
+        DISPATCH_PASS(k_passC, false, s, B, par);
         k_passC_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par);
     }
     return cudaGetLastError();

@@ -45,6 +45,8 @@ struct Bufs {
     float4* VH;     // (v, half-kicked drho) input of pass M
     int uni_fluid;  // every case has a single fluid material
     int tune_batch; // list entries loaded together per thread in the pair passes (1, 2, 4, 8)
+    int tune_tpp;   // threads per particle in the list passes VT, M, C (1 or 2)
+    int tune_block; // block size of the pair passes (64, 128, 256)
     // FP64 pair arithmetic (fp64 = 1): particle state in FP64 beside the
     // FP32 arrays above, which then only carry tags, snapshot offsets and lists
     int fp64;
@@ -77,6 +79,7 @@ cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_
                              const int64_t* start_by_id, int32_t* list, cudaStream_t s);
 int kernels_per_advection_step(int kcap, bool fp64);
 cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_search_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
 
 // FP64 pair passes (sph_kernels64.cu)
 cudaError_t launch_passD64(const Bufs& B, int par, cudaStream_t s);

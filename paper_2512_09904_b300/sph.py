@@ -23,7 +23,7 @@ PI32 = C.POINTER(C.c_int32)
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "SPH_OK", -1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_EUNSTABLE",
           -5: "SPH_ETIMEOUT", -6: "SPH_ESTATE"}
-TUNE = dict(list_batch=0)
+TUNE = dict(list_batch=0, tpp=1, block=2)
 PROF_CLASSES = ("sort", "pass_D", "pass_VT", "pass_M", "pass_C", "control", "adv_end", "idle")
 FIELDS = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1), a_visc=(6, 3),
               dTdt=(7, 1), normal=(9, 3))
@@ -43,6 +43,11 @@ class sph_info(C.Structure):
     _fields_ = [("n_fluid", I64), ("n_solid", I64), ("t", D), ("adv_steps", I64), ("substeps", I64),
                 ("last_dt_ad", D), ("last_nsub", C.c_int), ("kcap", C.c_int), ("ncell", C.c_int * 3),
                 ("cell_width", D * 3), ("error_bits", C.c_int), ("graph_launches", C.c_int)]
+
+
+class sph_tune_report(C.Structure):
+    _fields_ = [("list_batch", C.c_int), ("tpp", C.c_int), ("block", C.c_int), ("ms_step_start", D),
+                ("ms_step_chosen", D), ("substeps_ref", D), ("trials", C.c_int), ("steps", I64)]
 
 
 class sph_batch_config(C.Structure):
@@ -87,6 +92,7 @@ def lib():
         L.sph_cell_sort.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile.argtypes = [vp, C.c_int]
         L.sph_pair_stats.argtypes = [vp, PI64, PI64]
+        L.sph_search_stats.argtypes = [vp, PI64, PI64, PI64]
         L.sph_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         L.sph_batch_bytes.argtypes = [C.POINTER(sph_batch_config)]
         L.sph_batch_bytes.restype = I64
@@ -108,6 +114,8 @@ def lib():
         L.sph_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.sph_cell_sort_noalloc.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile_read.argtypes = [vp, PD, PI64, C.c_int]
+        L.sph_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
+        L.sph_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
@@ -256,6 +264,11 @@ class Context:
         self._check(self._L.sph_pair_stats(self._p, C.byref(ff), C.byref(fw)), "sph_pair_stats")
         return ff.value, fw.value
 
+    def sph_search_stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.sph_search_stats(self._p, C.byref(a), C.byref(b), C.byref(c)), "sph_search_stats")
+        return dict(searched=a.value, candidates=b.value, partners=c.value)
+
     def sph_set_tuning(self, key, value):
         self._check(self._L.sph_set_tuning(self._p, int(TUNE[key]), int(value)), "sph_set_tuning")
 
@@ -263,6 +276,11 @@ class Context:
         v = C.c_int()
         self._check(self._L.sph_get_tuning(self._p, int(TUNE[key]), C.byref(v)), "sph_get_tuning")
         return v.value
+
+    def sph_autotune(self, steps_per_trial=3):
+        r = sph_tune_report()
+        self._check(self._L.sph_autotune(self._p, int(steps_per_trial), C.byref(r)), "sph_autotune")
+        return {f: getattr(r, f) for f, _ in sph_tune_report._fields_}
 
     def sph_profile(self, enable=True):
         self._check(self._L.sph_profile(self._p, int(bool(enable))), "sph_profile")
@@ -406,6 +424,11 @@ class Batch:
 
     def set_tuning(self, key, value):
         self._check(self._L.sph_batch_set_tuning(self._p, int(TUNE[key]), int(value)), "sph_batch_set_tuning")
+
+    def autotune(self, steps_per_trial=3):
+        r = sph_tune_report()
+        self._check(self._L.sph_batch_autotune(self._p, int(steps_per_trial), C.byref(r)), "sph_batch_autotune")
+        return {f: getattr(r, f) for f, _ in sph_tune_report._fields_}
 
     def profile(self, enable=True):
         self._check(self._L.sph_batch_profile(self._p, int(bool(enable))), "sph_batch_profile")

@@ -105,3 +105,16 @@ def test_reads_before_first_step_are_state_errors(sphlib):
         ctx.sph_read_torque_heat(0)
     assert e.value.status == sphlib.SPH_ESTATE
     ctx.close()
+
+
+def test_tuning_keys_are_validated(sphlib):
+    case = W.still_tank(nx=4, ny=4, nz=4, wall_h=6)
+    ctx = sphlib.Context(case.config, stream=0)
+    for key, good, bad in (("list_batch", 4, 3), ("tpp", 2, 3), ("block", 256, 96)):
+        ctx.sph_set_tuning(key, good)
+        assert ctx.sph_get_tuning(key) == good
+        with pytest.raises(sphlib.SphError) as e:
+            ctx.sph_set_tuning(key, bad)
+        assert e.value.status == sphlib.SPH_EINVAL
+        assert ctx.sph_get_tuning(key) == good
+    ctx.close()

@@ -1,0 +1,118 @@
+"""Pair-pass variants and the autotuner.
+
+List batch and block size change how the work is laid out, not the order of
+any sum: results stay bitwise equal.  Two threads per particle add each
+particle's pair terms in two interleaved halves: FP32 rounding changes, and
+the result keeps parity with the oracle at the FP32 tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_09904_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("pos", "vel", "rho", "T")
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2512_09904_b300 import build
+    build.build()
+    from paper_2512_09904_b300 import sph as S
+    return S
+
+
+def _run(sph, case, steps, **tune):
+    ctx = sph.from_case(case, stream=0)
+    for k, v in tune.items():
+        ctx.sph_set_tuning(k, v)
+    ctx.sph_step(steps)
+    out = {f: ctx.sph_read_fields(f) for f in FIELDS}
+    out["th"] = ctx.sph_read_torque_heat(0)
+    ctx.close()
+    return out
+
+
+def test_batch_and_block_leave_results_bitwise_unchanged(sph):
+    case = W.rotating_cylinder()
+    ref = _run(sph, case, 3)
+    for batch in (1, 2, 4, 8):
+        for block in (64, 128, 256):
+            got = _run(sph, case, 3, list_batch=batch, block=block)
+            for f in FIELDS:
+                assert np.array_equal(got[f], ref[f]), (batch, block, f)
+            assert got["th"] == ref["th"], (batch, block)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("still_tank_small", lambda: W.still_tank(nx=12, ny=12, nz=8, wall_h=12)),
+    ("rotating_cylinder", lambda: W.rotating_cylinder()),
+])
+def test_two_threads_per_particle_parity(sph, oracle, name, make):
+    case = make()
+    ctx = sph.from_case(case, stream=0)
+    ctx.sph_set_tuning("tpp", 2)
+    assert ctx.sph_get_tuning("tpp") == 2
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(3)
+    sim.step(3)
+    f = W.flatten(case)
+    sel = f["kind"] == 0
+    cfg = case.config
+    for k, s in (("pos", cfg["dx"]), ("vel", cfg["u_ref"])):
+        g, r = ctx.sph_read_fields(k)[sel], sim.field(k)[sel]
+        err = float(np.max(np.abs(g - r) / np.maximum(np.abs(r), s)))
+        assert err <= 3e-5, (name, k, err)
+    ctx.close()
+
+
+def test_autotune_picks_a_variant_and_keeps_stepping(sph):
+    case = W.gear_bath(dx=4e-3, omega=600.0)
+    ctx = sph.from_case(case, stream=0)
+    ctx.sph_step(2)
+    t0 = ctx.sph_get_info()["adv_steps"]
+    rep = ctx.sph_autotune(steps_per_trial=1)
+    print(rep)
+    assert rep["list_batch"] in (1, 2, 4, 8) and rep["tpp"] in (1, 2) and rep["block"] in (64, 128, 256)
+    assert rep["trials"] == 1 + 3 + 1 + 2
+    assert ctx.sph_get_info()["adv_steps"] == t0 + rep["steps"] == t0 + 2 * rep["trials"]
+    assert 0.0 < rep["ms_step_chosen"] <= rep["ms_step_start"]
+    assert ctx.sph_get_tuning("list_batch") == rep["list_batch"]
+    assert ctx.sph_get_tuning("tpp") == rep["tpp"]
+    assert ctx.sph_get_tuning("block") == rep["block"]
+    ctx.sph_step(2)
+    ctx.close()
+
+
+def test_batch_autotune(sph):
+    cases = [W.gear_bath(dx=6e-3, omega=w) for w in (150.0, 600.0)]
+    cap = sum(c.n_total for c in cases)
+    cells = sum(sph.cells_of(c) for c in cases) + 16
+    b = sph.Batch(cap, 4, cells, history_steps=64)
+    slots = [b.admit(c, 40) for c in cases]
+    b.step(1)
+    rep = b.autotune(steps_per_trial=1)
+    print(rep)
+    assert rep["trials"] == 7 and rep["steps"] == 14
+    b.step(2)
+    for s in slots:
+        assert b.poll(s)[2] == sph.BATCH_RUNNING
+    b.close()
+
+
+def test_search_stats(sph):
+    case = W.still_tank()
+    ctx = sph.from_case(case, stream=0)
+    ctx.sph_step(1)
+    st = ctx.sph_search_stats()
+    ff, fw = ctx.sph_pair_stats()
+    assert case.n_fluid <= st["searched"] <= case.n_total
+    assert ff + fw <= st["partners"] < st["candidates"]
+    # interior lattice particle: 80 partners among 27 cells of >= (2h)^3 / dx^3 = 17.6 each
+    assert 60 < st["partners"] / st["searched"] < 90
+    assert 27 * 17.6 * 0.8 < st["candidates"] / st["searched"] < 27 * 17.6 * 1.4
+    ctx.close()
