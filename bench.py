@@ -191,7 +191,7 @@ def main():
 
     case = workload(args.dx, args.omega)
     stream = torch.cuda.current_stream()
-    ctx = sph.from_case(case, stream=stream.cuda_stream)
+    warm = max(args.warmup, 3)
     tune = None
     if not args.no_autotune:
         # pick the pair-pass variant on a scratch copy of the workload, so the
@@ -201,16 +201,21 @@ def main():
         tune = tctx.sph_autotune(steps_per_trial=2)
         tctx.close()
         del tctx
-        for key in ("list_batch", "tpp", "block"):
-            ctx.sph_set_tuning(key, tune[key])
-    ctx.sph_step(1)                     # upload + first advection step
+    variant = {k: (tune[k] if tune else 0) for k in ("list_batch", "tpp", "block")}
     for key, val in (("list_batch", args.list_batch), ("tpp", args.tpp), ("block", args.block)):
         if val:
-            ctx.sph_set_tuning(key, val)
-    ctx.sph_profile(True)               # event records between kernel groups
-    ctx.sph_step(max(args.warmup, 3) - 1)
+            variant[key] = val
+
+    def make_ctx():
+        c = sph.from_case(case, stream=stream.cuda_stream)
+        for key, val in variant.items():
+            if val:
+                c.sph_set_tuning(key, val)
+        return c
+
+    ctx = make_ctx()
+    ctx.sph_step(warm)                  # upload + first advection step + warm-up
     info0 = ctx.sph_get_info()
-    ctx.sph_profile_read(reset=True)
 
     clocks = Clocks(local)
     if world > 1:
@@ -227,7 +232,6 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     info1 = ctx.sph_get_info()
-    prof = ctx.sph_profile_read(reset=True)
     substeps = info1["substeps"] - info0["substeps"]
     units = case.n_fluid * substeps
     ff, fw = ctx.sph_pair_stats()
@@ -236,6 +240,17 @@ def main():
     th = ctx.sph_read_torque_heat(0)
     ctx.close()
     del ctx
+
+    # per-kernel-group device times: the same steps replayed from the same
+    # state (the step is deterministic) with event records between the groups
+    rctx = make_ctx()
+    rctx.sph_step(warm)
+    rctx.sph_profile(True)
+    rctx.sph_step(args.steps)
+    prof = rctx.sph_profile_read(reset=True)
+    replay_substeps = rctx.sph_get_info()["substeps"] - info0["substeps"]
+    rctx.close()
+    del rctx
 
     if world > 1:
         t = torch.tensor([ms, float(units)], dtype=torch.float64, device="cuda")
@@ -273,6 +288,8 @@ def main():
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max from {src} peaks file)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
                 "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
+                "timing": "per-group device times from a replay of the timed steps with event records "
+                          f"between kernel groups (same sub-steps: {replay_substeps == substeps})",
                 "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": hbm_gbs / peaks.get("hbm_gbs", 6505.9), "bytes_per_launch": bytes_launch},
                 "share": {k: round(v[0] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
@@ -289,7 +306,7 @@ def main():
                       "pair_variant": {k: ctx_tuning[k] for k in ("list_batch", "tpp", "block")},
                       "autotune": tune},
            "roofline": roofline,
-           "gpu_launches": int(info1["graph_launches"]) * args.steps,
+           "gpu_launches": int(info1["kernels_fixed"]) * args.steps + int(info1["kernels_per_substep"]) * substeps,
            "clocks": clk}
 
     # end to end through the C ABI from host arrays: create + upload + steps +
@@ -297,7 +314,7 @@ def main():
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = sph.from_case(case, stream=stream.cuda_stream)
+        c2 = make_ctx()
         for _ in range(args.steps):
             c2.sph_step(1)
             c2.sph_read_torque_heat(0)

@@ -169,7 +169,9 @@ typedef struct {
     int ncell[3];
     double cell_width[3];
     int error_bits;           /* 1 NaN/Inf, 2 fluid left the box */
-    int graph_launches;       /* kernels launched per advection step */
+    int graph_launches;       /* kernels per advection step of the profiling graph (kcap sub-step slots) */
+    int kernels_fixed;        /* kernels per advection step of the stepping graph: kernels_fixed + */
+    int kernels_per_substep;  /* kernels_per_substep x (its sub-steps) */
 } sph_info;
 
 sph_status sph_get_info(sph_ctx* ctx, sph_info* info);

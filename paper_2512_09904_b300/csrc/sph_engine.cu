@@ -103,6 +103,7 @@ struct HostCase {
     int ncell[3] = {0, 0, 0};
     double cellw[3] = {0, 0, 0};
     int64_t steps_req = 0;
+    int body_lo[MAX_BODY] = {0, 0, 0, 0}, body_hi[MAX_BODY] = {0, 0, 0, 0};  // rigid-body id ranges
 };
 
 // device bytes per particle slot and per cell of an engine
@@ -117,6 +118,7 @@ constexpr int64_t kBytesPerCell = 4 * 2 + 1;
 struct Engine {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only to capture the step graph
+    cudaStream_t cap2 = nullptr; // ... and the body of its sub-step loop
     std::string err;
     int64_t n_cap = 0, cells_cap = 0;
     int c_cap = 0, hist_cap = 0;
@@ -133,6 +135,7 @@ struct Engine {
     RangeAlloc ids, cells;
     bool need_prepare = false;
     int64_t graph_steps = 0;  // advection steps launched so far
+    int tq_cap = 0;           // capacity of the torque chunk table
     int64_t graph_instantiations = 0, graph_updates = 0;
     // profiling: CUDA events recorded between kernel groups inside the graph
     bool prof = false;
@@ -154,6 +157,7 @@ struct Engine {
         if (allocated) cudaStreamSynchronize(stream);
         for (auto e : ev) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
+        if (cap2) cudaStreamDestroy(cap2);
         for (void* p : allocs) cudaFree(p);
     }
 };
@@ -279,6 +283,10 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     AL(B.SCANBLK, scan_blocks((int)cells_cap + 1) + 1);
     AL(B.PART, (size_t)3 * B.max_chunks);
     AL(B.CHUNK_CASE, B.max_chunks);
+    E.tq_cap = (int)((n + TQ_CHUNK - 1) / TQ_CHUNK) + c_cap * MAX_BODY;
+    AL(B.TQC, E.tq_cap);
+    AL(B.TQR, (size_t)c_cap * MAX_BODY);
+    AL(B.TQP, (size_t)2 * E.tq_cap);
     AL(B.nchunks, 1);
     AL(B.HIST, (size_t)8 * (hist_cap > 0 ? hist_cap : 1) * c_cap);
     AL(E.d_field, (size_t)3 * n);
@@ -450,6 +458,10 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     }
     CaseDev C;
     build_case(c, H, C);
+    for (int b = 0; b < MAX_BODY; ++b) {
+        H.body_lo[b] = C.body[b].set ? C.body[b].id_lo : 0;
+        H.body_hi[b] = C.body[b].set ? C.body[b].id_hi : 0;
+    }
     CaseState S;
     memset(&S, 0, sizeof S);
     S.alive = 1;
@@ -539,6 +551,7 @@ static cudaError_t mark(Engine& E, int cls, int sub) {
 static sph_status capture(Engine& E) {
     // capture runs nothing; it needs a stream other than the legacy default one
     if (!E.cap) E_CUDA(E, cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking));
+    if (!E.cap2) E_CUDA(E, cudaStreamCreateWithFlags(&E.cap2, cudaStreamNonBlocking));
     E.kcap_max = 0;
     for (const HostCase& H : E.cases)
         if (H.used) E.kcap_max = std::max(E.kcap_max, H.kcap);
@@ -546,6 +559,28 @@ static sph_status capture(Engine& E) {
     // particles, not the capacity, so one particle's slots stay close together
     E.B.nb_stride = std::max(E.B.n, 1);
     E.B.max_chunks_used = (int)((E.B.n + RED_CHUNK - 1) / RED_CHUNK) + E.c_cap + 1;
+    {
+        // torque chunks of the resident rigid bodies (fixed TQ_CHUNK id blocks from each body's start)
+        std::vector<int4> tqc;
+        std::vector<int2> tqr((size_t)E.c_cap * MAX_BODY, make_int2(0, 0));
+        for (int c = 0; c < E.c_cap; ++c) {
+            const HostCase& H = E.cases[c];
+            if (!H.used) continue;
+            for (int b = 0; b < MAX_BODY; ++b) {
+                const int lo = H.body_lo[b], hi = H.body_hi[b];
+                if (hi <= lo) continue;
+                tqr[(size_t)c * MAX_BODY + b] = make_int2((int)tqc.size(), (hi - lo + TQ_CHUNK - 1) / TQ_CHUNK);
+                for (int a = lo; a < hi; a += TQ_CHUNK) tqc.push_back(make_int4(c, b, a, std::min(a + TQ_CHUNK, hi)));
+            }
+        }
+        if ((int)tqc.size() > E.tq_cap) return E.fail(SPH_ECUDA, "torque chunk table overflow");
+        E.B.ntq = (int)tqc.size();
+        if (!tqc.empty())
+            E_CUDA(E, cudaMemcpyAsync(E.B.TQC, tqc.data(), sizeof(int4) * tqc.size(), cudaMemcpyHostToDevice,
+                                      E.stream));
+        E_CUDA(E, cudaMemcpyAsync(E.B.TQR, tqr.data(), sizeof(int2) * tqr.size(), cudaMemcpyHostToDevice, E.stream));
+        E_CUDA(E, cudaStreamSynchronize(E.stream));
+    }
     const size_t nev = 8 + 4 * (size_t)E.kcap_max + 8;
     if (E.prof && E.ev.size() < nev) {
         for (auto e : E.ev) cudaEventDestroy(e);
@@ -565,15 +600,53 @@ static sph_status capture(Engine& E) {
         if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_D, -1);
         if (e == cudaSuccess) e = launch_passVT(E.B, p, E.cap);
         if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_VT, -1);
-        for (int k = 0; k < E.kcap_max && e == cudaSuccess; ++k) {
-            e = launch_sub_begin(E.B, E.cap);
-            if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
-            if (e == cudaSuccess) e = launch_passM(E.B, p, k == 0, E.cap);
-            if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_M, k);
-            if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap);
-            if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_C, k);
-            if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap);
-            if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
+        if (E.prof) {
+            // profiling: kcap unrolled sub-step slots with event records between
+            // the kernel groups (slots past a step's last sub-step exit at once)
+            for (int k = 0; k < E.kcap_max && e == cudaSuccess; ++k) {
+                e = launch_sub_begin(E.B, E.cap);
+                if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
+                if (e == cudaSuccess) e = launch_passM(E.B, p, E.cap);
+                if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_M, k);
+                if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap);
+                if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_C, k);
+                if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap);
+                if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
+            }
+        } else if (e == cudaSuccess) {
+            // the sub-steps as a WHILE conditional node: its body is one
+            // sub-step, and k_sub_cond clears the condition once no case has a
+            // sub-step left, so only the sub-steps a step needs are launched
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            e = cudaStreamGetCaptureInfo(E.cap, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+            cudaGraphConditionalHandle h = 0;
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t cn = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&cn, cg, deps, nullptr, ndeps, &np);
+            if (e == cudaSuccess) {
+                e = cudaStreamBeginCaptureToGraph(E.cap2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    e = launch_sub_begin(E.B, E.cap2);
+                    if (e == cudaSuccess) e = launch_passM(E.B, p, E.cap2);
+                    if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap2);
+                    if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap2);
+                    if (e == cudaSuccess) e = launch_sub_cond(E.B, h, E.cap2);
+                    cudaGraph_t bg = nullptr;
+                    const cudaError_t e3 = cudaStreamEndCapture(E.cap2, &bg);
+                    if (e == cudaSuccess) e = e3;
+                }
+            }
+            if (e == cudaSuccess)
+                e = cudaStreamUpdateCaptureDependencies(E.cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
         }
         if (e == cudaSuccess) e = launch_adv_end(E.B, p, E.cap);
         if (e == cudaSuccess) e = mark(E, SPH_PROF_ADV_END, -1);
@@ -996,6 +1069,8 @@ sph_status sph_get_info(sph_ctx* c, sph_info* info) {
         info->cell_width[a] = c->cellw[a];
     }
     info->graph_launches = kernels_per_advection_step(c->kcap, c->cfg.pair_precision == 1);
+    kernels_in_step(c->cfg.pair_precision == 1, true, &info->kernels_fixed, &info->kernels_per_substep);
+    info->kernels_per_substep += 1;  // the loop condition
     if (c->started) {
         Engine& E = *c->eng;
         sph_status s = pull_state(E);

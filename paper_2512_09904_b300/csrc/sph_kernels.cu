@@ -128,43 +128,66 @@ __device__ double block_sum_256(double v, double* sh) {
     return r;
 }
 
-// Torque of the fluid on each rigid body: sum of per-particle contributions
+// Torque of the fluid on each rigid body: per-particle contributions summed
 // over the body's id range (id order: independent of the sort and of other
-// resident cases), then sub-step time bookkeeping.
-__global__ void __launch_bounds__(256) k_sub_end(Bufs B) {
-    const int c = blockIdx.x;
+// resident cases) in two fixed-order levels, chunks of TQ_CHUNK ids first.
+__global__ void __launch_bounds__(256) k_torque_chunks(Bufs B) {
+    __shared__ double sh[256];
+    const int4 q = B.TQC[blockIdx.x];  // (case, body, id_lo, id_hi)
+    const CaseDev& C = B.cases[q.x];
+    const CaseState& S = B.st[q.x];
+    if (!S.active) return;
+    const bool first = S.nsub == 0;
+    double acc = 0.0, accv = 0.0;
+    for (int id = q.z + threadIdx.x; id < q.w; id += 256) {
+        acc += C.fp64 ? B.TORQ64[id] : (double)B.TORQ[id];
+        if (first) accv += C.fp64 ? B.TORQV64[id] : (double)B.TORQV[id];
+    }
+    acc = block_sum_256(acc, sh);
+    accv = first ? block_sum_256(accv, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        B.TQP[2 * blockIdx.x] = acc;
+        B.TQP[2 * blockIdx.x + 1] = accv;
+    }
+}
+
+// ... then the chunk sums of each body in order, and the sub-step's time
+// bookkeeping (one thread per case).
+__global__ void k_sub_end(Bufs B) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.ncases) return;
     const CaseDev& C = B.cases[c];
     CaseState& S = B.st[c];
-    __shared__ double sh[256];
-    const int active = S.active;
+    if (!S.active) return;
     const int first = S.nsub == 0;
-    __syncthreads();  // every thread has read the state before thread 0 updates it
-    if (!active) return;
     for (int b = 0; b < C.n_body; ++b) {
-        const BodyDev& Bd = C.body[b];
-        if (!Bd.set) continue;
-        double acc = 0.0, accv = 0.0;
-        for (int id = Bd.id_lo + threadIdx.x; id < Bd.id_hi; id += 256) {
-            acc += C.fp64 ? B.TORQ64[id] : (double)B.TORQ[id];
-            if (first) accv += C.fp64 ? B.TORQV64[id] : (double)B.TORQV[id];
+        if (!C.body[b].set) continue;
+        const int2 r = B.TQR[c * MAX_BODY + b];  // (first chunk, chunks)
+        double tq = 0.0, tqv = 0.0;
+        for (int k = 0; k < r.y; ++k) {
+            tq += B.TQP[2 * (r.x + k)];
+            tqv += B.TQP[2 * (r.x + k) + 1];
         }
-        double tq = block_sum_256(acc, sh);
-        double tqv = first ? block_sum_256(accv, sh) : 0.0;
-        if (threadIdx.x == 0) {
-            S.tq_p[b] = tq;
-            if (first) S.tq_v[b] = tqv;
-            S.tq_inst[b] = S.tq_p[b] + S.tq_v[b];
-            S.tq_int[b] += S.dt * S.tq_inst[b];
-        }
+        S.tq_p[b] = tq;
+        if (first) S.tq_v[b] = tqv;
+        S.tq_inst[b] = S.tq_p[b] + S.tq_v[b];
+        S.tq_int[b] += S.dt * S.tq_inst[b];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        S.time_int += S.dt;
-        S.tau = S.reach ? S.dt_ad : S.tau + S.dt;
-        S.nsub += 1;
-        S.substeps += 1;
-        if (S.last) S.active = 0;
-    }
+    S.time_int += S.dt;
+    S.tau = S.reach ? S.dt_ad : S.tau + S.dt;
+    S.nsub += 1;
+    S.substeps += 1;
+    if (S.last) S.active = 0;
+}
+
+// Condition of the graph's sub-step loop (a WHILE conditional node): run
+// another sub-step while any case has one left.  Every case stops after at
+// most kcap sub-steps (k_sub_begin), so the loop always ends.
+__global__ void k_sub_cond(Bufs B, cudaGraphConditionalHandle h) {
+    int any = 0;
+    for (int c = threadIdx.x; c < B.ncases; c += blockDim.x) any |= B.st[c].active;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // ------------------------------------------------------------ cell sort ---
@@ -840,7 +863,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
 }
 
 template <bool UNI, int BATCH, int TPP>
-__global__ void __launch_bounds__(256) k_passM(Bufs B, int par, int first) {
+__global__ void __launch_bounds__(256) k_passM(Bufs B, int par) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
     int c = -1;
@@ -850,6 +873,7 @@ __global__ void __launch_bounds__(256) k_passM(Bufs B, int par, int first) {
         const float4 si = B.SNAP[i];
         const uint32_t tag = __float_as_uint(si.w);
         const CaseState& S = B.st[tag_case(tag)];
+        const int first = S.nsub == 0;  // first sub-step of the advection step
         if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
             const CaseDev& C = B.cases[tag_case(tag)];
             m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub}, &c, &vb);
@@ -867,7 +891,7 @@ __global__ void __launch_bounds__(256) k_passM(Bufs B, int par, int first) {
 }
 
 template <bool UNI>
-__global__ void __launch_bounds__(128) k_passM_ovf(Bufs B, int par, int first) {
+__global__ void __launch_bounds__(128) k_passM_ovf(Bufs B, int par) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < *B.novf; k += gridDim.x * blockDim.x) {
         const int i = B.OVFL[k];
         const float4 si = B.SNAP[i];
@@ -877,7 +901,7 @@ __global__ void __launch_bounds__(128) k_passM_ovf(Bufs B, int par, int first) {
         const CaseDev& C = B.cases[tag_case(tag)];
         int c = -1;
         unsigned vb = 0u;
-        m_particle<UNI>(B, par, first, i, si, tag, C, S, CellVis{C, B, i, si}, &c, &vb);
+        m_particle<UNI>(B, par, S.nsub == 0, i, si, tag, C, S, CellVis{C, B, i, si}, &c, &vb);
         if (c >= 0) atomicMax(&B.st[c].vmax_bits, vb);
     }
 }
@@ -1379,16 +1403,15 @@ cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s) {
-    if (B.fp64) return launch_passM64(B, par, first, s);
+cudaError_t launch_passM(const Bufs& B, int par, cudaStream_t s) {
+    if (B.fp64) return launch_passM64(B, par, s);
     k_halfkick<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
-    const int f = first ? 1 : 0;
     if (B.uni_fluid) {
-        DISPATCH_PASS(k_passM, true, s, B, par, f);
-        k_passM_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par, f);
+        DISPATCH_PASS(k_passM, true, s, B, par);
+        k_passM_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);
     } else {
-        DISPATCH_PASS(k_passM, false, s, B, par, f);
-        k_passM_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par, f);
+        DISPATCH_PASS(k_passM, false, s, B, par);
+        k_passM_ovf<false><<<kOvfGrid, 128, 0, s>>>(B, par);
     }
     return cudaGetLastError();
 }
@@ -1406,7 +1429,8 @@ cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
 }
 
 cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s) {
-    k_sub_end<<<B.ncases, 256, 0, s>>>(B);
+    if (B.ntq > 0) k_torque_chunks<<<B.ntq, 256, 0, s>>>(B);
+    k_sub_end<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -1462,11 +1486,23 @@ cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_sub_cond(const Bufs& B, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_sub_cond<<<1, 256, 0, s>>>(B, h);
+    return cudaGetLastError();
+}
+
+void kernels_in_step(bool fp64, bool torque, int* fixed, int* per_substep) {
+    // adv_begin + sort (hash, 3 scan, scatter, order, reorder, segments) + D + VT (+ overflow)
+    // + T update, 2 reductions, adv_end
+    *fixed = 1 + 8 + 1 + (fp64 ? 1 : 2) + 4;
+    // sub_begin, half kick, M (+ overflow), C (+ overflow), torque chunks, sub_end
+    *per_substep = 1 + 1 + (fp64 ? 1 : 2) + (fp64 ? 1 : 2) + (torque ? 1 : 0) + 1;
+}
+
 int kernels_per_advection_step(int kcap, bool fp64) {
-    // adv_begin + sort(hash, 3 scan, scatter, order, reorder, segments)
-    // + D + VT(+ovf) + kcap * (sub_begin, halfkick, M(+ovf), C(+ovf), sub_end)
-    // + T_update + 2 reduce + adv_end; the FP64 passes have no overflow kernels
-    return fp64 ? 1 + 8 + 2 + 5 * kcap + 4 : 1 + 8 + 3 + 7 * kcap + 4;
+    int f = 0, k = 0;
+    kernels_in_step(fp64, true, &f, &k);
+    return f + kcap * k;
 }
 
 cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int id_base, double* out,

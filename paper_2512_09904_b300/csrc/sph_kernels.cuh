@@ -6,6 +6,7 @@ namespace sph {
 
 constexpr int RED_CHUNK = 4096;  // slots per fixed-order reduction chunk
 constexpr int SCAN_TILE = 2048;  // cells per scan tile
+constexpr int TQ_CHUNK = 2048;   // body ids per torque partial sum
 
 // All device buffers of one engine (pointers only; passed by value).
 struct Bufs {
@@ -43,6 +44,10 @@ struct Bufs {
     int* OVFL;      // slots whose partners overflowed their list (this step)
     int* novf;      // number of entries in OVFL
     float4* VH;     // (v, half-kicked drho) input of pass M
+    int4* TQC;      // torque chunks: (case, body, id_lo, id_hi), TQ_CHUNK ids each
+    int2* TQR;      // per (case, body): (first chunk, chunks)
+    double* TQP;    // chunk partial sums (pressure, viscous)
+    int ntq;        // chunks in use
     int uni_fluid;  // every case has a single fluid material
     int tune_batch; // list entries loaded together per thread in the pair passes (1, 2, 4, 8)
     int tune_tpp;   // threads per particle in the list passes VT, M, C (1 or 2)
@@ -67,7 +72,7 @@ cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s);  // hash..reord
 cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s);
-cudaError_t launch_passM(const Bufs& B, int par, bool first, cudaStream_t s);
+cudaError_t launch_passM(const Bufs& B, int par, cudaStream_t s);  // first sub-step: decided on the device
 cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s);
 cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s);
@@ -77,14 +82,18 @@ cudaError_t launch_gather_field(const Bufs& B, int par, int field, int cs, int i
                                 cudaStream_t s);
 cudaError_t launch_neighbors(const Bufs& B, int par, int cs, int id_base, int64_t* counts_by_id,
                              const int64_t* start_by_id, int32_t* list, cudaStream_t s);
-int kernels_per_advection_step(int kcap, bool fp64);
+int kernels_per_advection_step(int kcap, bool fp64);  // unrolled graph with kcap sub-step slots
+// Kernels of one advection step: fixed part and per sub-step (the loop graph
+// adds its condition kernel per sub-step).
+void kernels_in_step(bool fp64, bool torque, int* fixed, int* per_substep);
+cudaError_t launch_sub_cond(const Bufs& B, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_pair_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_search_stats(const Bufs& B, unsigned long long* out, cudaStream_t s);
 
 // FP64 pair passes (sph_kernels64.cu)
 cudaError_t launch_passD64(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_passVT64(const Bufs& B, int par, cudaStream_t s);
-cudaError_t launch_passM64(const Bufs& B, int par, bool first, cudaStream_t s);
+cudaError_t launch_passM64(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_passC64(const Bufs& B, int par, cudaStream_t s);
 
 // stateless cell sort (positions AoS)

@@ -222,12 +222,13 @@ __global__ void k_halfkick64(Bufs B, int par) {
 // Pass M: Riemann pressure force (Eqs. 10-12), wall problem (Eqs. 16-19 with
 // the dissipation term of Eq. 12), kick and both half drifts; pressure torque
 // on rigid-body particles.
-__global__ void __launch_bounds__(128) k_passM64(Bufs B, int par, int first) {
+__global__ void __launch_bounds__(128) k_passM64(Bufs B, int par) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const uint32_t tag = B.TAG[1 - par][i];
     const CaseState& S = B.st[tag_case(tag)];
     const uint32_t kind = tag_kind(tag);
+    const bool first = S.nsub == 0;  // first sub-step of the advection step
     if (!S.active) {
         if (first && kind == KIND_FLUID)
             for (int a = 0; a < 3; ++a) B.X[a][i] = B.Y[a][i];
@@ -378,9 +379,9 @@ cudaError_t launch_passVT64(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_passM64(const Bufs& B, int par, bool first, cudaStream_t s) {
+cudaError_t launch_passM64(const Bufs& B, int par, cudaStream_t s) {
     k_halfkick64<<<blocks(B.n, 256), 256, 0, s>>>(B, par);
-    k_passM64<<<blocks(B.n, 128), 128, 0, s>>>(B, par, first ? 1 : 0);
+    k_passM64<<<blocks(B.n, 128), 128, 0, s>>>(B, par);
     return cudaGetLastError();
 }
 
