@@ -51,6 +51,26 @@ BYTES_M, BYTES_C = 120, 56
 BYTES_VT, BYTES_D = 56, 80
 BYTES_PER_LIST_ENTRY = 4
 
+# Measured DRAM bytes (read + write) per unit of work, from one ncu capture per
+# kernel (profiles/pass_kernels_gear_bath_650k.md: the same geometry at
+# dx = 1.5 mm; traffic scales with the units, own state plus list entries).
+# Units: pass D and VT per partner found, M and C per directed fluid pair.
+# Valid only for the kernel sources they were taken on (hash below); after
+# any change to them the roofline reports traffic = null.
+TRAFFIC = {"sources_sha256_16": "c264847d03508b7d",
+           "bytes_per_unit": {"pass_D": 6.60, "pass_VT": 5.41, "pass_M": 6.26, "pass_C": 5.50}}
+KERNEL_SOURCES = ("paper_2512_09904_b300/csrc/sph_kernels.cu", "paper_2512_09904_b300/csrc/sph_internal.cuh",
+                  "paper_2512_09904_b300/csrc/sph_kernels.cuh")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -283,8 +303,12 @@ def main():
     bytes_launch = n_part * per_particle + BYTES_PER_LIST_ENTRY * n_list
     hbm_gbs = bytes_launch / avg_s / 1e9
     total_prof = sum(v[0] for v in prof.values())
+    traffic = None
+    if kernel_sources_hash() == TRAFFIC["sources_sha256_16"]:
+        n_units = search["partners"] if dom in ("pass_D", "pass_VT") else ff + fw
+        traffic = TRAFFIC["bytes_per_unit"][dom] * n_units
     roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
-                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": traffic,
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max from {src} peaks file)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
                 "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
