@@ -140,7 +140,12 @@ enum {
     SPH_FIELD_DRHO = 5,     /* n; last continuity rate */
     SPH_FIELD_AVISC = 6,    /* n*3; viscous acceleration of the last advection step */
     SPH_FIELD_DTDT = 7,     /* n; conduction rate of the last advection step */
-    SPH_FIELD_NORMAL = 9    /* n*3; wall normal at the current time (solids) */
+    SPH_FIELD_NORMAL = 9,   /* n*3; wall normal at the current time (solids) */
+    SPH_FIELD_CONTACT = 11  /* n; contact factor of rigid-body particles (Sec. 2.7, Eq. 24):
+                               sum of V_j W_ij over lubricant partners, V_j = m_j / rho_j,
+                               over its fully immersed value dx^3 (sum of W over the full
+                               lattice, the particle itself excluded); last advection
+                               step; 0 for fluid and static walls */
 };
 
 /* Copy field `field` of all n particles (n must equal the particle count)

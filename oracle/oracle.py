@@ -141,7 +141,7 @@ def cell_order(pos, origin, cellw, ncell):
 
 
 FIELD = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1), a_visc=(6, 3),
-             dTdt=(7, 1), sigma=(8, 1), normal=(9, 3), wall_vel=(10, 3))
+             dTdt=(7, 1), sigma=(8, 1), normal=(9, 3), wall_vel=(10, 3), contact=(11, 1))
 
 
 class OracleSim:

@@ -214,7 +214,7 @@ struct orc_sim {
     int64_t n, cap;
     int *kind, *mat_id, *body_id;
     double *pos, *vel, *rho, *drho, *p, *T, *T0, *mass;
-    double *ref_pos, *ref_nrm, *nrm, *wvel, *av, *dTdt, *acc, *sigma, *snap;
+    double *ref_pos, *ref_nrm, *nrm, *wvel, *av, *dTdt, *acc, *sigma, *snap, *contact;
     int64_t* nb_start;
     int32_t* nb;
     int64_t nb_cap;
@@ -259,7 +259,7 @@ void orc_destroy(orc_sim* S) {
     if (!S) return;
     void* ptrs[] = {S->kind, S->mat_id, S->body_id, S->pos, S->vel, S->rho, S->drho, S->p, S->T,
                     S->T0, S->mass, S->ref_pos, S->ref_nrm, S->nrm, S->wvel, S->av, S->dTdt,
-                    S->acc, S->sigma, S->snap, S->nb_start, S->nb};
+                    S->acc, S->sigma, S->snap, S->contact, S->nb_start, S->nb};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(S);
 }
@@ -289,7 +289,7 @@ static void grow(orc_sim* S, int64_t need) {
     RE(S->p, double, 1); RE(S->T, double, 1); RE(S->T0, double, 1); RE(S->mass, double, 1);
     RE(S->ref_pos, double, 3); RE(S->ref_nrm, double, 3); RE(S->nrm, double, 3);
     RE(S->wvel, double, 3); RE(S->av, double, 3); RE(S->dTdt, double, 1); RE(S->acc, double, 3);
-    RE(S->sigma, double, 1); RE(S->snap, double, 3);
+    RE(S->sigma, double, 1); RE(S->snap, double, 3); RE(S->contact, double, 1);
 #undef RE
     S->cap = c;
 }
@@ -325,6 +325,7 @@ int orc_add_particles(orc_sim* S, int64_t n, const int* kind, const int* mat, co
         S->mass[i] = r0 * S->vol;
         S->dTdt[i] = 0.0;
         S->sigma[i] = 0.0;
+        S->contact[i] = 0.0;
     }
     S->n += n;
     return 0;
@@ -489,6 +490,29 @@ int orc_step(orc_sim* S, int n_adv) {
                 for (int k = 0; k < 3; ++k) F[k] = -S->mass[i] * c * (S->vel[3 * i + k] - S->wvel[3 * j + k]);
                 S->tq_visc[b] += axial_torque(&S->body[b], S->snap + 3 * j, F);
                 for (int k = 0; k < 3; ++k) S->f_visc[b][k] += F[k];
+            }
+        }
+
+        /* ---- contact factor of rigid-body particles (Sec. 2.7) -------- */
+        /* READING: V_j = m_j / rho_j of the lubricant partners at the advection
+         * step (densities after re-initialisation); the fully immersed reference
+         * is the kernel sum over the full lattice of spacing dx around the
+         * particle, the particle itself excluded: dx^3 (sigma0 - W(0)). */
+        {
+            const double full = S->vol * (S->sigma0 - orc_W(0.0, S->h));
+            #pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < n; ++i) {
+                const int b = S->body_id[i];
+                if (S->kind[i] != 1 || b < 0 || !S->body[b].set) { S->contact[i] = 0.0; continue; }
+                double s = 0.0;
+                for (int64_t q = S->nb_start[i]; q < S->nb_start[i + 1]; ++q) {
+                    int64_t j = S->nb[q];
+                    if (S->kind[j] != 0) continue;
+                    double rv[3];
+                    double r2 = dist2(S->snap + 3 * i, S->snap + 3 * j, C->periodic_mask, C->extent, rv);
+                    s += fluid_volume(S, j) * orc_W(sqrt(r2), S->h);
+                }
+                S->contact[i] = s / full;
             }
         }
 
@@ -662,6 +686,7 @@ int orc_get_field(const orc_sim* S, int field, double* out) {
     case 8: memcpy(out, S->sigma, sizeof(double) * (size_t)n); return 0;
     case 9: memcpy(out, S->nrm, sizeof(double) * 3 * (size_t)n); return 0;
     case 10: memcpy(out, S->wvel, sizeof(double) * 3 * (size_t)n); return 0;
+    case 11: memcpy(out, S->contact, sizeof(double) * (size_t)n); return 0;
     default: return -1;
     }
 }

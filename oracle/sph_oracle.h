@@ -77,7 +77,8 @@ int orc_add_particles(orc_sim*, int64_t n, const int* kind, const int* mat, cons
                       const double* T, const double* rho);
 int orc_step(orc_sim*, int n_adv);
 /* fields (id order): 0 pos[3], 1 vel[3], 2 rho, 3 p, 4 T, 5 drho, 6 a_visc[3], 7 dTdt,
- * 8 sigma (kernel sum of pass D), 9 wall normal[3], 10 wall velocity[3] */
+ * 8 sigma (kernel sum of pass D), 9 wall normal[3], 10 wall velocity[3],
+ * 11 contact factor of rigid-body particles (Sec. 2.7; 0 for the others) */
 int orc_get_field(const orc_sim*, int field, double* out);
 /* body: torque about its axis (last sub-step), dt-weighted average since
  * start, heat into fluid sum m cp (T - T0), mean fluid temperature */

@@ -109,7 +109,7 @@ struct HostCase {
 // device bytes per particle slot and per cell of an engine
 constexpr int64_t kBytesPerParticle =
     3 * 8 * 2 /*X,Y*/ + 3 * 8 /*RP*/ + 16 * 2 /*V*/ + 4 * 2 /*DR*/ + 8 * 2 /*T64*/ + 4 * 2 /*ID*/ + 4 * 2 /*TAG*/ +
-    4 /*T32*/ + 16 /*SNAP*/ + 4 /*CELLK*/ + 16 /*AV*/ + 16 /*NRM*/ + 16 /*RN*/ + 4 * 2 /*TORQ*/ + 4 * 4 /*sort*/ +
+    4 /*T32*/ + 16 /*SNAP*/ + 4 /*CELLK*/ + 16 /*AV*/ + 16 /*NRM*/ + 16 /*RN*/ + 4 * 2 /*TORQ*/ + 8 /*CF*/ + 4 * 4 /*sort*/ +
     4 * NB_CAP /*NB*/ + 4 /*NBC*/ + 4 /*OVFL*/ + 16 /*VH*/ + 3 * 8 /*field*/ + 1 /*PART*/;
 constexpr int64_t kBytesPerCell = 4 * 2 + 1;
 
@@ -262,6 +262,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     AL(B.RN, n);
     AL(B.TORQ, n);
     AL(B.TORQV, n);
+    AL(B.CF, n);
     if (B.fp64) {
         for (int p = 0; p < 2; ++p) {
             AL(B.V64[p], n);
@@ -344,6 +345,8 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.kdw = (float)(-5.0 * alpha / h);
     C.w0 = (float)alpha;
     C.inv_sigma0 = (float)(1.0 / c->sigma0);
+    C.inv_contact_full = (float)(1.0 / (F.dx * F.dx * F.dx * (c->sigma0 - alpha)));
+    C.inv_contact_full64 = 1.0 / (F.dx * F.dx * F.dx * (c->sigma0 - alpha));
     C.vol = (float)(F.dx * F.dx * F.dx);
     C.c0 = (float)F.c0;
     C.c02 = (float)(F.c0 * F.c0);
@@ -507,6 +510,7 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     E_CUDA(E, cudaMemcpyAsync(B.RN + idb, rn.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemsetAsync(B.TORQ + idb, 0, sizeof(float) * n, s));
     E_CUDA(E, cudaMemsetAsync(B.TORQV + idb, 0, sizeof(float) * n, s));
+    E_CUDA(E, cudaMemsetAsync(B.CF + idb, 0, sizeof(double) * n, s));
     E_CUDA(E, cudaMemcpyAsync(B.T64[p] + at, c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     std::vector<double4_32a> v64, rn64;
     if (B.fp64) {
@@ -789,7 +793,8 @@ static sph_status read_fields(Engine& E, int slot, int field, void* dst, int64_t
     int k;
     switch (field) {
     case SPH_FIELD_POS: case SPH_FIELD_VEL: case SPH_FIELD_AVISC: case SPH_FIELD_NORMAL: k = 3; break;
-    case SPH_FIELD_RHO: case SPH_FIELD_P: case SPH_FIELD_T: case SPH_FIELD_DRHO: case SPH_FIELD_DTDT: k = 1; break;
+    case SPH_FIELD_RHO: case SPH_FIELD_P: case SPH_FIELD_T: case SPH_FIELD_DRHO: case SPH_FIELD_DTDT:
+    case SPH_FIELD_CONTACT: k = 1; break;
     default: return E.fail(SPH_EINVAL, "unknown field %d", field);
     }
     E_CUDA(E, launch_gather_field(E.B, E.parity ^ 1, field, slot, (int)H.id_base, E.d_field, E.stream));

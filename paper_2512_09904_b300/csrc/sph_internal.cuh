@@ -78,12 +78,14 @@ struct CaseDev {
     float R2lo, R2hi, R2eps;      // FP32 guard band around the rule
     float h, inv_h, w0, kw, kdw;  // W(0), alpha, -5 alpha / h
     float inv_sigma0, vol;
+    float inv_contact_full;  // 1 / (dx^3 (sigma0 - W(0))): the fully immersed kernel volume sum
     float c0, c02, inv_c0, inv_c02;
     float g[3];
     double h64, c0_64, u_ref, cfl_ad, cfl_ac, nu_max;
     double T_ref;
     // FP64 copies of the constants above (pair arithmetic in FP64)
     double kw64, kdw64, w0_64, inv_sigma0_64, vol64, c02_64, inv_c0_64, inv_c02_64, g64[3];
+    double inv_contact_full64;
     int free_surface, kcap, n_body, fp64;
     MatDev mat[MAX_MAT];
     MatDev64 mat64[MAX_MAT];

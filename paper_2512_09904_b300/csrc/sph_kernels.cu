@@ -668,7 +668,7 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     const bool thermal = !Mi.fixed_T;
     const bool rot = kind == KIND_ROT;
     const float4 vw = V[i];
-    float dT = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    float dT = 0.f, fx = 0.f, fy = 0.f, fz = 0.f, cf = 0.f;
     vis.template run<PART_ALL>([&](int j, float4 sj, float, float, float, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
@@ -690,21 +690,26 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
         if (rot && fj) {
             // force of fluid j on this wall particle: -m_j a_jw, with
             // a_jw = 2 V_w / rho_j mu_j (v_j - v_w) / r dW/dr
-            const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * Mj.mu * inv_r * dW;
-            fx = fmaf(cf, vj.x - vw.x, fx);
-            fy = fmaf(cf, vj.y - vw.y, fy);
-            fz = fmaf(cf, vj.z - vw.z, fz);
+            const float c = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * Mj.mu * inv_r * dW;
+            fx = fmaf(c, vj.x - vw.x, fx);
+            fy = fmaf(c, vj.y - vw.y, fy);
+            fz = fmaf(c, vj.z - vw.z, fz);
+            // contact factor (Eq. 24): lubricant volume weighted by W
+            cf = fmaf(Vj, kernel_W(C, r2 * inv_r), cf);
         }
     });
     dT = vis.sum(dT);
     fx = vis.sum(fx);
     fy = vis.sum(fy);
     fz = vis.sum(fz);
+    cf = vis.sum(cf);
     if (!vis.lead()) return;
     B.AV[i] = make_float4(0.f, 0.f, 0.f, thermal ? dT * Mi.inv_rho0_cp : 0.f);
     if (rot) {
         const BodyDev& Bd = C.body[tag_body(tag)];
-        B.TORQV[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
+        const int id = B.ID[1 - par][i];
+        B.TORQV[id] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
+        B.CF[id] = (double)(cf * C.inv_contact_full);
     }
 }
 
@@ -1164,6 +1169,7 @@ __global__ void k_gather_field(Bufs B, int par, int field, int cs, int id_base, 
             break;
         }
         case 7: out[id] = C.fp64 ? B.AV64[i].w : (double)B.AV[i].w; break;
+        case 11: out[id] = tag_kind(tag) == KIND_ROT ? B.CF[gid] : 0.0; break;
         case 9:
             out[3 * (size_t)id + 0] = fluid ? 0.0 : sn[0];
             out[3 * (size_t)id + 1] = fluid ? 0.0 : sn[1];

@@ -33,6 +33,7 @@ struct Bufs {
     float4* RN;
     float* TORQ;
     float* TORQV;
+    double* CF;     // per-id contact factor of rigid-body particles (Eq. 24), last advection step
     uint32_t *KEYS, *RANK, *TMP, *PERM, *CNT, *CSTART, *SCANBLK;
     double* PART;
     int* CHUNK_CASE;

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(128) k_passVT64(Bufs B, int par) {
     const bool thermal = !C.mat[tag_mat(tag)].fixed_T;
     const bool rot = kind == KIND_ROT;
     const double4_32a vw = V[i];
-    double dT = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    double dT = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, cf = 0.0;
     visit64<P_ALL>(C, B, i, [&](int j, uint32_t tj, double, double, double, double r2) {
         const double r = sqrt(r2), inv_r = 1.0 / r;
         const double dW = dW64(C, r);
@@ -197,14 +197,19 @@ __global__ void __launch_bounds__(128) k_passVT64(Bufs B, int par) {
         }
         if (thermal) dT += Vj * 2.0 * harm2(Mi.k, Mj.k) * (Ti - T[j]) * inv_r * dW;
         if (rot && fj) {
-            const double cf = -Mj.mass * (2.0 * C.vol64 / rho_j) * Mj.mu * inv_r * dW;
-            fx += cf * (vj.x - vw.x);
-            fy += cf * (vj.y - vw.y);
-            fz += cf * (vj.z - vw.z);
+            const double c = -Mj.mass * (2.0 * C.vol64 / rho_j) * Mj.mu * inv_r * dW;
+            fx += c * (vj.x - vw.x);
+            fy += c * (vj.y - vw.y);
+            fz += c * (vj.z - vw.z);
+            cf += Vj * W64(C, r);  // contact factor (Eq. 24)
         }
     });
     B.AV64[i] = make_double4_32a(0.0, 0.0, 0.0, thermal ? dT * Mi.inv_rho0_cp : 0.0);
-    if (rot) B.TORQV64[B.ID[cur][i]] = axial_torque64(C.body[tag_body(tag)], B, i, fx, fy, fz);
+    if (rot) {
+        const int id = B.ID[cur][i];
+        B.TORQV64[id] = axial_torque64(C.body[tag_body(tag)], B, i, fx, fy, fz);
+        B.CF[id] = cf * C.inv_contact_full64;
+    }
 }
 
 // Half kick of density for the sub-step into VH64 (input of pass M).

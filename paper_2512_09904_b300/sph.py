@@ -26,7 +26,7 @@ STATUS = {0: "SPH_OK", -1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: 
 TUNE = dict(list_batch=0, tpp=1, block=2)
 PROF_CLASSES = ("sort", "pass_D", "pass_VT", "pass_M", "pass_C", "control", "adv_end", "idle")
 FIELDS = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1), a_visc=(6, 3),
-              dTdt=(7, 1), normal=(9, 3))
+              dTdt=(7, 1), normal=(9, 3), contact=(11, 1))
 
 
 class sph_config(C.Structure):

@@ -281,6 +281,34 @@ def mini_gear_bath(omega=300.0, dx=1.5e-3, depth_frac=0.5, mu=0.1, seed=9):
                      gear=dict(r_pitch=GEAR["r_pitch"] / 5, face=GEAR["face"] / 5))
 
 
+def contact_probe(fill="full", rho_factor=1.0, dx=1e-3, n=9):
+    """One rigid-body particle at the centre lattice point of an n^3 oil
+    lattice block, at rest, no gravity.  fill selects the oil around it:
+    'full' (every other lattice point), 'above' / 'below' (lattice points with
+    z above / below the particle's), 'plane' (its own z plane), 'none'.  The
+    oil density is rho_factor x rho0 everywhere."""
+    idx = _grid((0, 0, 0), (n, n, n))
+    c = n // 2
+    sel = np.any(idx != c, axis=1)
+    if fill == "above":
+        sel &= idx[:, 2] > c
+    elif fill == "below":
+        sel &= idx[:, 2] < c
+    elif fill == "plane":
+        sel &= idx[:, 2] == c
+    elif fill == "none":
+        sel &= False
+    fpos = (idx[sel] + 0.5) * dx
+    rho0 = 900.0
+    cfg = _cfg(origin=(-2 * dx,) * 3, extent=((n + 4) * dx,) * 3, dx=dx, gravity=(0, 0, 0), c0=10.0)
+    mats = {0: _mat(rho0, 0.05, 0.15, 2000.0, 300.0), 1: _mat(7850.0, 0.0, 0.0, 460.0, 300.0, fixed_T=1)}
+    center = (np.array([c, c, c]) + 0.5) * dx
+    fluids = [dict(mat=0, pos=fpos, vel=None, T=None, rho=np.full(len(fpos), rho_factor * rho0))] if len(fpos) else []
+    solids = [dict(body=0, mat=1, pos=center[None, :], normal=np.array([[0.0, 0.0, 1.0]]), T=None)]
+    bodies = {0: dict(center=list(center + np.array([0.0, 0.0, -5 * dx])), axis=[0.0, 1.0, 0.0], omega=0.0)}
+    return Case("contact_probe", cfg, mats, fluids, solids, bodies)
+
+
 # --------------------------------------------------------------------------
 # Two-material slab of the conduction validation (Sec. 3.2, Table 3):
 # x in [0,1], interface x=0.5, T=0 left / 1 right; periodic in y and z.

@@ -141,3 +141,15 @@ def test_fp64_still_tank_full_200_steps(sph, oracle):
     for f, e in err.items():
         assert e <= 1e-11, (f, e)
     ctx.close()
+
+
+def test_fp64_contact_factor(sph, oracle):
+    case = _fp64(W.gear_bath(dx=5e-3, omega=600.0))
+    ctx = sph.from_case(case, stream=0)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(2)
+    sim.step(2)
+    g, r = ctx.sph_read_fields("contact"), sim.field("contact")
+    assert np.max(r) > 0.0
+    assert np.max(np.abs(g - r)) <= 1e-12
+    ctx.close()

@@ -171,3 +171,21 @@ def test_rotating_cylinder_torque_heat_parity(sph, oracle):
     assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=1e-3)
     assert g["heat"] == pytest.approx(r["heat"], rel=1e-3)
     assert g["mean_T"] == pytest.approx(r["mean_T"], rel=1e-9)
+
+
+# --------------------------------------------------------- contact factor ---
+@pytest.mark.parametrize("name,make", [
+    ("contact_probe", lambda: W.contact_probe(fill="above")),
+    ("rotating_cylinder", lambda: W.rotating_cylinder()),
+    ("gear_bath_coarse", lambda: W.gear_bath(dx=5e-3, omega=600.0)),
+])
+def test_contact_factor_parity(sph, oracle, name, make):
+    # contact factor of every rigid-body particle (Eq. 24) after 2 advection steps
+    case = make()
+    ctx = _ctx(sph, case)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(2)
+    sim.step(2)
+    g, r = ctx.sph_read_fields("contact"), sim.field("contact")
+    assert np.max(r) > 0.0
+    assert np.max(np.abs(g - r)) <= 1e-5 * 2, (name, float(np.max(np.abs(g - r))))

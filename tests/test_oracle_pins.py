@@ -378,3 +378,33 @@ def test_rotating_cylinder_drag_opposes_rotation(oracle):
         # fluid near the wall moves with the wall: positive angular velocity sense
         lz = p[:, 0] * v[:, 1] - p[:, 1] * v[:, 0]
         assert lz.sum() * omega > 0.0
+
+
+# ---------------------------------------------------- contact factor ---
+def _contact(oracle, **kw):
+    case = W.contact_probe(**kw)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    return float(sim.field("contact")[-1])  # the probe particle is the last id
+
+
+def test_contact_factor_full_immersion_is_one(oracle):
+    # every lattice point of the support around the particle holds oil at rho0:
+    # the sum equals its fully immersed reference
+    assert _contact(oracle, fill="full") == pytest.approx(1.0, rel=1e-12)
+
+
+def test_contact_factor_half_spaces_mirror_and_add_up(oracle):
+    up, down, plane = (_contact(oracle, fill=f) for f in ("above", "below", "plane"))
+    assert up == pytest.approx(down, rel=1e-12)          # mirror symmetry in z
+    assert up + down + plane == pytest.approx(1.0, rel=1e-12)  # the parts cover the full support
+    assert 0.0 < up < 0.5 and 0.0 < plane < 1.0  # each half space holds less than half
+
+
+def test_contact_factor_scales_with_partner_volume(oracle):
+    # V_j = m_j / rho_j: oil 10% denser everywhere fills 10% less volume
+    assert _contact(oracle, fill="full", rho_factor=1.1) == pytest.approx(1.0 / 1.1, rel=1e-12)
+
+
+def test_contact_factor_dry(oracle):
+    assert _contact(oracle, fill="none") == 0.0
