@@ -272,14 +272,8 @@ def main():
     rctx.close()
     del rctx
 
-    if world > 1:
-        t = torch.tensor([ms, float(units)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, units_all = float(tmax[0]), float(t[1])
-    else:
-        ms_max, units_all = ms, float(units)
+    from paper_2512_09904_b300.shard import reduce_timing
+    ms_max, units_all = reduce_timing(ms, units, world, device="cuda")
     value = units_all / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (largest share of device time)

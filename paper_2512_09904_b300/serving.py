@@ -2,6 +2,7 @@
 
     python -m paper_2512_09904_b300.serving sweep [--cases 64] [--steps 50] [--count-scale 1.0]
     python -m paper_2512_09904_b300.serving serve [--requests 64] [--steps 200] [--rate 4] ...
+    torchrun --nproc-per-node N -m paper_2512_09904_b300.serving sweep-sharded [--cases 64] [--steps 50]
 
 Sweep: the paper's parametric study (shaft speed x immersion depth x oil
 viscosity, Sec. 4) as 64 gear-bath cases of uneven size packed by case id in
@@ -106,6 +107,43 @@ def sweep(n_cases=64, steps=50, count_scale=1.0, seed=4, sequential=True):
         out["max_abs_diff_torque_avg"] = max(abs(a["torque_avg"] - s["torque_avg"]) for a, s in zip(res_b, res_s))
         out["max_abs_diff_heat"] = max(abs(a["heat"] - s["heat"]) for a, s in zip(res_b, res_s))
     return out
+
+
+def sweep_sharded(n_cases=64, steps=50, count_scale=1.0, seed=4):
+    """The sweep over the ranks of one node (torchrun, one GPU per rank):
+    whole cases assigned by particle count, each rank batches its share, the
+    per-case torque / heat results are gathered on rank 0 (host objects)."""
+    import os
+    import torch
+    import torch.distributed as dist
+    from . import shard
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    reqs = W.sweep_cases(n_cases, seed=seed, count_scale=count_scale)
+    cases = [_case(r) for r in reqs]
+    owner = shard.assign_cases([c.n_total for c in cases], world)
+    mine = [i for i in range(n_cases) if owner[i] == rank]
+    local = {}
+    t0 = time.perf_counter()
+    if mine:
+        cap = int(sum(cases[i].n_total for i in mine))
+        cells = int(sum(sph.cells_of(cases[i]) for i in mine)) + 16
+        b = sph.Batch(cap, len(mine), cells, history_steps=steps)
+        slots = {i: b.admit(cases[i], steps) for i in mine}
+        b.step(steps)
+        for i, s in slots.items():
+            th = b.torque_heat(s)
+            local[i] = dict(torque_avg=th["torque_avg"], heat=th["heat"], mean_T=th["mean_T"])
+        b.close()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    sec_max, _ = shard.reduce_timing(sec, 0.0, world, device="cuda")
+    res = shard.gather_results(local, rank, world)
+    if rank != 0:
+        return None
+    return dict(mode="sweep_sharded", ranks=world, cases=n_cases, steps=steps, seconds=sec_max,
+                cases_per_h=n_cases / sec_max * 3600.0, results=[res[i] for i in range(n_cases)])
 
 
 # ---------------------------------------------------------------- serving ---
@@ -227,7 +265,7 @@ def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["sweep", "serve"])
+    ap.add_argument("mode", choices=["sweep", "serve", "sweep-sharded"])
     ap.add_argument("--cases", type=int, default=64)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--steps", type=int, default=0)
@@ -237,7 +275,20 @@ def main(argv=None):
     ap.add_argument("--no-sequential", action="store_true")
     ap.add_argument("--max-cases", type=int, default=64)
     a = ap.parse_args(argv)
+    import os
     import torch
+    if a.mode == "sweep-sharded":
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        r = sweep_sharded(a.cases, a.steps or 50, a.count_scale or 1.0)
+        if r is not None:
+            print(json.dumps(r), flush=True)
+        if dist.is_initialized():
+            dist.destroy_process_group()
+        return
     torch.cuda.set_device(0)
     if a.mode == "sweep":
         r = sweep(a.cases, a.steps or 50, a.count_scale or 1.0, sequential=not a.no_sequential)
