@@ -50,6 +50,8 @@ def lib():
         L.orc_dt_thermal.restype = D; L.orc_dt_thermal.argtypes = [D, D, D, D]
         L.orc_neighbors.restype = I64
         L.orc_neighbors.argtypes = [I64, PD, D, C.c_int, PD, PI64, PI32, I64]
+        L.orc_neighbors_of.restype = I64
+        L.orc_neighbors_of.argtypes = [I64, PD, D, C.c_int, PD, I64, PI64, PI64, PI32, I64]
         L.orc_cell_order.argtypes = [I64, PD, PD, PD, PI, PI64, PI64]
         L.orc_create.restype = C.c_void_p; L.orc_create.argtypes = [C.POINTER(OrcConfig)]
         L.orc_destroy.argtypes = [C.c_void_p]
@@ -122,6 +124,23 @@ def neighbors(pos, R2, periodic_mask=0, extent=(0, 0, 0)):
     lst = np.zeros(max(total, 1), np.int32)
     got = lib().orc_neighbors(n, _pd(pos), float(R2), int(periodic_mask), _pd(ext),
                               counts.ctypes.data_as(PI64), lst.ctypes.data_as(PI32), total)
+    assert got == total
+    return counts, lst[:total]
+
+
+def neighbors_of(pos, R2, idx, periodic_mask=0, extent=(0, 0, 0)):
+    """Brute-force neighbour sets of the particles idx only: (counts[m], list)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    idx = np.ascontiguousarray(idx, np.int64)
+    n, m = len(pos), len(idx)
+    ext = np.ascontiguousarray(extent, np.float64)
+    counts = np.zeros(m, np.int64)
+    total = lib().orc_neighbors_of(n, _pd(pos), float(R2), int(periodic_mask), _pd(ext), m,
+                                   idx.ctypes.data_as(PI64), counts.ctypes.data_as(PI64), None, 0)
+    lst = np.zeros(max(total, 1), np.int32)
+    got = lib().orc_neighbors_of(n, _pd(pos), float(R2), int(periodic_mask), _pd(ext), m,
+                                 idx.ctypes.data_as(PI64), counts.ctypes.data_as(PI64),
+                                 lst.ctypes.data_as(PI32), total)
     assert got == total
     return counts, lst[:total]
 

@@ -176,6 +176,44 @@ int64_t orc_neighbors(int64_t n, const double* pos, double R2, int periodic_mask
     return total;
 }
 
+/* Brute-force neighbour sets of the m particles idx[] only (same rule as
+ * orc_neighbors): for checking a large case on a sample of its particles. */
+int64_t orc_neighbors_of(int64_t n, const double* pos, double R2, int periodic_mask, const double* extent,
+                         int64_t m, const int64_t* idx, int64_t* counts, int32_t* list, int64_t cap) {
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        int64_t c = 0;
+        double v[3];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r2 = dist2(pos + 3 * i, pos + 3 * j, periodic_mask, extent, v);
+            if (r2 > 0.0 && r2 < R2) ++c;
+        }
+        counts[q] = c;
+    }
+    int64_t total = 0;
+    for (int64_t q = 0; q < m; ++q) total += counts[q];
+    if (!list) return total;
+    if (total > cap) return -1;
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    start[0] = 0;
+    for (int64_t q = 0; q < m; ++q) start[q + 1] = start[q] + counts[q];
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        int64_t c = start[q];
+        double v[3];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r2 = dist2(pos + 3 * i, pos + 3 * j, periodic_mask, extent, v);
+            if (r2 > 0.0 && r2 < R2) list[c++] = (int32_t)j;
+        }
+    }
+    free(start);
+    return total;
+}
+
 void orc_cell_order(int64_t n, const double* pos, const double* origin, const double* cellw,
                     const int* ncell, int64_t* perm, int64_t* cell_start) {
     int64_t nc = (int64_t)ncell[0] * ncell[1] * ncell[2];

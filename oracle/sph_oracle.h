@@ -57,6 +57,8 @@ double orc_dt_thermal(double rho, double cp, double h, double k);
  * minimum image on periodic axes.  counts[i] = neighbours of i; if list is
  * non-NULL it receives, for each i in order, its neighbours in ascending j.
  * Returns total pair entries, or -1 if cap is too small. */
+int64_t orc_neighbors_of(int64_t n, const double* pos, double R2, int periodic_mask, const double* extent,
+                         int64_t m, const int64_t* idx, int64_t* counts, int32_t* list, int64_t cap);
 int64_t orc_neighbors(int64_t n, const double* pos, double R2, int periodic_mask,
                       const double* extent, int64_t* counts, int32_t* list, int64_t cap);
 /* expected cell order: key = linear cell index (x fastest) of

@@ -408,3 +408,20 @@ def test_contact_factor_scales_with_partner_volume(oracle):
 
 def test_contact_factor_dry(oracle):
     assert _contact(oracle, fill="none") == 0.0
+
+
+def test_neighbors_of_sample_matches_kdtree(oracle):
+    # the sampled brute-force search agrees with an independent k-d tree query
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(11)
+    pos = rng.random((3000, 3))
+    R = 0.09
+    idx = rng.choice(len(pos), 64, replace=False)
+    counts, lst = oracle.neighbors_of(pos, R * R, idx)
+    tree = cKDTree(pos)
+    off = 0
+    for q, i in enumerate(idx):
+        ref = sorted(j for j in tree.query_ball_point(pos[i], R) if j != i and np.sum((pos[j] - pos[i]) ** 2) < R * R)
+        assert counts[q] == len(ref)
+        assert list(lst[off:off + counts[q]]) == ref
+        off += counts[q]
