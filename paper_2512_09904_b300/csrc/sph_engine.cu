@@ -322,6 +322,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.origin[a] = F.origin[a];
         C.ext[a] = F.extent[a];
         C.cellw[a] = c->cellw[a];
+        C.inv_cellw[a] = 1.0 / c->cellw[a];
         C.gcellw[a] = 2.0 * c->cellw[a];
         C.gcellwf[a] = (float)C.gcellw[a];
         C.scellwf[a] = (float)c->cellw[a];

@@ -68,7 +68,7 @@ struct BodyDev {
 // to whose corners the FP32 snapshot offsets refer; a partner's geometry
 // cell is within one of the particle's on every axis.
 struct CaseDev {
-    double origin[3], ext[3], cellw[3], gcellw[3];
+    double origin[3], ext[3], cellw[3], gcellw[3], inv_cellw[3];
     float gcellwf[3], scellwf[3], inv_scellwf[3];
     float Rmargin;  // slack on the search sphere (FP32 rounding of the clipping)
     int ncell[3];

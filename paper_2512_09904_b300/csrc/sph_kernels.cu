@@ -195,7 +195,13 @@ __device__ __forceinline__ uint32_t cell_key(const CaseDev& C, const double p[3]
     int cc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double f = floor((p[a] - C.origin[a]) / C.cellw[a]);
+        // floor((p - o) / w) in FP64: the product with 1/w is within a few ulp
+        // of the quotient, so it decides unless it lies within 1e-9 of an
+        // integer; there the division itself is taken
+        const double d = p[a] - C.origin[a];
+        double q = d * C.inv_cellw[a];
+        if (fabs(q - rint(q)) < 1e-9 * fmax(1.0, fabs(q))) q = d / C.cellw[a];
+        double f = floor(q);
         double top = (double)(C.ncell[a] - 1);
         if (!(f >= 0.0)) {
             f = 0.0;
@@ -1031,18 +1037,24 @@ __global__ void __launch_bounds__(256) k_reduce_chunks(Bufs B, int cur) {
     }
 }
 
-__global__ void k_reduce_cases(Bufs B) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= B.ncases) return;
+// one block per case: the case's chunk partials in a fixed order (thread t
+// takes chunks t, t + 256, ..., then a fixed tree)
+__global__ void __launch_bounds__(256) k_reduce_cases(Bufs B) {
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
     CaseState& S = B.st[c];
+    const bool live = S.running && S.alive;
     double a = 0.0, b = 0.0, m = 0.0;
-    for (int k = 0; k < S.nchunks; ++k) {
+    for (int k = threadIdx.x; k < S.nchunks; k += 256) {
         const int q = S.chunk_lo + k;
         a += B.PART[3 * q + 0];
         b += B.PART[3 * q + 1];
         m += B.PART[3 * q + 2];
     }
-    if (!S.running || !S.alive) return;
+    a = block_sum_256(a, sh);
+    b = block_sum_256(b, sh);
+    m = block_sum_256(m, sh);
+    if (threadIdx.x != 0 || !live) return;
     S.heat = a - S.heat0;
     S.sum_mcpT = a;
     S.sum_mT = b;
@@ -1424,7 +1436,7 @@ cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s) {
 cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s) {
     int g = B.max_chunks_used < g_grid_cap ? B.max_chunks_used : g_grid_cap;
     k_reduce_chunks<<<g < 1 ? 1 : g, 256, 0, s>>>(B, 1 - par);
-    k_reduce_cases<<<(B.ncases + 63) / 64, 64, 0, s>>>(B);
+    k_reduce_cases<<<B.ncases, 256, 0, s>>>(B);
     return cudaGetLastError();
 }
 
