@@ -175,18 +175,18 @@ def dam_break(dx=2e-3, seed=2, jitter=0.01, layers=3, rho0=870.0, mu=0.05, g=9.8
 GEAR = dict(r_pitch=0.050, teeth=24, face=0.020, pressure_angle_deg=20.0)
 
 
-def _gear_inside(px, pz, r_p, z_teeth, pa):
+def _gear_inside(px, pz, r_p, z_teeth, pa, phase=0.0):
     """Inside test of a spur gear with straight-flanked (trapezoidal) teeth.
 
     px, pz: coordinates in the gear plane relative to the axis.  Module
     m = 2 r_p / z; tip radius r_p + m; root radius r_p - 1.25 m; the tooth
     half-thickness is pi m / 4 at the pitch circle and narrows with the
-    pressure angle.
+    pressure angle.  Teeth are centred at angles phase + k 2 pi / z.
     """
     m = 2.0 * r_p / z_teeth
     r_a, r_f = r_p + m, r_p - 1.25 * m
     rr = np.hypot(px, pz)
-    phi = np.arctan2(pz, px)
+    phi = np.arctan2(pz, px) - phase
     pitch = 2.0 * math.pi / z_teeth
     dphi = np.abs((phi + 0.5 * pitch) % pitch - 0.5 * pitch)
     half = math.pi * m / 4.0 - (rr - r_p) * math.tan(math.radians(pa))
@@ -203,8 +203,6 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     gear properties follow the paper's property table (Table 6).  `gear`
     overrides r_pitch / teeth / face (a geometrically similar smaller case).
     """
-    from scipy import ndimage
-
     rng = np.random.default_rng(seed)
     G = dict(GEAR, **(gear or {}))
     r_p, z_t, b = G["r_pitch"], G["teeth"], G["face"]
@@ -216,25 +214,7 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     c = np.array([Lx / 2, Ly / 2, Lz / 2])
     z_fill = (c[2] - r_a) + depth_frac * 2.0 * r_a
 
-    # gear voxels on the particle lattice (bounding box of the gear)
-    lo = np.floor((c - np.array([r_a, b / 2, r_a])) / dx).astype(int) - 2
-    hi = np.ceil((c + np.array([r_a, b / 2, r_a])) / dx).astype(int) + 3
-    lo = np.maximum(lo, 0)
-    hi = np.minimum(hi, n)
-    shape = tuple(hi - lo)
-    gi = _grid(tuple(lo), tuple(hi))
-    gp = (gi + 0.5) * dx
-    inside = _gear_inside(gp[:, 0] - c[0], gp[:, 2] - c[2], r_p, z_t, G["pressure_angle_deg"])
-    inside &= np.abs(gp[:, 1] - c[1]) <= b / 2
-    vol = inside.reshape(shape[2], shape[1], shape[0])  # (k, j, i)
-    depth_in = ndimage.distance_transform_edt(vol)
-    depth_out = ndimage.distance_transform_edt(~vol)
-    sdf = depth_out - depth_in  # >0 outside, <0 inside (lattice units)
-    gz, gy, gx = np.gradient(sdf)
-    keep_vol = vol & (depth_in <= gear_layers)
-    keep = keep_vol.ravel()
-    gpos = gp[keep]
-    gnrm = _unit(np.stack([gx.ravel()[keep], gy.ravel()[keep], gz.ravel()[keep]], axis=1))
+    gpos, gnrm = _gear_shell(c, G, dx, n, gear_layers)
 
     # fluid: lattice points below the fill level outside the gear body
     fidx = _grid((0, 0, 0), (n[0], n[1], int(math.ceil(z_fill / dx))))
@@ -261,6 +241,80 @@ def gear_bath(dx=1e-3, omega=600.0, depth_frac=0.5, mu=0.1, scale=1.5, seed=3, j
     return Case("gear_bath", cfg, mats, fluids, solids, bodies,
                 dict(omega=omega, depth_frac=depth_frac, mu=mu, dx=dx, z_fill=z_fill, r_tip=r_a,
                      seed=seed, scale=scale))
+
+
+def _gear_shell(c, G, dx, n, gear_layers, phase=0.0):
+    """Lattice particles of a gear's outer shell (gear_layers deep) and their
+    normals from the gradient of the lattice signed distance."""
+    from scipy import ndimage
+
+    r_p, z_t, b = G["r_pitch"], G["teeth"], G["face"]
+    r_a = r_p + 2.0 * r_p / z_t
+    lo = np.floor((c - np.array([r_a, b / 2, r_a])) / dx).astype(int) - 2
+    hi = np.ceil((c + np.array([r_a, b / 2, r_a])) / dx).astype(int) + 3
+    lo = np.maximum(lo, 0)
+    hi = np.minimum(hi, n)
+    shape = tuple(hi - lo)
+    gp = (_grid(tuple(lo), tuple(hi)) + 0.5) * dx
+    inside = _gear_inside(gp[:, 0] - c[0], gp[:, 2] - c[2], r_p, z_t, G["pressure_angle_deg"], phase)
+    inside &= np.abs(gp[:, 1] - c[1]) <= b / 2
+    vol = inside.reshape(shape[2], shape[1], shape[0])  # (k, j, i)
+    depth_in = ndimage.distance_transform_edt(vol)
+    sdf = ndimage.distance_transform_edt(~vol) - depth_in  # >0 outside, <0 inside (lattice units)
+    gz, gy, gx = np.gradient(sdf)
+    keep = (vol & (depth_in <= gear_layers)).ravel()
+    return gp[keep], _unit(np.stack([gx.ravel()[keep], gy.ravel()[keep], gz.ravel()[keep]], axis=1))
+
+
+def gear_pair(dx=2.5e-3, omega=300.0, depth_frac=0.5, mu=0.1, seed=13, jitter=0.01, layers=3, gear_layers=3,
+              rho0=968.1, k_oil=0.15, cp_oil=2000.0, T_oil=298.15, T_gear=318.15, g=9.81):
+    """A meshing gear pair in one sump (a two-shaft gear train): driver of 24
+    teeth (pitch radius 30 mm) and follower of 16 teeth (20 mm), module
+    2.5 mm, face 12 mm, axes along y 50 mm apart at the same height; the
+    follower turns at -omega 24/16 with its teeth phased into the driver's
+    gaps on the line of centres.  Oil (Table 6 properties) fills the sump to
+    depth_frac of the driver's tip diameter above its lowest point."""
+    rng = np.random.default_rng(seed)
+    G1 = dict(GEAR, r_pitch=0.030, teeth=24, face=0.012)
+    G2 = dict(GEAR, r_pitch=0.020, teeth=16, face=0.012)
+    ra1 = G1["r_pitch"] * (1 + 2.0 / G1["teeth"])
+    ra2 = G2["r_pitch"] * (1 + 2.0 / G2["teeth"])
+    L = np.array([0.15, 0.03, 0.09])
+    n = [int(round(v / dx)) for v in L]
+    Lx, Ly, Lz = (np.array(n) * dx)
+    c1 = np.array([0.045, Ly / 2, Lz / 2])
+    c2 = c1 + np.array([G1["r_pitch"] + G2["r_pitch"], 0.0, 0.0])
+    pitch2 = 2.0 * math.pi / G2["teeth"]
+    phase2 = math.pi - 0.5 * pitch2  # a follower gap faces the driver's tooth at angle 0
+    p1, n1 = _gear_shell(c1, G1, dx, n, gear_layers)
+    p2, n2 = _gear_shell(c2, G2, dx, n, gear_layers, phase2)
+    z_fill = (c1[2] - ra1) + depth_frac * 2.0 * ra1
+    fidx = _grid((0, 0, 0), (n[0], n[1], int(math.ceil(z_fill / dx))))
+    fpos0 = (fidx + 0.5) * dx
+    fpos0 = fpos0[fpos0[:, 2] < z_fill]
+    in1 = _gear_inside(fpos0[:, 0] - c1[0], fpos0[:, 2] - c1[2], G1["r_pitch"], G1["teeth"],
+                       G1["pressure_angle_deg"]) & (np.abs(fpos0[:, 1] - c1[1]) <= G1["face"] / 2)
+    in2 = _gear_inside(fpos0[:, 0] - c2[0], fpos0[:, 2] - c2[2], G2["r_pitch"], G2["teeth"],
+                       G2["pressure_angle_deg"], phase2) & (np.abs(fpos0[:, 1] - c2[1]) <= G2["face"] / 2)
+    fpos0 = fpos0[~(in1 | in2)]
+    fpos = fpos0 + _jitter(rng, len(fpos0), dx, jitter)
+    omega2 = -omega * G1["teeth"] / G2["teeth"]
+    c0 = 10.0 * max(omega * ra1, abs(omega2) * ra2, math.sqrt(2 * g * z_fill))
+    rho = _hydrostatic_rho(rho0, g, z_fill, fpos[:, 2], c0)
+    widx, inward = _box_walls(n[0], n[1], n[2], layers, lid=True)
+    mats = {0: _mat(rho0, mu, k_oil, cp_oil, T_oil),
+            1: _mat(7850.0, 0.0, 20.0, 460.0, T_gear, fixed_T=1),
+            2: _mat(7850.0, 0.0, 0.0, 460.0, T_oil, fixed_T=1)}
+    cfg = _cfg(origin=(-layers * dx,) * 3, extent=tuple((v + 2 * layers) * dx for v in n),
+               dx=dx, c0=c0, u_ref=c0 / 10.0, gravity=(0, 0, -g))
+    solids = [dict(body=-1, mat=2, pos=(widx + 0.5) * dx, normal=_unit(inward), T=None),
+              dict(body=0, mat=1, pos=p1, normal=n1, T=None),
+              dict(body=1, mat=1, pos=p2, normal=n2, T=None)]
+    fluids = [dict(mat=0, pos=fpos, vel=None, T=None, rho=rho)]
+    bodies = {0: dict(center=c1.tolist(), axis=[0.0, 1.0, 0.0], omega=float(omega)),
+              1: dict(center=c2.tolist(), axis=[0.0, 1.0, 0.0], omega=float(omega2))}
+    return Case("gear_pair", cfg, mats, fluids, solids, bodies,
+                dict(omega=omega, omega2=omega2, dx=dx, z_fill=z_fill, seed=seed))
 
 
 def gear_bath_dx_for(n_fluid_target, depth_frac=0.5, scale=1.5):

@@ -39,6 +39,7 @@ NEIGHBOR_CASES = [
     ("rotating_cylinder", lambda: W.rotating_cylinder()),
     ("gear_bath_coarse", lambda: W.gear_bath(dx=5e-3, omega=600.0)),
     ("slab", lambda: W.slab()),
+    ("gear_pair", lambda: W.gear_pair()),
 ]
 
 
@@ -189,3 +190,20 @@ def test_contact_factor_parity(sph, oracle, name, make):
     g, r = ctx.sph_read_fields("contact"), sim.field("contact")
     assert np.max(r) > 0.0
     assert np.max(np.abs(g - r)) <= 1e-5 * 2, (name, float(np.max(np.abs(g - r))))
+
+
+def test_gear_pair_per_shaft_torque_heat_parity(sph, oracle):
+    # a two-shaft gear train: the torque on each shaft and the heat-up
+    case = W.gear_pair()
+    ctx = _ctx(sph, case)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(10)
+    sim.step(10)
+    for body in (0, 1):
+        g, r = ctx.sph_read_torque_heat(body), sim.torque_heat(body)
+        print(body, g, r)
+        assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=1e-3)
+        assert g["torque"] == pytest.approx(r["torque"], rel=1e-3)
+    assert ctx.sph_read_torque_heat(0)["torque_avg"] < 0.0 < ctx.sph_read_torque_heat(1)["torque_avg"]
+    g, r = ctx.sph_read_torque_heat(0), sim.torque_heat(0)
+    assert g["heat"] == pytest.approx(r["heat"], rel=1e-3)

@@ -425,3 +425,14 @@ def test_neighbors_of_sample_matches_kdtree(oracle):
         assert counts[q] == len(ref)
         assert list(lst[off:off + counts[q]]) == ref
         off += counts[q]
+
+
+def test_gear_pair_drag_opposes_each_shaft(oracle):
+    # two meshing gears turning in opposite senses: the oil's torque on each
+    # shaft opposes that shaft's own rotation
+    case = W.gear_pair(dx=4e-3)
+    assert case.bodies[0]["omega"] > 0 > case.bodies[1]["omega"]
+    sim = oracle.OracleSim(case)
+    sim.step(4)
+    t0, t1 = sim.torque_heat(0)["torque_avg"], sim.torque_heat(1)["torque_avg"]
+    assert t0 < 0.0 < t1
