@@ -65,6 +65,11 @@ typedef struct {
                                     reductions (default); 1: FP64 pair arithmetic and particle
                                     state throughout (the plain FP64 method, for small cases;
                                     not admissible to a batch).  Other values: SPH_EINVAL. */
+    int viscous_heating;         /* 1: add the viscous-dissipation heating Phi = 2 mu S:S to
+                                    dT/dt (S from the SPH velocity gradient over fluid and wall
+                                    partners); an extension: the paper's thermal model omits it
+                                    (Sec. 2.6).  0 (default): the paper's model.  Other values:
+                                    SPH_EINVAL. */
 } sph_config;
 
 /* Material table entry (Sec. 2.6 and the paper's property tables). */

@@ -30,7 +30,8 @@ PI32 = C.POINTER(C.c_int32)
 class OrcConfig(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D),
                 ("gravity", D * 3), ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D),
-                ("free_surface", C.c_int), ("periodic_mask", C.c_int), ("max_substeps", C.c_int)]
+                ("free_surface", C.c_int), ("periodic_mask", C.c_int), ("max_substeps", C.c_int),
+                ("viscous_heating", C.c_int)]
 
 
 class OrcMaterial(C.Structure):
@@ -178,6 +179,7 @@ class OracleSim:
         oc.cfl_ad = cfg["cfl_ad"]; oc.cfl_ac = cfg["cfl_ac"]
         oc.free_surface = cfg["free_surface"]; oc.periodic_mask = cfg["periodic_mask"]
         oc.max_substeps = cfg.get("max_substeps", 0)
+        oc.viscous_heating = cfg.get("viscous_heating", 0)
         self._p = L.orc_create(C.byref(oc))
         for mid, m in case.materials.items():
             om = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])

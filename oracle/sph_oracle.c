@@ -570,6 +570,30 @@ int orc_step(orc_sim* S, int n_adv) {
             }
             double rho_i = S->kind[i] == 0 ? S->rho[i] : Mi->rho0;
             S->dTdt[i] = s / (rho_i * Mi->cp);
+            /* READING (an extension: the paper's thermal model omits it): viscous
+             * dissipation Phi = 2 mu S:S, S the symmetric part of the SPH velocity
+             * gradient sum_j V_j (v_j - v_i) (x) grad_i W_ij over fluid and wall
+             * partners (walls with their no-slip velocity), from the velocities of
+             * the advection step; dT/dt += Phi / (rho c_p). */
+            if (C->viscous_heating && S->kind[i] == 0) {
+                double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                for (int64_t q = S->nb_start[i]; q < S->nb_start[i + 1]; ++q) {
+                    int64_t j = S->nb[q];
+                    double rv[3], r, e[3], dW;
+                    pair_geom(S, i, j, rv, &r, e, &dW);
+                    const double* vj = S->kind[j] == 0 ? S->vel + 3 * j : S->wvel + 3 * j;
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            G[a][b] += fluid_volume(S, j) * (vj[a] - S->vel[3 * i + a]) * e[b] * dW;
+                }
+                double ss = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        const double sab = 0.5 * (G[a][b] + G[b][a]);
+                        ss += sab * sab;
+                    }
+                S->dTdt[i] += 2.0 * Mi->mu * ss / (rho_i * Mi->cp);
+            }
         }
 
         /* ---- acoustic sub-steps ---------------------------------------- */

@@ -32,6 +32,8 @@ typedef struct {
     int free_surface;            /* 1: Eq. (14) max() form; 0: Eq. (15) */
     int periodic_mask;           /* bit a: axis a periodic */
     int max_substeps;            /* acoustic sub-steps cap per advection step; 0 = default */
+    int viscous_heating;         /* 1: add the viscous-dissipation heating 2 mu S:S (not in the
+                                    paper's model, which omits it; default 0) */
 } orc_config;
 
 typedef struct { double rho0, mu, k, cp, T_init; int fixed_T; } orc_material;

@@ -104,6 +104,7 @@ struct HostCase {
     double cellw[3] = {0, 0, 0};
     int64_t steps_req = 0;
     int body_lo[MAX_BODY] = {0, 0, 0, 0}, body_hi[MAX_BODY] = {0, 0, 0, 0};  // rigid-body id ranges
+    bool visc_heat = false;
 };
 
 // device bytes per particle slot and per cell of an engine
@@ -365,6 +366,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.inv_c02_64 = 1.0 / (F.c0 * F.c0);
     for (int a = 0; a < 3; ++a) C.g64[a] = F.gravity[a];
     C.fp64 = F.pair_precision == 1 ? 1 : 0;
+    C.visc_heat = F.viscous_heating ? 1 : 0;
     C.u_ref = F.u_ref;
     C.cfl_ad = F.cfl_ad;
     C.cfl_ac = F.cfl_ac;
@@ -466,6 +468,7 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     }
     CaseDev C;
     build_case(c, H, C);
+    H.visc_heat = C.visc_heat != 0;
     for (int b = 0; b < MAX_BODY; ++b) {
         H.body_lo[b] = C.body[b].set ? C.body[b].id_lo : 0;
         H.body_hi[b] = C.body[b].set ? C.body[b].id_hi : 0;
@@ -568,6 +571,9 @@ static sph_status capture(Engine& E) {
     // particles, not the capacity, so one particle's slots stay close together
     E.B.nb_stride = std::max(E.B.n, 1);
     E.B.max_chunks_used = (int)((E.B.n + RED_CHUNK - 1) / RED_CHUNK) + E.c_cap + 1;
+    E.B.visc_heat = 0;
+    for (const HostCase& H : E.cases)
+        if (H.used && H.visc_heat) E.B.visc_heat = 1;
     {
         // torque chunks of the resident rigid bodies (fixed TQ_CHUNK id blocks from each body's start)
         std::vector<int4> tqc;
@@ -830,7 +836,8 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     *out = nullptr;
     const double h = cfg->h_over_dx * cfg->dx;
     if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
-        !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1))
+        !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1) ||
+        (cfg->viscous_heating != 0 && cfg->viscous_heating != 1))
         return SPH_EINVAL;
     sph_ctx* c = new sph_ctx();
     c->cfg = *cfg;

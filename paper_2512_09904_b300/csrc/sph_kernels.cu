@@ -625,7 +625,11 @@ __device__ __forceinline__ const MatDev& fluid_mat(const CaseDev& C, const MatDe
 // Pass VT for one particle: viscous acceleration (Eq. 10 second term; wall
 // term of Eq. 18), held for the sub-steps, and dT/dt by the Cleary form
 // (Eq. 22).  Rigid-body particles also record the viscous torque on them.
-template <bool UNI, class Vis>
+// VH: also the viscous-dissipation heating Phi = 2 mu S:S (an extension the
+// paper's thermal model omits; per case by its flag), S the symmetric part of
+// the velocity gradient sum_j V_j (v_j - v_i) (x) grad_i W_ij over fluid and
+// wall partners, added to dT/dt as Phi / (rho c_p).
+template <bool UNI, class Vis, bool VH = false>
 __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag,
                                             const CaseDev& C, const Vis& vis) {
     const uint32_t kind = tag_kind(tag);
@@ -637,8 +641,17 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
         const float4 vi = V[i];
         const float rho_i = Mi.rho0 + vi.w;
         float ax = 0.f, ay = 0.f, az = 0.f, dT = 0.f;
+        float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        const bool vh = VH && C.visc_heat;
+        auto grad = [&](float g, float4 vj, float rx, float ry, float rz) {
+            const float dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z}, rr[3] = {rx, ry, rz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) G[a][b] = fmaf(g * dv[a], rr[b], G[a][b]);
+        };
         const float Kii = 2.f * harmonic2(Mi.k, Mi.k), eii = harmonic2(Mi.mu, Mi.mu);
-        vis.template run<PART_FLUID>([&](int j, float4 sj, float, float, float, float r2) {
+        vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
             const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
@@ -650,8 +663,9 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
             az = fmaf(cv, vi.z - vj.z, az);
             const float K = UNI ? Kii : 2.f * harmonic2(Mi.k, Mj.k);
             dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+            if (VH && vh) grad(Vj * dW * inv_r, vj, rx, ry, rz);
         });
-        vis.template run<PART_WALL>([&](int j, float4 sj, float, float, float, float r2) {
+        vis.template run<PART_WALL>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
             const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
@@ -662,7 +676,25 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
             az = fmaf(cv, vi.z - vw.z, az);
             const float K = 2.f * harmonic2(Mi.k, Mj.k);
             dT = fmaf(C.vol * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+            if (VH && vh) grad(C.vol * dW * inv_r, vw, rx, ry, rz);
         });
+        if (VH && vh) {
+            // r_ij = r_i - r_j and grad_i W = W' r_ij / r, so the sums above carry
+            // V_j W' / r (v_j - v_i)_a (r_ij)_b
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) G[a][b] = vis.sum(G[a][b]);
+            float ss = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const float sab = 0.5f * (G[a][b] + G[b][a]);
+                    ss = fmaf(sab, sab, ss);
+                }
+            dT = fmaf(2.f * Mi.mu, ss, dT);  // Phi, divided by rho_i c_p with the conduction sum below
+        }
         ax = vis.sum(ax);
         ay = vis.sum(ay);
         az = vis.sum(az);
@@ -719,7 +751,7 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     }
 }
 
-template <bool UNI, int BATCH, int TPP>
+template <bool UNI, int BATCH, int TPP, bool VH = false>
 __global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
@@ -733,17 +765,17 @@ __global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
     const uint32_t tag = __float_as_uint(si.w);
     if (!B.st[tag_case(tag)].active) return;
     const CaseDev& C = B.cases[tag_case(tag)];
-    vt_particle<UNI>(B, par, i, si, tag, C, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
+    vt_particle<UNI, ListVis<BATCH, TPP>, VH>(B, par, i, si, tag, C, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
 }
 
-template <bool UNI>
+template <bool UNI, bool VH = false>
 __global__ void __launch_bounds__(128) k_passVT_ovf(Bufs B, int par) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < *B.novf; k += gridDim.x * blockDim.x) {
         const int i = B.OVFL[k];
         const float4 si = B.SNAP[i];
         const uint32_t tag = __float_as_uint(si.w);
         const CaseDev& C = B.cases[tag_case(tag)];
-        vt_particle<UNI>(B, par, i, si, tag, C, CellVis{C, B, i, si});
+        vt_particle<UNI, CellVis, VH>(B, par, i, si, tag, C, CellVis{C, B, i, si});
     }
 }
 
@@ -1387,6 +1419,18 @@ cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
 
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
     if (B.fp64) return launch_passVT64(B, par, s);
+    if (B.visc_heat) {
+        // cases with viscous-dissipation heating: one variant (8 entries per load, 1 thread per particle)
+        const int blk = pair_block(B);
+        if (B.uni_fluid) {
+            k_passVT<true, 8, 1, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT_ovf<true, true><<<kOvfGrid, 128, 0, s>>>(B, par);
+        } else {
+            k_passVT<false, 8, 1, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT_ovf<false, true><<<kOvfGrid, 128, 0, s>>>(B, par);
+        }
+        return cudaGetLastError();
+    }
     if (B.uni_fluid) {
         DISPATCH_PASS(k_passVT, true, s, B, par);
         k_passVT_ovf<true><<<kOvfGrid, 128, 0, s>>>(B, par);

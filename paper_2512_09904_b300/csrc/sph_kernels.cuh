@@ -50,6 +50,7 @@ struct Bufs {
     double* TQP;    // chunk partial sums (pressure, viscous)
     int ntq;        // chunks in use
     int uni_fluid;  // every case has a single fluid material
+    int visc_heat;  // some resident case adds viscous-dissipation heating
     int tune_batch; // list entries loaded together per thread in the pair passes (1, 2, 4, 8)
     int tune_tpp;   // threads per particle in the list passes VT, M, C (1 or 2)
     int tune_block; // block size of the pair passes (64, 128, 256)

@@ -153,7 +153,13 @@ __global__ void __launch_bounds__(128) k_passVT64(Bufs B, int par) {
         const double4_32a vi = V[i];
         const double rho_i = Mi.rho0 + vi.w;
         double ax = 0.0, ay = 0.0, az = 0.0, dT = 0.0;
-        visit64<P_FLUID>(C, B, i, [&](int j, uint32_t tj, double, double, double, double r2) {
+        double G[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        auto grad = [&](double g, double4_32a vj, double rx, double ry, double rz) {
+            const double dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z}, rr[3] = {rx, ry, rz};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) G[a][b] += g * dv[a] * rr[b];
+        };
+        visit64<P_FLUID>(C, B, i, [&](int j, uint32_t tj, double rx, double ry, double rz, double r2) {
             const double r = sqrt(r2), inv_r = 1.0 / r;
             const double dW = dW64(C, r);
             const MatDev64& Mj = C.mat64[tag_mat(tj)];
@@ -164,8 +170,9 @@ __global__ void __launch_bounds__(128) k_passVT64(Bufs B, int par) {
             ay += cv * (vi.y - vj.y);
             az += cv * (vi.z - vj.z);
             dT += Vj * 2.0 * harm2(Mi.k, Mj.k) * (Ti - T[j]) * inv_r * dW;
+            if (C.visc_heat) grad(Vj * dW * inv_r, vj, rx, ry, rz);
         });
-        visit64<P_WALL>(C, B, i, [&](int j, uint32_t tj, double, double, double, double r2) {
+        visit64<P_WALL>(C, B, i, [&](int j, uint32_t tj, double rx, double ry, double rz, double r2) {
             const double r = sqrt(r2), inv_r = 1.0 / r;
             const double dW = dW64(C, r);
             const MatDev64& Mj = C.mat64[tag_mat(tj)];
@@ -175,7 +182,17 @@ __global__ void __launch_bounds__(128) k_passVT64(Bufs B, int par) {
             ay += cv * (vi.y - vw.y);
             az += cv * (vi.z - vw.z);
             dT += C.vol64 * 2.0 * harm2(Mi.k, Mj.k) * (Ti - T[j]) * inv_r * dW;
+            if (C.visc_heat) grad(C.vol64 * dW * inv_r, vw, rx, ry, rz);
         });
+        if (C.visc_heat) {  // viscous-dissipation heating Phi = 2 mu S:S (extension)
+            double ss = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const double sab = 0.5 * (G[a][b] + G[b][a]);
+                    ss += sab * sab;
+                }
+            dT += 2.0 * Mi.mu * ss;
+        }
         B.AV64[i] = make_double4_32a(ax / rho_i, ay / rho_i, az / rho_i, dT / (rho_i * Mi.cp));
         return;
     }

@@ -32,7 +32,8 @@ FIELDS = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1
 class sph_config(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D), ("gravity", D * 3),
                 ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D), ("free_surface", C.c_int),
-                ("periodic_mask", C.c_int), ("max_substeps", C.c_int), ("pair_precision", C.c_int)]
+                ("periodic_mask", C.c_int), ("max_substeps", C.c_int), ("pair_precision", C.c_int),
+                ("viscous_heating", C.c_int)]
 
 
 class sph_material(C.Structure):
@@ -169,6 +170,7 @@ def config_from_dict(cfg: dict) -> sph_config:
     c.periodic_mask = cfg["periodic_mask"]
     c.max_substeps = cfg.get("max_substeps", 0)
     c.pair_precision = cfg.get("pair_precision", 0)
+    c.viscous_heating = cfg.get("viscous_heating", 0)
     return c
 
 

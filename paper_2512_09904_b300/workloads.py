@@ -363,6 +363,30 @@ def contact_probe(fill="full", rho_factor=1.0, dx=1e-3, n=9):
     return Case("contact_probe", cfg, mats, fluids, solids, bodies)
 
 
+def flow_block(field="shear", rate=20.0, n=14, dx=1e-3, viscous_heating=1, mu=0.1, seed=None):
+    """An n^3 oil lattice with a prescribed velocity field and uniform
+    temperature, no gravity, no walls: 'shear' v = (rate z, 0, 0), 'rotation'
+    v = rate e_z x r (rigid), 'translation' v = (rate dx, 0, 0) per unit time.
+    For the viscous-dissipation term: its interior particles see a complete
+    kernel support."""
+    idx = _grid((0, 0, 0), (n, n, n))
+    pos = (idx + 0.5) * dx
+    c = 0.5 * n * dx
+    vel = np.zeros_like(pos)
+    if field == "shear":
+        vel[:, 0] = rate * (pos[:, 2] - c)
+    elif field == "rotation":
+        vel[:, 0] = -rate * (pos[:, 1] - c)
+        vel[:, 1] = rate * (pos[:, 0] - c)
+    elif field == "translation":
+        vel[:, 0] = rate * dx
+    cfg = _cfg(origin=(-2 * dx,) * 3, extent=((n + 4) * dx,) * 3, dx=dx, gravity=(0, 0, 0), c0=10.0)
+    cfg["viscous_heating"] = int(viscous_heating)
+    mats = {0: _mat(900.0, mu, 0.0, 2000.0, 300.0)}
+    fluids = [dict(mat=0, pos=pos, vel=vel, T=None, rho=None)]
+    return Case("flow_block", cfg, mats, fluids, [], {}, dict(rate=rate, field=field))
+
+
 # --------------------------------------------------------------------------
 # Two-material slab of the conduction validation (Sec. 3.2, Table 3):
 # x in [0,1], interface x=0.5, T=0 left / 1 right; periodic in y and z.

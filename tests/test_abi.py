@@ -69,6 +69,9 @@ def test_create_validates_config(sphlib):
         sphlib.Context(bad, stream=0)
     # pair precision: 0 (FP32 pairs) or 1 (FP64 throughout)
     sphlib.Context(dict(cfg, pair_precision=1), stream=0).close()
+    sphlib.Context(dict(cfg, viscous_heating=1), stream=0).close()
+    with pytest.raises(sphlib.SphError):
+        sphlib.Context(dict(cfg, viscous_heating=2), stream=0)
     with pytest.raises(sphlib.SphError) as e:
         sphlib.Context(dict(cfg, pair_precision=2), stream=0)
     assert e.value.status == sphlib.SPH_EINVAL

@@ -153,3 +153,15 @@ def test_fp64_contact_factor(sph, oracle):
     assert np.max(r) > 0.0
     assert np.max(np.abs(g - r)) <= 1e-12
     ctx.close()
+
+
+def test_fp64_viscous_heating(sph, oracle):
+    case = _fp64(W.flow_block("shear"))
+    ctx = sph.from_case(case, stream=0)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(2)
+    sim.step(2)
+    g, r = ctx.sph_read_fields("dTdt"), sim.field("dTdt")
+    assert np.max(r) > 0.0
+    assert np.max(np.abs(g - r)) <= 1e-12 * np.max(np.abs(r))
+    ctx.close()

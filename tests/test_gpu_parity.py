@@ -207,3 +207,32 @@ def test_gear_pair_per_shaft_torque_heat_parity(sph, oracle):
     assert ctx.sph_read_torque_heat(0)["torque_avg"] < 0.0 < ctx.sph_read_torque_heat(1)["torque_avg"]
     g, r = ctx.sph_read_torque_heat(0), sim.torque_heat(0)
     assert g["heat"] == pytest.approx(r["heat"], rel=1e-3)
+
+
+# ---------------------------------------- viscous-dissipation heating ---
+def _with_heating(case):
+    case.config = dict(case.config, viscous_heating=1)
+    return case
+
+
+@pytest.mark.parametrize("name,make", [
+    ("flow_block_shear", lambda: W.flow_block("shear")),
+    ("rotating_cylinder", lambda: _with_heating(W.rotating_cylinder())),
+])
+def test_viscous_heating_parity(sph, oracle, name, make):
+    # dT/dt of the first advection step (conduction + Phi / (rho c_p)), then
+    # temperatures after 3 steps
+    case = make()
+    ctx = _ctx(sph, case)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(1)
+    sim.step(1)
+    fl = W.flatten(case)["kind"] == 0
+    g, r = ctx.sph_read_fields("dTdt")[fl], sim.field("dTdt")[fl]
+    scale = max(float(np.max(np.abs(r))), 1e-30)
+    assert float(np.max(np.abs(g - r))) <= 1e-4 * scale, name
+    ctx.sph_step(2)
+    sim.step(2)
+    gT, rT = ctx.sph_read_fields("T")[fl], sim.field("T")[fl]
+    rise = max(float(np.max(np.abs(rT - W.flatten(case)["T"][fl]))), 1e-30)
+    assert float(np.max(np.abs(gT - rT))) <= 1e-4 * rise + 1e-9, name

@@ -436,3 +436,44 @@ def test_gear_pair_drag_opposes_each_shaft(oracle):
     sim.step(4)
     t0, t1 = sim.torque_heat(0)["torque_avg"], sim.torque_heat(1)["torque_avg"]
     assert t0 < 0.0 < t1
+
+
+# ------------------------------------------- viscous-dissipation heating ---
+def _phi(oracle, field, on=1):
+    case = W.flow_block(field, viscous_heating=on)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    pos = W.flatten(case)["pos"]
+    dx, n, R = case.config["dx"], 14, case.support_radius()
+    inner = np.all((pos > 2 * dx + R) & (pos < n * dx - 2 * dx - R), axis=1)
+    m = case.materials[0]
+    return sim.field("dTdt")[inner] * m["rho0"] * m["cp"], case
+
+
+def test_viscous_heating_simple_shear(oracle):
+    # v = (g z, 0, 0): S_xz = S_zx = g M / 2, so Phi = 2 mu S:S = mu g^2 M^2 with
+    # M = -(dx^3 / 3) sum over the lattice of r W'(r), the lattice's first
+    # moment of the kernel gradient (1 for the continuous kernel)
+    phi, case = _phi(oracle, "shear")
+    dx, h = case.config["dx"], case.config["h_over_dx"] * case.config["dx"]
+    k = np.arange(-3, 4)
+    X, Y, Z = np.meshgrid(k, k, k, indexing="ij")
+    r = dx * np.sqrt(X ** 2 + Y ** 2 + Z ** 2).ravel()
+    r = r[r > 0]
+    M = -(dx ** 3 / 3.0) * sum(ri * oracle.dW(ri, h) for ri in r)
+    mu, g = case.materials[0]["mu"], case.meta["rate"]
+    assert np.allclose(phi, mu * g * g * M * M, rtol=1e-9)
+    assert mu * g * g * M * M == pytest.approx(mu * g * g, rel=0.05)
+
+
+def test_viscous_heating_vanishes_for_rigid_motion(oracle):
+    phi_rot, case = _phi(oracle, "rotation")
+    mu, g = case.materials[0]["mu"], case.meta["rate"]
+    assert np.max(np.abs(phi_rot)) < 1e-20 * mu * g * g
+    phi_tr, _ = _phi(oracle, "translation")
+    assert np.max(np.abs(phi_tr)) == 0.0
+
+
+def test_viscous_heating_off_by_default(oracle):
+    phi, _ = _phi(oracle, "shear", on=0)
+    assert np.max(np.abs(phi)) == 0.0
