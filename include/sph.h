@@ -259,6 +259,33 @@ sph_status sph_profile(sph_ctx* ctx, int enable);
  * clears the counters after reading. */
 sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* launches, int reset);
 
+/* Physics-driven particle relaxation (Sec. 2.2): pre-processing that moves
+ * particles seeded on a lattice inside a body towards an isotropic,
+ * body-fitted distribution under a constant background pressure p0
+ * (scale-free, p0 / rho0 = 1), confined by the body's level set.  Per
+ * iteration: F_p,i = -2 sum_j V_j W'(r) e_ij over partners within 2h, plus
+ * -2 n A(d) for the kernel volume missing beyond the surface (n = unit
+ * gradient of phi, d = -phi the depth, A(d) = 2 pi int_d^{2h} W(r) r dr);
+ * dt = 0.25 sqrt(h / max |F_p|); r += F_p dt^2 / 2; a particle that ends
+ * outside (phi > 0) is moved back along n by phi.  FP64 throughout. */
+typedef struct {
+    double dx, h_over_dx;    /* particle spacing (V = dx^3) and h = h_over_dx dx */
+    const double* phi;       /* host: level set, negative inside, nphi[0] x nphi[1] x nphi[2]
+                                nodes, x fastest; node (i, j, k) at phi_origin + (i, j, k) phi_spacing;
+                                trilinear in between.  The particles stay inside this box. */
+    int nphi[3];             /* >= 2 each */
+    double phi_origin[3], phi_spacing;
+} sph_relax_config;
+
+/* Relax the n particles pos (host double[n*3], in place) for `iterations`
+ * steps on `stream` (a cudaStream_t or NULL); device memory is allocated and
+ * freed on that stream.  max_accel: host double[iterations] receiving
+ * max |F_p| of each step, or NULL.  Errors: SPH_EINVAL (NULL arguments,
+ * non-positive sizes, a level-set grid under 2 nodes on an axis), SPH_ENOMEM,
+ * SPH_ECUDA; the message is in sph_last_error(NULL). */
+sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* pos, int iterations, void* stream,
+                     double* max_accel);
+
 /* Message of the last failed call on ctx ("" if none).  With ctx == NULL:
  * the last failed context-free call (sph_cell_sort*) of this host thread.
  * Never NULL. */

@@ -34,6 +34,11 @@ class OrcConfig(C.Structure):
                 ("viscous_heating", C.c_int)]
 
 
+class OrcRelaxConfig(C.Structure):
+    _fields_ = [("dx", D), ("h_over_dx", D), ("phi", C.POINTER(D)), ("nphi", C.c_int * 3),
+                ("phi_origin", D * 3), ("phi_spacing", D)]
+
+
 class OrcMaterial(C.Structure):
     _fields_ = [("rho0", D), ("mu", D), ("k", D), ("cp", D), ("T_init", D), ("fixed_T", C.c_int)]
 
@@ -51,6 +56,9 @@ def lib():
         L.orc_dt_thermal.restype = D; L.orc_dt_thermal.argtypes = [D, D, D, D]
         L.orc_neighbors.restype = I64
         L.orc_neighbors.argtypes = [I64, PD, D, C.c_int, PD, PI64, PI32, I64]
+        L.orc_relax_A.restype = D; L.orc_relax_A.argtypes = [D, D]
+        L.orc_relax.restype = C.c_int
+        L.orc_relax.argtypes = [C.POINTER(OrcRelaxConfig), I64, PD, C.c_int, PD]
         L.orc_neighbors_of.restype = I64
         L.orc_neighbors_of.argtypes = [I64, PD, D, C.c_int, PD, I64, PI64, PI64, PI32, I64]
         L.orc_cell_order.argtypes = [I64, PD, PD, PD, PI, PI64, PI64]
@@ -127,6 +135,27 @@ def neighbors(pos, R2, periodic_mask=0, extent=(0, 0, 0)):
                               counts.ctypes.data_as(PI64), lst.ctypes.data_as(PI32), total)
     assert got == total
     return counts, lst[:total]
+
+
+def relax_A(d, h):
+    return lib().orc_relax_A(float(d), float(h))
+
+
+def relax(pos, dx, h_over_dx, phi, phi_origin, phi_spacing, iterations):
+    """Particle relaxation (Sec. 2.2) of pos[n, 3] in the level set phi[nz, ny, nx]
+    (nodes at phi_origin + (i, j, k) phi_spacing): returns (positions, max |F_p|
+    per iteration)."""
+    pos = np.ascontiguousarray(pos, np.float64).copy()
+    phi = np.ascontiguousarray(phi, np.float64)
+    c = OrcRelaxConfig()
+    c.dx, c.h_over_dx = float(dx), float(h_over_dx)
+    c.phi = phi.ctypes.data_as(C.POINTER(D))
+    c.nphi = (C.c_int * 3)(phi.shape[2], phi.shape[1], phi.shape[0])
+    c.phi_origin = (D * 3)(*[float(v) for v in phi_origin])
+    c.phi_spacing = float(phi_spacing)
+    amax = np.zeros(max(int(iterations), 1), np.float64)
+    assert lib().orc_relax(C.byref(c), len(pos), _pd(pos), int(iterations), _pd(amax)) == 0
+    return pos, amax[:iterations]
 
 
 def neighbors_of(pos, R2, idx, periodic_mask=0, extent=(0, 0, 0)):

@@ -786,3 +786,120 @@ int orc_time(const orc_sim* S, double* t, int64_t* adv, int64_t* sub, double* dt
 }
 
 int64_t orc_count(const orc_sim* S) { return S->n; }
+
+/* ------------------------------------------------------------------------ */
+/* Physics-driven particle relaxation (Sec. 2.2).  Particles move under the
+ * constant background pressure p0 (scale-free: p0 / rho0 = 1),
+ *   F_p,i = -(2 / m_i) sum_j V_i V_j p0 grad_i W_ij = -2 sum_j V_j W'(r) e_ij,
+ * with r += F_p dt^2 / 2 and dt = 0.25 sqrt(h / max |F_p|).
+ * READING of the static level-set confinement the paper takes from its
+ * reference: (i) the kernel volume missing beyond the surface is replaced by
+ * the half space at the particle's depth d = -phi: sum over it of V grad_i W
+ * = n A(d), n the outward unit normal grad phi / |grad phi|, A(d) =
+ * 2 pi int_d^{2h} W(r) r dr; (ii) a particle that ends a step outside
+ * (phi > 0) is moved back along n onto the surface, x -= phi n. */
+double orc_relax_A(double d, double h) {
+    if (d < 0.0) d = 0.0;
+    const double R = 2.0 * h;
+    if (d >= R) return 0.0;
+    const int m = 2000; /* Simpson on [d, 2h] */
+    const double a = d, b = R, dh = (b - a) / m;
+    double s = orc_W(a, h) * a + orc_W(b, h) * b;
+    for (int k = 1; k < m; ++k) {
+        const double r = a + k * dh;
+        s += (k % 2 ? 4.0 : 2.0) * orc_W(r, h) * r;
+    }
+    return 2.0 * PI * s * dh / 3.0;
+}
+
+static double phi_node(const orc_relax_config* c, int i, int j, int k) {
+    if (i < 0) i = 0;
+    if (j < 0) j = 0;
+    if (k < 0) k = 0;
+    if (i > c->nphi[0] - 1) i = c->nphi[0] - 1;
+    if (j > c->nphi[1] - 1) j = c->nphi[1] - 1;
+    if (k > c->nphi[2] - 1) k = c->nphi[2] - 1;
+    return c->phi[((int64_t)k * c->nphi[1] + j) * c->nphi[0] + i];
+}
+
+/* central difference of phi along axis a at node (i, j, k) (one-sided at the
+ * grid's faces) */
+static double phi_grad_node(const orc_relax_config* c, int i, int j, int k, int a) {
+    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+    lo[a] -= 1;
+    hi[a] += 1;
+    const int idx[3] = {i, j, k};
+    double span = 2.0;
+    if (lo[a] < 0) { lo[a] = idx[a]; span -= 1.0; }
+    if (hi[a] > c->nphi[a] - 1) { hi[a] = idx[a]; span -= 1.0; }
+    return (phi_node(c, hi[0], hi[1], hi[2]) - phi_node(c, lo[0], lo[1], lo[2])) / (span * c->phi_spacing);
+}
+
+/* trilinear interpolation of phi; n_out = the normalised trilinear
+ * interpolation of the nodes' central-difference gradients (continuous, so
+ * mirror-image points get mirror-image normals) */
+double orc_phi(const orc_relax_config* c, const double* x, double* n_out) {
+    double u[3], f[3];
+    int b[3];
+    for (int a = 0; a < 3; ++a) {
+        u[a] = (x[a] - c->phi_origin[a]) / c->phi_spacing;
+        double fl = floor(u[a]);
+        if (fl < 0.0) fl = 0.0;
+        if (fl > c->nphi[a] - 2) fl = c->nphi[a] - 2;
+        b[a] = (int)fl;
+        f[a] = u[a] - fl;
+    }
+    double phi = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 2; ++j)
+            for (int i = 0; i < 2; ++i) {
+                const double w = (i ? f[0] : 1.0 - f[0]) * (j ? f[1] : 1.0 - f[1]) * (k ? f[2] : 1.0 - f[2]);
+                phi += w * phi_node(c, b[0] + i, b[1] + j, b[2] + k);
+                for (int a = 0; a < 3; ++a) g[a] += w * phi_grad_node(c, b[0] + i, b[1] + j, b[2] + k, a);
+            }
+    if (n_out) {
+        const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        for (int a = 0; a < 3; ++a) n_out[a] = gn > 0.0 ? g[a] / gn : 0.0;
+    }
+    return phi;
+}
+
+int orc_relax(const orc_relax_config* cfg, int64_t n, double* pos, int iterations, double* max_accel) {
+    const double dx = cfg->dx, h = cfg->h_over_dx * dx, R2 = 4.0 * h * h, V = dx * dx * dx;
+    double* acc = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    for (int it = 0; it < iterations; ++it) {
+        double amax = 0.0;
+        #pragma omp parallel for schedule(dynamic, 64) reduction(max : amax)
+        for (int64_t i = 0; i < n; ++i) {
+            double a[3] = {0.0, 0.0, 0.0}, v[3];
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const double r2 = dist2(pos + 3 * i, pos + 3 * j, 0, NULL, v);
+                if (!(r2 > 0.0 && r2 < R2)) continue;
+                const double r = sqrt(r2), c = -2.0 * V * orc_dW(r, h) / r;
+                for (int k = 0; k < 3; ++k) a[k] += c * v[k];
+            }
+            double nrm[3];
+            const double phi = orc_phi(cfg, pos + 3 * i, nrm);
+            const double A = orc_relax_A(-phi, h);
+            for (int k = 0; k < 3; ++k) a[k] += -2.0 * nrm[k] * A;
+            for (int k = 0; k < 3; ++k) acc[3 * i + k] = a[k];
+            const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            if (am > amax) amax = am;
+        }
+        if (max_accel) max_accel[it] = amax;
+        if (!(amax > 0.0)) continue;
+        const double dt = 0.25 * sqrt(h / amax);
+        #pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double* x = pos + 3 * i;
+            for (int k = 0; k < 3; ++k) x[k] = x[k] + 0.5 * acc[3 * i + k] * dt * dt;
+            double nrm[3];
+            const double phi = orc_phi(cfg, x, nrm);
+            if (phi > 0.0)
+                for (int k = 0; k < 3; ++k) x[k] -= phi * nrm[k];
+        }
+    }
+    free(acc);
+    return 0;
+}

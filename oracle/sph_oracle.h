@@ -84,6 +84,21 @@ int orc_step(orc_sim*, int n_adv);
  * 8 sigma (kernel sum of pass D), 9 wall normal[3], 10 wall velocity[3],
  * 11 contact factor of rigid-body particles (Sec. 2.7; 0 for the others) */
 int orc_get_field(const orc_sim*, int field, double* out);
+
+/* --- physics-driven particle relaxation (Sec. 2.2), a pre-processing step --- */
+typedef struct {
+    double dx, h_over_dx;          /* particle spacing, smoothing length h = h_over_dx dx */
+    const double* phi;             /* level set (negative inside), nphi[0] x nphi[1] x nphi[2] nodes, x fastest */
+    int nphi[3];
+    double phi_origin[3], phi_spacing;
+} orc_relax_config;
+/* half-space kernel integral A(d) = 2 pi int_d^{2h} W(r) r dr (quadrature) */
+double orc_relax_A(double d, double h);
+/* level set and its unit gradient at x (trilinear) */
+double orc_phi(const orc_relax_config* c, const double* x, double* n_out);
+/* `iterations` relaxation steps of the n particles pos[n*3] (in place);
+ * max_accel[k] = max |F_p| of step k (may be NULL) */
+int orc_relax(const orc_relax_config* cfg, int64_t n, double* pos, int iterations, double* max_accel);
 /* body: torque about its axis (last sub-step), dt-weighted average since
  * start, heat into fluid sum m cp (T - T0), mean fluid temperature */
 int orc_torque_heat(const orc_sim*, int body, double* torque, double* torque_avg,

@@ -47,6 +47,11 @@ class sph_info(C.Structure):
                 ("kernels_fixed", C.c_int), ("kernels_per_substep", C.c_int)]
 
 
+class sph_relax_config(C.Structure):
+    _fields_ = [("dx", D), ("h_over_dx", D), ("phi", C.POINTER(D)), ("nphi", C.c_int * 3),
+                ("phi_origin", D * 3), ("phi_spacing", D)]
+
+
 class sph_tune_report(C.Structure):
     _fields_ = [("list_batch", C.c_int), ("tpp", C.c_int), ("block", C.c_int), ("ms_step_start", D),
                 ("ms_step_chosen", D), ("substeps_ref", D), ("trials", C.c_int), ("steps", I64)]
@@ -117,6 +122,7 @@ def lib():
         L.sph_cell_sort_noalloc.argtypes = [vp, I64, PD, PD, C.POINTER(C.c_int), vp, vp, vp]
         L.sph_profile_read.argtypes = [vp, PD, PI64, C.c_int]
         L.sph_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
+        L.sph_relax.argtypes = [C.POINTER(sph_relax_config), I64, PD, C.c_int, vp, PD]
         L.sph_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
@@ -453,6 +459,26 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sph_relax(pos, dx, h_over_dx, phi, phi_origin, phi_spacing, iterations, stream=None):
+    """Particle relaxation (Sec. 2.2) on the GPU: pos[n, 3] (host) relaxed in the
+    level set phi[nz, ny, nx]; returns (positions, max |F_p| per iteration)."""
+    L = lib()
+    pos = np.ascontiguousarray(pos, np.float64).copy()
+    phi = np.ascontiguousarray(phi, np.float64)
+    c = sph_relax_config()
+    c.dx, c.h_over_dx = float(dx), float(h_over_dx)
+    c.phi = phi.ctypes.data_as(C.POINTER(D))
+    c.nphi = (C.c_int * 3)(phi.shape[2], phi.shape[1], phi.shape[0])
+    c.phi_origin = (D * 3)(*[float(v) for v in phi_origin])
+    c.phi_spacing = float(phi_spacing)
+    amax = np.zeros(max(int(iterations), 1), np.float64)
+    st = L.sph_relax(C.byref(c), len(pos), pos.ctypes.data_as(PD), int(iterations),
+                     C.c_void_p(0 if stream is None else stream), amax.ctypes.data_as(PD))
+    if st != 0:
+        raise SphError(st, "sph_relax: " + L.sph_last_error(None).decode())
+    return pos, amax[:iterations]
 
 
 def cells_of(case):

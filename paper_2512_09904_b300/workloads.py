@@ -387,6 +387,39 @@ def flow_block(field="shear", rate=20.0, n=14, dx=1e-3, viscous_heating=1, mu=0.
     return Case("flow_block", cfg, mats, fluids, [], {}, dict(rate=rate, field=field))
 
 
+def relax_body(shape="sphere", size=10e-3, dx=1e-3, h_over_dx=1.3, phi_step=None, offset=0.5):
+    """A body for the particle relaxation of Sec. 2.2: its level set sampled on
+    a grid (negative inside) and the lattice seeds inside it.
+
+    shape 'sphere' (radius `size`) or 'box' (half width `size`, faces half a
+    spacing beyond the outermost lattice points); the body is centred at the
+    origin; lattice points at (k + offset) dx.  Returns a dict with pos[n, 3],
+    phi[nz, ny, nx], phi_origin, phi_spacing, dx, h_over_dx."""
+    step = phi_step or 0.5 * dx
+    pad = 3.0 * h_over_dx * dx
+    half = int(math.ceil((size + pad) / step))  # nodes on each side of the centre: a symmetric grid
+    lo = -half * step
+    m = 2 * half + 1
+    ax = step * np.arange(-half, half + 1)
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    if shape == "sphere":
+        phi = np.sqrt(X ** 2 + Y ** 2 + Z ** 2) - size
+    elif shape == "box":
+        q = np.abs(np.stack([X, Y, Z])) - size
+        outside = np.linalg.norm(np.maximum(q, 0.0), axis=0)
+        phi = outside + np.minimum(np.max(q, axis=0), 0.0)
+    else:
+        raise ValueError(shape)
+    k = int(math.ceil(size / dx)) + 1
+    g = (np.arange(-k, k + 1) + offset) * dx
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    if shape == "sphere":
+        inside = np.linalg.norm(P, axis=1) < size
+    else:
+        inside = np.all(np.abs(P) < size, axis=1)
+    return dict(pos=P[inside], phi=phi, phi_origin=[lo, lo, lo], phi_spacing=step, dx=dx, h_over_dx=h_over_dx)
+
+
 # --------------------------------------------------------------------------
 # Two-material slab of the conduction validation (Sec. 3.2, Table 3):
 # x in [0,1], interface x=0.5, T=0 left / 1 right; periodic in y and z.

@@ -122,3 +122,12 @@ def test_tuning_keys_are_validated(sphlib):
         assert e.value.status == sphlib.SPH_EINVAL
         assert ctx.sph_get_tuning(key) == good
     ctx.close()
+
+
+def test_relax_validates_arguments(sphlib):
+    b = W.relax_body("sphere", size=3e-3)
+    with pytest.raises(sphlib.SphError) as e:
+        sphlib.sph_relax(b["pos"], -1.0, b["h_over_dx"], b["phi"], b["phi_origin"], b["phi_spacing"], 2)
+    assert e.value.status == sphlib.SPH_EINVAL
+    with pytest.raises(sphlib.SphError):
+        sphlib.sph_relax(b["pos"], b["dx"], b["h_over_dx"], b["phi"][:1], b["phi_origin"], b["phi_spacing"], 2)

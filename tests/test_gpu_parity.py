@@ -236,3 +236,14 @@ def test_viscous_heating_parity(sph, oracle, name, make):
     gT, rT = ctx.sph_read_fields("T")[fl], sim.field("T")[fl]
     rise = max(float(np.max(np.abs(rT - W.flatten(case)["T"][fl]))), 1e-30)
     assert float(np.max(np.abs(gT - rT))) <= 1e-4 * rise + 1e-9, name
+
+
+# ---------------------------------------------------- particle relaxation ---
+@pytest.mark.parametrize("shape,size", [("sphere", 7e-3), ("box", 6e-3)])
+def test_relax_parity(sph, oracle, shape, size):
+    b = W.relax_body(shape, size=size)
+    args = (b["dx"], b["h_over_dx"], b["phi"], b["phi_origin"], b["phi_spacing"], 20)
+    g, ga = sph.sph_relax(b["pos"], *args)
+    r, ra = oracle.relax(b["pos"], *args)
+    assert np.max(np.abs(g - r)) <= 1e-9 * b["dx"]
+    assert np.allclose(ga, ra, rtol=1e-9)
