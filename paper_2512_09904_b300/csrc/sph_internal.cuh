@@ -157,6 +157,21 @@ static __device__ __noinline__ bool member_fp64(const CaseDev& C, const double* 
     return r2 > 0.0 && r2 < C.R2;
 }
 
+// Half-width of the x interval of the 2h sphere around a point at squared
+// distance d2 (< R2) from a row's slab, plus Rmargin.  The square root is the
+// hardware reciprocal estimate: its relative error (~1e-7) is far inside the
+// margin, so the clipping stays conservative.
+__device__ __forceinline__ float row_half_width(const CaseDev& C, float d2) {
+    const float e2 = C.R2hi - d2;
+    return e2 * rsqrtf(e2) + C.Rmargin;
+}
+
+// Distance from a point at offset o inside its sort cell (width w) to the
+// slab of the cell d sort cells away on that axis.
+__device__ __forceinline__ float slab_gap(int d, float w, float o) {
+    return d > 0 ? fmaxf(fmaf((float)(d - 1), w, w - o), 0.f) : (d < 0 ? fmaxf(fmaf((float)(-d - 1), w, o), 0.f) : 0.f);
+}
+
 // Candidate runs of slot i (sort cell key_i, geometry offsets si): the rows
 // of sort cells within two of i's on y and z whose slab the sphere of radius
 // 2h around i reaches, and in each row the cells within two on x that the
@@ -184,8 +199,7 @@ __device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* _
             if (!pz) continue;
             z = (z + nz) % nz;
         }
-        const float gz = dz > 0 ? fmaxf(fmaf((float)(dz - 1), wz, wz - oz), 0.f)
-                                : (dz < 0 ? fmaxf(fmaf((float)(-dz - 1), wz, oz), 0.f) : 0.f);
+        const float gz = slab_gap(dz, wz, oz);
         if (gz * gz >= R2) continue;
         const int dcz = ((sz + dz) >> 1) - (sz >> 1);
 #pragma unroll 1
@@ -195,11 +209,10 @@ __device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* _
                 if (!py) continue;
                 y = (y + ny) % ny;
             }
-            const float gy = dy > 0 ? fmaxf(fmaf((float)(dy - 1), wy, wy - oy), 0.f)
-                                    : (dy < 0 ? fmaxf(fmaf((float)(-dy - 1), wy, oy), 0.f) : 0.f);
+            const float gy = slab_gap(dy, wy, oy);
             const float d2 = fmaf(gy, gy, gz * gz);
             if (d2 >= R2) continue;
-            const float ex = sqrtf(R2 - d2) + C.Rmargin;
+            const float ex = row_half_width(C, d2);
             int xl = sx + max(-2, (int)floorf((ox - ex) * C.inv_scellwf[0]));
             int xh = sx + min(2, (int)floorf((ox + ex) * C.inv_scellwf[0]));
             if (!px) {
@@ -219,6 +232,75 @@ __device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* _
     }
 }
 
+// Every candidate j of slot i, in the order of for_each_run (rows by z, y;
+// slots ascending), as f(j, ox, oy, oz, code): (ox, oy, oz) = i's offsets
+// moved into j's geometry cell, so r_ij = o - (j's offsets), and code =
+// (dcx+1) | (dcy+1) << 2 | (dcz+1) << 4 that cell's offset.  Without periodic
+// axes a clipped row is one contiguous slot range, walked in a single loop
+// that steps the geometry-cell offset at the first slot of each next cell:
+// the threads of a warp then diverge per row, not per row and cell.
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint32_t* __restrict__ cstart, float4 si,
+                                                   uint32_t key_i, F&& f) {
+    if (C.periodic) {
+        for_each_run(C, cstart, si, key_i, [&](int a, int b, int dcx, int dcy, int dcz) {
+            const float ox = si.x - (float)dcx * C.gcellwf[0];
+            const float oy = si.y - (float)dcy * C.gcellwf[1];
+            const float oz = si.z - (float)dcz * C.gcellwf[2];
+            const uint32_t code = (uint32_t)((dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4));
+            for (int j = a; j < b; ++j) f(j, ox, oy, oz, code);
+        });
+        return;
+    }
+    const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
+    const int cl = (int)key_i - C.cell_base;
+    const int sx = cl % nx, sy = (cl / nx) % ny, sz = cl / (nx * ny);
+    const float wx = C.scellwf[0], wy = C.scellwf[1], wz = C.scellwf[2];
+    const float cx = si.x - (float)(sx & 1) * wx;
+    const float cy = si.y - (float)(sy & 1) * wy;
+    const float cz = si.z - (float)(sz & 1) * wz;
+    const float R2 = C.R2hi, gw = C.gcellwf[0];
+#pragma unroll 1
+    for (int dz = -2; dz <= 2; ++dz) {
+        const int z = sz + dz;
+        if (z < 0 || z >= nz) continue;
+        const float gz = slab_gap(dz, wz, cz);
+        if (gz * gz >= R2) continue;
+        const int dcz = ((sz + dz) >> 1) - (sz >> 1);
+        const float oz = si.z - (float)dcz * C.gcellwf[2];
+#pragma unroll 1
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int y = sy + dy;
+            if (y < 0 || y >= ny) continue;
+            const float gy = slab_gap(dy, wy, cy);
+            const float d2 = fmaf(gy, gy, gz * gz);
+            if (d2 >= R2) continue;
+            const float ex = row_half_width(C, d2);
+            const int xl = max(0, sx + max(-2, (int)floorf((cx - ex) * C.inv_scellwf[0])));
+            const int xh = min(nx - 1, sx + min(2, (int)floorf((cx + ex) * C.inv_scellwf[0])));
+            if (xl > xh) continue;
+            const int row = C.cell_base + (z * ny + y) * nx;
+            const int dcy = ((sy + dy) >> 1) - (sy >> 1);
+            const float oy = si.y - (float)dcy * C.gcellwf[1];
+            const int dcx = (xl >> 1) - (sx >> 1);
+            float ox = si.x - (float)dcx * gw;
+            uint32_t code = (uint32_t)((dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4));
+            const int end = (int)cstart[row + xh + 1];
+            int xb = (xl & ~1) + 2;  // first sort cell of the next geometry cell
+            int jb = xb <= xh ? (int)cstart[row + xb] : end;
+            for (int j = (int)cstart[row + xl]; j < end; ++j) {
+                while (j == jb) {  // ends: jb = end > j once xb passes xh
+                    ox -= gw;
+                    ++code;
+                    xb += 2;
+                    jb = xb <= xh ? (int)cstart[row + xb] : end;
+                }
+                f(j, ox, oy, oz, code);
+            }
+        }
+    }
+}
+
 // Visit every neighbour j of slot i.  Pair geometry comes from the FP32
 // geometry-cell offsets of the frozen snapshot: r_ij = off_i - off_j - dc w.
 // Membership is decided in FP32 away from the cut-off and re-decided from
@@ -232,22 +314,16 @@ __device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32
                                                   const double* __restrict__ Yy,
                                                   const double* __restrict__ Yz, int i, float4 si,
                                                   uint32_t key_i, F&& f) {
-    for_each_run(C, cstart, si, key_i, [&](int a, int b, int dcx, int dcy, int dcz) {
-        const float ox = si.x - (float)dcx * C.gcellwf[0];
-        const float oy = si.y - (float)dcy * C.gcellwf[1];
-        const float oz = si.z - (float)dcz * C.gcellwf[2];
-        const int code = (dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4);
-        for (int j = a; j < b; ++j) {
-            if (j == i) continue;
-            const float4 sj = __ldg(snap + j);
-            const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
-            const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-            bool in;
-            if (r2 >= C.R2hi) in = false;
-            else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
-            else in = member_fp64(C, Yx, Yy, Yz, i, j);
-            if (in) f(j, sj, rx, ry, rz, r2, code);
-        }
+    for_each_candidate(C, cstart, si, key_i, [&](int j, float ox, float oy, float oz, uint32_t code) {
+        if (j == i) return;
+        const float4 sj = __ldg(snap + j);
+        const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
+        const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        bool in;
+        if (r2 >= C.R2hi) in = false;
+        else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
+        else in = member_fp64(C, Yx, Yy, Yz, i, j);
+        if (in) f(j, sj, rx, ry, rz, r2, (int)code);
     });
 }
 

@@ -560,7 +560,7 @@ __device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && 
 // their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
 // runs over all partners (fluid and wall) plus the particle itself.  Static
 // walls of fixed temperature have no pair sums of their own and get no list.
-__global__ void __launch_bounds__(256, 4) k_passD(Bufs B, int par) {
+__global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(256, 4) k_passD(Bufs B, int par) {
     float sum = C.w0;
     uint32_t nf = 0, nw = 0;
     for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i], [&](int j, float4 sj, float, float, float, float r2, int code) {
-        sum += kernel_W(C, sqrtf(r2));
+        sum += kernel_W(C, r2 * rsqrtf(fmaxf(r2, 1e-30f)));  // r from the reciprocal root estimate
         const uint32_t e = (uint32_t)j | ((uint32_t)code << 26);
         const bool room = nf + nw < (uint32_t)NB_CAP;
         if (tag_kind(__float_as_uint(sj.w)) == KIND_FLUID) {
