@@ -149,15 +149,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(omega, steps=1):
+def cpu_baseline(omega, min_seconds=10.0, max_steps=40):
     """The FP64 O(N^2) oracle, as it stands, on a bounded sample of the
-    workload: the same gear bath at dx = 5 mm, one advection step per step."""
+    workload: the same gear bath at dx = 5 mm, advection steps until about
+    min_seconds of host time have passed."""
     from oracle import oracle as O
     threads = O.set_threads(0)
     case = workload(5e-3, omega)
     sim = O.OracleSim(case)
+    steps = 0
     t0 = time.perf_counter()
-    sim.step(steps)
+    while steps < max_steps and (time.perf_counter() - t0) < min_seconds:
+        sim.step(1)
+        steps += 1
     dt = time.perf_counter() - t0
     sub = sim.time()["substeps"]
     return dict(value=case.n_fluid * sub / dt, unit=UNIT, cores=threads, kind="oracle",
@@ -287,7 +291,9 @@ def main():
         fl = dict(pass_M=FLOP_M, pass_C=FLOP_C, pass_VT=FLOP_VT)[dom]
         flops = ff * fl["ff"] + fw * fl["fw"]
     sm_max = peaks.get("sm_max_mhz", 2032.0)
-    peak_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
+    nominal_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
+    # the ALU denominator: FP32 FMA throughput measured on this device by the library's probe
+    peak_fp32, probe_ms = sph.sph_fma_peak(reps=5)
     achieved = flops / avg_s / 1e12
     # HBM bytes per launch: own state in and out plus one pass over the lists
     # (pass D writes them; VT reads them like M and C)
@@ -303,7 +309,8 @@ def main():
         traffic = TRAFFIC["bytes_per_unit"][dom] * n_units
     roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": traffic,
-                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max from {src} peaks file)",
+                "peak_source": f"measured: FP32 FMA probe (sph_fma_peak, best of 5 launches of {probe_ms:.2f} ms); "
+                               f"nominal 148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz = {nominal_fp32:.1f} TFLOP/s",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
                 "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
                 "timing": "per-group device times from a replay of the timed steps with event records "

@@ -70,6 +70,13 @@ typedef struct {
                                     partners); an extension: the paper's thermal model omits it
                                     (Sec. 2.6).  0 (default): the paper's model.  Other values:
                                     SPH_EINVAL. */
+    int vstar_literal;           /* 0 (default): Eq. (13)'s interface velocity read with U measured
+                                    along -e_ij as in Eq. (11), v* = -(U* - U~) e_ij + v~, so that
+                                    (v_i - v*).e_ij = U* - U_L; 1: the sign as printed,
+                                    v* = (U* - U~) e_ij + v~, which turns the pressure-difference
+                                    term of the continuity sum anti-diffusive (for study; needs
+                                    pair_precision = 1).  Other values, or 1 with FP32 pairs:
+                                    SPH_EINVAL. */
 } sph_config;
 
 /* Material table entry (Sec. 2.6 and the paper's property tables). */
@@ -198,6 +205,16 @@ sph_status sph_pair_stats(sph_ctx* ctx, int64_t* fluid_fluid, int64_t* fluid_wal
  * partners found.  Used to turn pass-D times into search rates.
  * Errors: SPH_ESTATE (no step yet), SPH_EINVAL (NULL output), SPH_ECUDA. */
 sph_status sph_search_stats(sph_ctx* ctx, int64_t* searched, int64_t* candidates, int64_t* partners);
+
+/* Measured FP32 throughput of the current device, the denominator of the
+ * pair passes' ALU roofline (they are bound by FP32 issue, not by HBM or
+ * tensor cores): a probe kernel in which every thread of one full wave of
+ * resident blocks runs independent chains of FP32 fused multiply-adds
+ * (2 flops each), timed with device events on `stream` after a warm-up
+ * launch.  Stateless (no context).  tflops: host, TFLOP/s of the fastest of
+ * `reps` launches; ms: host, may be NULL, that launch's duration.
+ * Errors: SPH_EINVAL (NULL tflops, reps < 1), SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_fma_peak(void* stream, int reps, double* tflops, double* ms);
 
 /* Kernel-variant knobs of the pair passes (performance only).  List batch
  * and block size leave every result bitwise unchanged; two threads per

@@ -31,7 +31,7 @@ class OrcConfig(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D),
                 ("gravity", D * 3), ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D),
                 ("free_surface", C.c_int), ("periodic_mask", C.c_int), ("max_substeps", C.c_int),
-                ("viscous_heating", C.c_int)]
+                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int)]
 
 
 class OrcRelaxConfig(C.Structure):
@@ -209,6 +209,7 @@ class OracleSim:
         oc.free_surface = cfg["free_surface"]; oc.periodic_mask = cfg["periodic_mask"]
         oc.max_substeps = cfg.get("max_substeps", 0)
         oc.viscous_heating = cfg.get("viscous_heating", 0)
+        oc.vstar_literal = cfg.get("vstar_literal", 0)
         self._p = L.orc_create(C.byref(oc))
         for mid, m in case.materials.items():
             om = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])

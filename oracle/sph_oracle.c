@@ -694,7 +694,19 @@ int orc_step(orc_sim* S, int n_adv) {
                     if (S->kind[j] == 0) {
                         double UL = -dot3(S->vel + 3 * i, e), UR = -dot3(S->vel + 3 * j, e);
                         orc_riemann(rho_i, UL, p_i, S->rho[j], UR, S->p[j], c0, &Ustar, &pstar);
-                        d += 2.0 * rho_i * fluid_volume(S, j) * (Ustar - UL) * dW;
+                        if (C->vstar_literal) {
+                            /* Eq. (13) with its printed sign: v* = (U* - U~) e_ij + v~,
+                             * U~ and v~ the density-weighted means of the two states */
+                            const double rho_j = S->rho[j], srho = rho_i + rho_j;
+                            const double Ut = (rho_i * UL + rho_j * UR) / srho;
+                            double dv[3];
+                            for (int k = 0; k < 3; ++k) {
+                                const double vt = (rho_i * S->vel[3 * i + k] + rho_j * S->vel[3 * j + k]) / srho;
+                                dv[k] = S->vel[3 * i + k] - ((Ustar - Ut) * e[k] + vt);
+                            }
+                            d += 2.0 * rho_i * fluid_volume(S, j) * dot3(dv, e) * dW;
+                        } else
+                            d += 2.0 * rho_i * fluid_volume(S, j) * (Ustar - UL) * dW;
                     } else {
                         /* READING: wall interface velocity v* = -U* n_w plus the
                          * fluid's tangential velocity, so (v_i - v*).e = (U* - U_L) n_w.e */

@@ -34,6 +34,8 @@ typedef struct {
     int max_substeps;            /* acoustic sub-steps cap per advection step; 0 = default */
     int viscous_heating;         /* 1: add the viscous-dissipation heating 2 mu S:S (not in the
                                     paper's model, which omits it; default 0) */
+    int vstar_literal;           /* 1: Eq. (13)'s interface velocity with its printed sign,
+                                    v* = (U* - U~) e_ij + v~ (default 0: v* = -(U* - U~) e_ij + v~) */
 } orc_config;
 
 typedef struct { double rho0, mu, k, cp, T_init; int fixed_T; } orc_material;

@@ -367,6 +367,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     for (int a = 0; a < 3; ++a) C.g64[a] = F.gravity[a];
     C.fp64 = F.pair_precision == 1 ? 1 : 0;
     C.visc_heat = F.viscous_heating ? 1 : 0;
+    C.vstar_lit = F.vstar_literal ? 1 : 0;
     C.u_ref = F.u_ref;
     C.cfl_ad = F.cfl_ad;
     C.cfl_ac = F.cfl_ac;
@@ -837,7 +838,8 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     const double h = cfg->h_over_dx * cfg->dx;
     if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
         !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1) ||
-        (cfg->viscous_heating != 0 && cfg->viscous_heating != 1))
+        (cfg->viscous_heating != 0 && cfg->viscous_heating != 1) ||
+        (cfg->vstar_literal != 0 && !(cfg->vstar_literal == 1 && cfg->pair_precision == 1)))
         return SPH_EINVAL;
     sph_ctx* c = new sph_ctx();
     c->cfg = *cfg;

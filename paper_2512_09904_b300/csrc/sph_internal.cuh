@@ -87,7 +87,8 @@ struct CaseDev {
     double kw64, kdw64, w0_64, inv_sigma0_64, vol64, c02_64, inv_c0_64, inv_c02_64, g64[3];
     double inv_contact_full64;
     int free_surface, kcap, n_body, fp64;
-    int visc_heat, pad_vh;  // add the viscous-dissipation heating 2 mu S:S (extension; off in the paper)
+    int visc_heat;  // add the viscous-dissipation heating 2 mu S:S (extension; off in the paper)
+    int vstar_lit;  // Eq. (13) with its printed sign (FP64 pairs only; off by default)
     MatDev mat[MAX_MAT];
     MatDev64 mat64[MAX_MAT];
     BodyDev body[MAX_BODY];

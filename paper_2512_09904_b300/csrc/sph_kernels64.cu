@@ -366,8 +366,12 @@ __global__ void __launch_bounds__(128) k_passC64(Bufs B, int par) {
         const MatDev64& Mj = C.mat64[tag_mat(tj)];
         const double4_32a vj = Vin[j];
         const double rho_j = Mj.rho0 + vj.w;
-        const double du = 0.5 * inv_r * dot3(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz) +
-                          C.c0_64 * (vi.w - vj.w) / (rho_i + rho_j);
+        // (v_i - v*).e_ij from U_R - U_L = (v_i - v_j).e_ij and p_i - p_j = c0^2 (drho_i - drho_j):
+        // U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)); with Eq. (13)'s printed
+        // sign it is 2 U~ - U_L - U* = (U_R - U_L)(1/2 - (rho_i - rho_j)/(rho_i + rho_j)) - (p_i - p_j) / (c0 (rho_i + rho_j))
+        const double dU = inv_r * dot3(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz);
+        const double dp = C.c0_64 * (vi.w - vj.w) / (rho_i + rho_j);
+        const double du = C.vstar_lit ? dU * (0.5 - (rho_i - rho_j) / (rho_i + rho_j)) - dp : 0.5 * dU + dp;
         d += Mj.mass / rho_j * du * dW;
     });
     visit64<P_WALL>(C, B, i, [&](int j, uint32_t, double rx, double ry, double rz, double r2) {

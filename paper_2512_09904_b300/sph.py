@@ -33,7 +33,7 @@ class sph_config(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D), ("gravity", D * 3),
                 ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D), ("free_surface", C.c_int),
                 ("periodic_mask", C.c_int), ("max_substeps", C.c_int), ("pair_precision", C.c_int),
-                ("viscous_heating", C.c_int)]
+                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int)]
 
 
 class sph_material(C.Structure):
@@ -124,6 +124,7 @@ def lib():
         L.sph_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
         L.sph_relax.argtypes = [C.POINTER(sph_relax_config), I64, PD, C.c_int, vp, PD]
         L.sph_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
+        L.sph_fma_peak.argtypes = [vp, C.c_int, PD, PD]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
                      "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
@@ -177,6 +178,7 @@ def config_from_dict(cfg: dict) -> sph_config:
     c.max_substeps = cfg.get("max_substeps", 0)
     c.pair_precision = cfg.get("pair_precision", 0)
     c.viscous_heating = cfg.get("viscous_heating", 0)
+    c.vstar_literal = cfg.get("vstar_literal", 0)
     return c
 
 
@@ -354,6 +356,17 @@ def sph_cell_sort_noalloc(pos_dev_ptr: int, n: int, origin, cellw, ncell, perm_d
                                  C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream))
     if rc != SPH_OK:
         raise SphError(rc, "sph_cell_sort_noalloc: " + L.sph_last_error(None).decode())
+
+
+def sph_fma_peak(reps=5, stream=None):
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of
+    the fastest probe launch)."""
+    L = lib()
+    tf, ms = D(), D()
+    st = L.sph_fma_peak(C.c_void_p(0 if stream is None else stream), int(reps), C.byref(tf), C.byref(ms))
+    if st != SPH_OK:
+        raise SphError(st, "sph_fma_peak")
+    return tf.value, ms.value
 
 
 class Batch:

@@ -75,6 +75,12 @@ def test_create_validates_config(sphlib):
     with pytest.raises(sphlib.SphError) as e:
         sphlib.Context(dict(cfg, pair_precision=2), stream=0)
     assert e.value.status == sphlib.SPH_EINVAL
+    # Eq. (13) with its printed sign: FP64 pairs only
+    sphlib.Context(dict(cfg, pair_precision=1, vstar_literal=1), stream=0).close()
+    for bad in (dict(vstar_literal=1), dict(pair_precision=1, vstar_literal=2)):
+        with pytest.raises(sphlib.SphError) as e:
+            sphlib.Context(dict(cfg, **bad), stream=0)
+        assert e.value.status == sphlib.SPH_EINVAL
 
 
 def test_add_validates_arguments(sphlib):
@@ -131,3 +137,10 @@ def test_relax_validates_arguments(sphlib):
     assert e.value.status == sphlib.SPH_EINVAL
     with pytest.raises(sphlib.SphError):
         sphlib.sph_relax(b["pos"], b["dx"], b["h_over_dx"], b["phi"][:1], b["phi_origin"], b["phi_spacing"], 2)
+
+
+def test_fma_peak_validates_arguments(sphlib):
+    L = sphlib.lib()
+    t = C.c_double()
+    assert L.sph_fma_peak(None, 0, C.byref(t), None) == sphlib.SPH_EINVAL
+    assert L.sph_fma_peak(None, 3, None, None) == sphlib.SPH_EINVAL

@@ -31,6 +31,11 @@ def _fp64(case):
     return case
 
 
+def _literal(case):
+    case.config = dict(case.config, vstar_literal=1)
+    return case
+
+
 def _scales(case):
     cfg = case.config
     rho0 = max(m["rho0"] for m in case.materials.values())
@@ -59,6 +64,8 @@ CASES = [
     ("periodic_box", lambda: W.periodic_box(n=12), 3),
     ("rotating_cylinder", lambda: W.rotating_cylinder(), 3),
     ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
+    # Eq. (13) with its printed sign (anti-diffusive; a short run)
+    ("periodic_box_vstar_literal", lambda: _literal(W.periodic_box(n=12, rho_amp=1e-4)), 2),
 ]
 
 
@@ -75,8 +82,12 @@ def test_fp64_field_parity(sph, oracle, name, make, steps):
         assert gi["t"] == pytest.approx(oi["t"], rel=1e-12)
         err = _errors(ctx, sim, case)
         print(name, k + 1, err)
+        # the printed sign of Eq. (13) is anti-diffusive: it amplifies the
+        # rounding difference of the two summation orders (a density bump
+        # grows ~40x per advection step, see the oracle pin), hence 100x
+        tol = TOL64 * (100.0 if "literal" in name else 1.0)
         for f, e in err.items():
-            assert e <= TOL64, (name, k + 1, f, e)
+            assert e <= tol, (name, k + 1, f, e)
     ctx.close()
 
 

@@ -117,3 +117,11 @@ def test_search_stats(sph):
     assert 60 < st["partners"] / st["searched"] < 90
     assert 120 < st["candidates"] / st["searched"] < 300
     ctx.close()
+
+
+def test_fma_peak_probe(sph):
+    # FP32 FMA throughput of one B300: 148 SMs x 128 lanes x 2 flops per clock,
+    # 77 TFLOP/s at the 2032 MHz maximum; the probe must land near it, never above
+    tf, ms = sph.sph_fma_peak(reps=3)
+    assert ms > 0.0
+    assert 35.0 < tf < 80.0, tf
