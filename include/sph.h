@@ -77,6 +77,12 @@ typedef struct {
                                     term of the continuity sum anti-diffusive (for study; needs
                                     pair_precision = 1).  Other values, or 1 with FP32 pairs:
                                     SPH_EINVAL. */
+    double cfl_T;                /* Eq. (26): dt_ad <= cfl_T rho c_p h^2 / k over every conducting
+                                    material whose temperature is integrated (fluid, free
+                                    solids); 0.5 as printed.  0: no thermal bound.  The printed
+                                    0.5 keeps the Cleary update stable at h = 1.0 dx but not at
+                                    h = 1.3 dx in 3-D, where about 0.2 is needed.  Negative or
+                                    NaN: SPH_EINVAL. */
 } sph_config;
 
 /* Material table entry (Sec. 2.6 and the paper's property tables). */

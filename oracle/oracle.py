@@ -31,7 +31,7 @@ class OrcConfig(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D),
                 ("gravity", D * 3), ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D),
                 ("free_surface", C.c_int), ("periodic_mask", C.c_int), ("max_substeps", C.c_int),
-                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int)]
+                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int), ("cfl_T", D)]
 
 
 class OrcRelaxConfig(C.Structure):
@@ -53,7 +53,7 @@ def lib():
         L.orc_riemann.argtypes = [D, D, D, D, D, D, D, PD, PD]
         L.orc_wall_riemann.argtypes = [D, D, D, D, D, D, D, PD, PD, PD, PD, PD]
         L.orc_timesteps.argtypes = [D, D, D, D, D, D, D, PD, PD]
-        L.orc_dt_thermal.restype = D; L.orc_dt_thermal.argtypes = [D, D, D, D]
+        L.orc_dt_thermal.restype = D; L.orc_dt_thermal.argtypes = [D, D, D, D, D]
         L.orc_neighbors.restype = I64
         L.orc_neighbors.argtypes = [I64, PD, D, C.c_int, PD, PI64, PI32, I64]
         L.orc_relax_A.restype = D; L.orc_relax_A.argtypes = [D, D]
@@ -113,8 +113,9 @@ def timesteps(h, vmax, u_ref, nu_max, c0, cfl_ad=0.25, cfl_ac=0.6):
     return a.value, b.value
 
 
-def dt_thermal(rho, cp, h, k):
-    return lib().orc_dt_thermal(rho, cp, h, k)
+def dt_thermal(rho, cp, h, k, cfl_T=0.5):
+    """Eq. (26): the thermal step bound, cfl_T rho c_p h^2 / k (0.5 as printed)."""
+    return lib().orc_dt_thermal(cfl_T, rho, cp, h, k)
 
 
 def set_threads(n=0):
@@ -210,6 +211,7 @@ class OracleSim:
         oc.max_substeps = cfg.get("max_substeps", 0)
         oc.viscous_heating = cfg.get("viscous_heating", 0)
         oc.vstar_literal = cfg.get("vstar_literal", 0)
+        oc.cfl_T = cfg.get("cfl_T", 0.5)
         self._p = L.orc_create(C.byref(oc))
         for mid, m in case.materials.items():
             om = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])

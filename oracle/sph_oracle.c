@@ -8,7 +8,7 @@
  * ((dx*dx + dy*dy) + dz*dz) in round-to-nearest FP64.
  *
  * The step (Sec. 2.8, dual-criteria time stepping) is:
- *   advection step (size dt_ad, Eq. 25 first line):
+ *   advection step (size dt_ad, Eq. 25 first line, at most the thermal bound of Eq. 26):
  *     rigid bodies placed at angle omega*t; snapshot of all positions;
  *     neighbour list from the snapshot (kept for the whole advection step);
  *     pass D  density re-initialisation (Eq. 14 / Eq. 15);
@@ -118,9 +118,9 @@ void orc_timesteps(double h, double vmax, double u_ref, double nu_max, double c0
     *dt_ac = cfl_ac * h / (c0 + vmax);
 }
 
-/* Eq. (26) */
-double orc_dt_thermal(double rho, double cp, double h, double k) {
-    return 0.5 * rho * cp * h * h / k;
+/* Eq. (26), printed with cfl_T = 0.5 */
+double orc_dt_thermal(double cfl_T, double rho, double cp, double h, double k) {
+    return cfl_T * rho * cp * h * h / k;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -245,6 +245,7 @@ typedef struct { double c[3], a[3], omega; int set; } orc_body;
 struct orc_sim {
     orc_config cfg;
     double h, R2, vol, sigma0, nu_max;
+    double dt_T;  /* Eq. (26) over the particles whose temperature is integrated */
     int kcap;
     orc_material mat[ORC_MAX_MAT];
     int mat_set[ORC_MAX_MAT];
@@ -425,6 +426,17 @@ int orc_step(orc_sim* S, int n_adv) {
             double nu = S->mat[S->mat_id[i]].mu / S->mat[S->mat_id[i]].rho0;
             if (nu > S->nu_max) S->nu_max = nu;
         }
+    /* READING of Eq. (26): the thermal bound caps the advection step for every
+     * conducting material whose temperature is integrated (fluid, free solids);
+     * cfl_T = 0 turns it off */
+    S->dt_T = INFINITY;
+    for (int64_t i = 0; i < n && C->cfl_T > 0.0; ++i) {
+        const orc_material* M = &S->mat[S->mat_id[i]];
+        if ((S->kind[i] == 0 || !M->fixed_T) && M->k > 0.0) {
+            double d = orc_dt_thermal(C->cfl_T, M->rho0, M->cp, h, M->k);
+            if (d < S->dt_T) S->dt_T = d;
+        }
+    }
     for (int st = 0; st < n_adv; ++st) {
         /* periodic wrap of fluid positions into the domain box */
         for (int64_t i = 0; i < n; ++i)
@@ -443,6 +455,7 @@ int orc_step(orc_sim* S, int n_adv) {
             }
         double dt_ad, dt_ac0;
         orc_timesteps(h, vmax, C->u_ref, S->nu_max, c0, C->cfl_ad, C->cfl_ac, &dt_ad, &dt_ac0);
+        if (S->dt_T < dt_ad) dt_ad = S->dt_T;
 
         /* rigid bodies: prescribed rotation theta = omega t about (c, axis) */
         for (int64_t i = 0; i < n; ++i) {

@@ -36,6 +36,7 @@ typedef struct {
                                     paper's model, which omits it; default 0) */
     int vstar_literal;           /* 1: Eq. (13)'s interface velocity with its printed sign,
                                     v* = (U* - U~) e_ij + v~ (default 0: v* = -(U* - U~) e_ij + v~) */
+    double cfl_T;                /* Eq. (26) coefficient (0.5 printed); 0: no thermal bound */
 } orc_config;
 
 typedef struct { double rho0, mu, k, cp, T_init; int fixed_T; } orc_material;
@@ -55,7 +56,7 @@ void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_
                       double* Ustar, double* pstar);
 void orc_timesteps(double h, double vmax, double u_ref, double nu_max, double c0,
                    double cfl_ad, double cfl_ac, double* dt_ad, double* dt_ac);
-double orc_dt_thermal(double rho, double cp, double h, double k);
+double orc_dt_thermal(double cfl_T, double rho, double cp, double h, double k);  /* Eq. (26) */
 
 /* brute-force pair list: pairs (i,j), 0 < |r_i - r_j|^2 < R2 (FP64, strict),
  * minimum image on periodic axes.  counts[i] = neighbours of i; if list is

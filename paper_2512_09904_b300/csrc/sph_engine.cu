@@ -384,6 +384,17 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     if (nfl == 0 && !c->T.empty()) Tref = c->T[0];
     C.nu_max = nu;
     C.T_ref = Tref;
+    // Eq. (26): the thermal bound over every conducting material whose
+    // temperature is integrated (fluid and free solids) caps dt_ad
+    double dtT = INFINITY;
+    const double hT = F.h_over_dx * F.dx;
+    if (F.cfl_T > 0.0)
+        for (size_t i = 0; i < c->kind.size(); ++i) {
+            const sph_material& M = c->mats[c->mat[i]];
+            if ((c->kind[i] == 0 || !M.fixed_T) && M.k > 0.0)
+                dtT = std::min(dtT, F.cfl_T * M.rho0 * M.cp * hT * hT / M.k);
+        }
+    C.dt_T = dtT;
     for (int m = 0; m < MAX_MAT; ++m) {
         if (!c->mat_set[m]) continue;
         const sph_material& M = c->mats[m];
@@ -839,7 +850,7 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
         !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1) ||
         (cfg->viscous_heating != 0 && cfg->viscous_heating != 1) ||
-        (cfg->vstar_literal != 0 && !(cfg->vstar_literal == 1 && cfg->pair_precision == 1)))
+        (cfg->vstar_literal != 0 && !(cfg->vstar_literal == 1 && cfg->pair_precision == 1)) || !(cfg->cfl_T >= 0))
         return SPH_EINVAL;
     sph_ctx* c = new sph_ctx();
     c->cfg = *cfg;

@@ -82,6 +82,7 @@ struct CaseDev {
     float c0, c02, inv_c0, inv_c02;
     float g[3];
     double h64, c0_64, u_ref, cfl_ad, cfl_ac, nu_max;
+    double dt_T;  // Eq. (26) thermal bound on dt_ad (infinite without conduction)
     double T_ref;
     // FP64 copies of the constants above (pair arithmetic in FP64)
     double kw64, kdw64, w0_64, inv_sigma0_64, vol64, c02_64, inv_c0_64, inv_c02_64, g64[3];

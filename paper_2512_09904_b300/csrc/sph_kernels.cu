@@ -61,7 +61,8 @@ __global__ void k_vmax_init(Bufs B, int par, int lo, int hi) {
     }
 }
 
-// Eq. (25) first line: dt_ad = cfl_ad min(h / max(|v|max, u_ref), h^2 / nu).
+// Eq. (25) first line: dt_ad = cfl_ad min(h / max(|v|max, u_ref), h^2 / nu),
+// at most the thermal bound of Eq. (26).
 __global__ void k_adv_begin(Bufs B) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= B.ncases) return;
@@ -75,6 +76,7 @@ __global__ void k_adv_begin(Bufs B) {
         if (b < a) a = b;
     }
     S.dt_ad = C.cfl_ad * a;
+    if (C.dt_T < S.dt_ad) S.dt_ad = C.dt_T;  // Eq. (26)
     S.tau = 0.0;
     S.nsub = 0;
     S.active = (S.alive && S.running) ? 1 : 0;

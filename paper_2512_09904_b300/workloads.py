@@ -29,7 +29,7 @@ class Case:
     """One simulation case: config table, materials, bodies and particle blocks.
 
     config keys: origin[3], extent[3], dx, h_over_dx, gravity[3], c0, u_ref,
-    cfl_ad, cfl_ac, free_surface, periodic_mask, max_substeps.
+    cfl_ad, cfl_ac, cfl_T, free_surface, periodic_mask, max_substeps.
     materials: {id: dict(rho0, mu, k, cp, T_init, fixed_T)}
     fluids: list of dict(mat, pos[n,3], vel[n,3]|None, T[n]|None, rho[n]|None)
     solids: list of dict(body, mat, pos[n,3], normal[n,3], T[n]|None)
@@ -68,7 +68,7 @@ def _cfg(origin, extent, dx, *, h_over_dx=1.3, gravity=(0.0, 0.0, -9.81), c0=10.
                 dx=float(dx), h_over_dx=float(h_over_dx),
                 gravity=[float(v) for v in gravity], c0=float(c0),
                 u_ref=float(c0 / 10.0 if u_ref is None else u_ref),
-                cfl_ad=0.25, cfl_ac=0.6, free_surface=int(free_surface),
+                cfl_ad=0.25, cfl_ac=0.6, cfl_T=0.5, free_surface=int(free_surface),
                 periodic_mask=int(periodic_mask), max_substeps=int(max_substeps))
 
 

@@ -75,6 +75,12 @@ def test_create_validates_config(sphlib):
     with pytest.raises(sphlib.SphError) as e:
         sphlib.Context(dict(cfg, pair_precision=2), stream=0)
     assert e.value.status == sphlib.SPH_EINVAL
+    # Eq. (26) coefficient: >= 0 (0 switches the thermal bound off)
+    sphlib.Context(dict(cfg, cfl_T=0.0), stream=0).close()
+    for bad in (-0.5, float("nan")):
+        with pytest.raises(sphlib.SphError) as e:
+            sphlib.Context(dict(cfg, cfl_T=bad), stream=0)
+        assert e.value.status == sphlib.SPH_EINVAL
     # Eq. (13) with its printed sign: FP64 pairs only
     sphlib.Context(dict(cfg, pair_precision=1, vstar_literal=1), stream=0).close()
     for bad in (dict(vstar_literal=1), dict(pair_precision=1, vstar_literal=2)):

@@ -161,6 +161,19 @@ def test_slab_temperature_parity(sph, oracle):
     assert abs((rc * g).sum() - (rc * f["T"]).sum()) <= 1e-6 * (rc * f["T"]).sum()
 
 
+def test_slab_thermal_bound_parity(sph, oracle):
+    # the paper's smoothing length h = 1.0 dx with a step that Eq. (26) caps:
+    # both sides take the same bounded step and the same temperatures
+    case = W.slab(h_over_dx=1.0, dt_ad=1.0)
+    ctx = _ctx(sph, case)
+    sim = oracle.OracleSim(case)
+    ctx.sph_step(10)
+    sim.step(10)
+    assert ctx.sph_get_info()["t"] == sim.time()["t"] < 10 * 1.0
+    g, r = ctx.sph_read_fields("T"), sim.field("T")
+    assert np.max(np.abs(g - r)) <= 1e-5
+
+
 def test_rotating_cylinder_torque_heat_parity(sph, oracle):
     case = W.rotating_cylinder()
     ctx = _ctx(sph, case)

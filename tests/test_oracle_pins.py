@@ -562,3 +562,37 @@ def test_vstar_sign_reading(oracle, literal):
         assert bump > 10.0  # from 1.0
     else:
         assert abs(bump) < 0.1
+
+
+# ----------------------------------------------- Eq. (26) thermal bound ---
+def _slab_bounded(oracle, h_over_dx, cfl_T, steps=40):
+    # u_ref so small that only the thermal bound limits the advection step
+    case = W.slab(h_over_dx=h_over_dx, dt_ad=1.0)
+    case.config = dict(case.config, cfl_T=cfl_T)
+    sim = oracle.OracleSim(case)
+    rc = np.where(W.flatten(case)["mat"] == 0, 1000.0, 2000.0)
+    E0 = (rc * sim.field("T")).sum()
+    sim.step(steps)
+    return sim, rc, E0
+
+
+def test_thermal_bound_keeps_conduction_stable_at_paper_h(oracle):
+    # at the paper's h = 1.0 dx the printed bound (cfl_T = 0.5) keeps the
+    # explicit Cleary update bounded: the temperatures stay within the
+    # initial range [0, 1] (maximum principle) and rho c_p T is conserved
+    sim, rc, E0 = _slab_bounded(oracle, 1.0, 0.5)
+    T = sim.field("T")
+    assert sim.time()["t"] < 40 * 1.0  # the bound, not u_ref, set the step
+    assert T.min() >= -1e-12 and T.max() <= 1.0 + 1e-12
+    assert abs((rc * T).sum() - E0) < 1e-12 * E0
+
+
+def test_thermal_bound_coefficient_at_h13(oracle):
+    # at h = 1.3 dx in 3-D many more partners contribute, the update's largest
+    # decay rate grows, and the printed coefficient no longer suffices: the
+    # temperatures run away; 0.2 keeps them bounded
+    sim, _, _ = _slab_bounded(oracle, 1.3, 0.5)
+    assert np.abs(sim.field("T")).max() > 10.0
+    sim, _, _ = _slab_bounded(oracle, 1.3, 0.2)
+    T = sim.field("T")
+    assert T.min() >= -1e-12 and T.max() <= 1.0 + 1e-12
