@@ -57,8 +57,8 @@ BYTES_PER_LIST_ENTRY = 4
 # Units: pass D and VT per partner found, M and C per directed fluid pair.
 # Valid only for the kernel sources they were taken on (hash below); after
 # any change to them the roofline reports traffic = null.
-TRAFFIC = {"sources_sha256_16": "c264847d03508b7d",
-           "bytes_per_unit": {"pass_D": 6.60, "pass_VT": 5.41, "pass_M": 6.26, "pass_C": 5.50}}
+TRAFFIC = {"sources_sha256_16": "8f39f3b155f4e92e",
+           "bytes_per_unit": {"pass_D": 7.15, "pass_VT": 5.35, "pass_M": 6.19, "pass_C": 5.44}}
 KERNEL_SOURCES = ("paper_2512_09904_b300/csrc/sph_kernels.cu", "paper_2512_09904_b300/csrc/sph_internal.cuh",
                   "paper_2512_09904_b300/csrc/sph_kernels.cuh")
 
@@ -280,43 +280,54 @@ def main():
     ms_max, units_all = reduce_timing(ms, units, world, device="cuda")
     value = units_all / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (largest share of device time)
+    # roofline of every pair pass; the dominant one (largest share of device
+    # time) is the line's `roofline`
     peaks, src = measured_peaks()
-    dom = max(("pass_D", "pass_VT", "pass_M", "pass_C"), key=lambda k: prof[k][0])
-    dms, dcnt = prof[dom]
-    avg_s = dms / max(dcnt, 1) * 1e-3
-    if dom == "pass_D":
-        flops = search["candidates"] * FLOP_D["cand"] + search["partners"] * FLOP_D["pair"]
-    else:
-        fl = dict(pass_M=FLOP_M, pass_C=FLOP_C, pass_VT=FLOP_VT)[dom]
-        flops = ff * fl["ff"] + fw * fl["fw"]
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     nominal_fp32 = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipes at max clock
     # the ALU denominator: FP32 FMA throughput measured on this device by the library's probe
     peak_fp32, probe_ms = sph.sph_fma_peak(reps=5)
-    achieved = flops / avg_s / 1e12
-    # HBM bytes per launch: own state in and out plus one pass over the lists
-    # (pass D writes them; VT reads them like M and C)
-    per_particle = dict(pass_M=BYTES_M, pass_C=BYTES_C, pass_VT=BYTES_VT, pass_D=BYTES_D)[dom]
-    n_part = search["searched"] if dom in ("pass_D", "pass_VT") else case.n_fluid
-    n_list = search["partners"] if dom in ("pass_D", "pass_VT") else ff + fw
-    bytes_launch = n_part * per_particle + BYTES_PER_LIST_ENTRY * n_list
-    hbm_gbs = bytes_launch / avg_s / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6505.9)
+    traffic_ok = kernel_sources_hash() == TRAFFIC["sources_sha256_16"]
+
+    def pass_roofline(k):
+        kms, kcnt = prof[k]
+        avg_s = kms / max(kcnt, 1) * 1e-3
+        if k == "pass_D":
+            flops = search["candidates"] * FLOP_D["cand"] + search["partners"] * FLOP_D["pair"]
+        else:
+            fl = dict(pass_M=FLOP_M, pass_C=FLOP_C, pass_VT=FLOP_VT)[k]
+            flops = ff * fl["ff"] + fw * fl["fw"]
+        # HBM bytes per launch: own state in and out plus one pass over the
+        # lists (pass D writes them; VT reads them like M and C)
+        per_particle = dict(pass_M=BYTES_M, pass_C=BYTES_C, pass_VT=BYTES_VT, pass_D=BYTES_D)[k]
+        n_part = search["searched"] if k in ("pass_D", "pass_VT") else case.n_fluid
+        n_list = search["partners"] if k in ("pass_D", "pass_VT") else ff + fw
+        bytes_launch = n_part * per_particle + BYTES_PER_LIST_ENTRY * n_list
+        achieved = flops / avg_s / 1e12
+        hbm_gbs = bytes_launch / avg_s / 1e9
+        traffic = TRAFFIC["bytes_per_unit"][k] * n_list if traffic_ok else None
+        return {"kernel": "k_" + k.replace("pass_", "pass"), "achieved": achieved, "frac": achieved / peak_fp32,
+                "traffic": traffic, "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": kcnt,
+                "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                        "bytes_per_launch": bytes_launch}}
+
+    kernels = {k: pass_roofline(k) for k in ("pass_D", "pass_VT", "pass_M", "pass_C")}
+    dom = max(kernels, key=lambda k: prof[k][0])
+    d = kernels[dom]
     total_prof = sum(v[0] for v in prof.values())
-    traffic = None
-    if kernel_sources_hash() == TRAFFIC["sources_sha256_16"]:
-        n_units = search["partners"] if dom in ("pass_D", "pass_VT") else ff + fw
-        traffic = TRAFFIC["bytes_per_unit"][dom] * n_units
-    roofline = {"bound": "alu", "kernel": "k_" + dom.replace("pass_", "pass"), "achieved": achieved,
-                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": traffic,
+    roofline = {"bound": "alu", "kernel": d["kernel"], "achieved": d["achieved"],
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": d["frac"], "traffic": d["traffic"],
                 "peak_source": f"measured: FP32 FMA probe (sph_fma_peak, best of 5 launches of {probe_ms:.2f} ms); "
                                f"nominal 148 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz = {nominal_fp32:.1f} TFLOP/s",
-                "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches": dcnt,
-                "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
+                "flops_per_launch": d["flops_per_launch"], "avg_launch_ms": d["avg_launch_ms"],
+                "launches": d["launches"], "pairs_fluid_fluid": ff, "pairs_fluid_wall": fw, "search": search,
                 "timing": "per-group device times from a replay of the timed steps with event records "
                           f"between kernel groups (same sub-steps: {replay_substeps == substeps})",
-                "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
-                        "frac": hbm_gbs / peaks.get("hbm_gbs", 6505.9), "bytes_per_launch": bytes_launch},
+                "hbm": d["hbm"],
+                "kernels": {k: {x: v[x] for x in ("avg_launch_ms", "launches", "achieved", "frac", "traffic")}
+                            | {"hbm_gbs": v["hbm"]["achieved_gbs"], "hbm_frac": v["hbm"]["frac"]}
+                            for k, v in kernels.items()},
                 "share": {k: round(v[0] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,6 +338,7 @@ def main():
                       "pair_arith": "f32", "integration_and_reductions": "f64",
                       "l2": "inputs larger than L2 (~0.7 GB resident state)",
                       "parallelism": f"replicas x{world}", "torque_avg_Nm": th["torque_avg"],
+                      "oil_particle_advection_steps_per_s": case.n_fluid * world * args.steps / (ms_max * 1e-3),
                       "heat_J": th["heat"],
                       "pair_variant": {k: ctx_tuning[k] for k in ("list_batch", "tpp", "block")},
                       "autotune": tune},
