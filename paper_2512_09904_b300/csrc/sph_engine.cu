@@ -133,6 +133,7 @@ struct Engine {
     double* d_field = nullptr;
     std::vector<HostCase> cases;
     std::vector<CaseState> st_h;
+    std::vector<CaseDev> cdev_h;  // host copies of the case table (for the single-case parameter copy)
     RangeAlloc ids, cells;
     bool need_prepare = false;
     int64_t graph_steps = 0;  // advection steps launched so far
@@ -238,6 +239,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     B.ncells = (int)cells_cap;
     B.max_chunks = (int)((n + RED_CHUNK - 1) / RED_CHUNK) + c_cap + 1;
     B.hist_cap = hist_cap;
+    B.one_case = -1;  // set when a step graph is captured over a single case
     cudaError_t e = cudaSuccess;
 #define AL(p, cnt) \
     if (e == cudaSuccess) e = dalloc(E, &(p), (size_t)(cnt))
@@ -307,6 +309,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     if (B.tune_block == 0) B.tune_block = 128;
     E.cases.assign(c_cap, HostCase{});
     E.st_h.assign(c_cap, CaseState{});
+    E.cdev_h.assign(c_cap, CaseDev{});
     E.ids.reset(n_cap);
     E.cells.reset(cells_cap);
     E.allocated = true;
@@ -555,6 +558,7 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     B.n = (int)(at + n);
     E.cases[slot] = H;
     E.st_h[slot] = S;
+    E.cdev_h[slot] = C;
     E.need_prepare = true;
     E.graph_dirty = true;
     if (slot_out) *slot_out = slot;
@@ -586,6 +590,21 @@ static sph_status capture(Engine& E) {
     E.B.visc_heat = 0;
     for (const HostCase& H : E.cases)
         if (H.used && H.visc_heat) E.B.visc_heat = 1;
+    // exactly one case holds slots (none retiring): the pair passes take its
+    // constants from their parameter block
+    E.B.one_case = -1;
+    {
+        int used = 0, k1 = -1;
+        for (int k = 0; k < E.c_cap; ++k)
+            if (E.cases[k].used) {
+                ++used;
+                k1 = k;
+            }
+        if (used == 1) {
+            E.B.one_case = k1;
+            E.B.one = E.cdev_h[k1];
+        }
+    }
     {
         // torque chunks of the resident rigid bodies (fixed TQ_CHUNK id blocks from each body's start)
         std::vector<int4> tqc;

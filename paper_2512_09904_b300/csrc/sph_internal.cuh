@@ -141,10 +141,12 @@ __device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, f
 
 // Exact pair-membership rule on the FP64 snapshot: 0 < r^2 < R2 with
 // r^2 = ((dx*dx + dy*dy) + dz*dz) in round-to-nearest, no contraction, and
-// the minimum image on periodic axes.
-static __device__ __noinline__ bool member_fp64(const CaseDev& C, const double* __restrict__ Yx,
-                                         const double* __restrict__ Yy,
-                                         const double* __restrict__ Yz, int i, int j) {
+// the minimum image on periodic axes.  Cg is the case in the global case
+// table (never a copy in a kernel's parameter block: the call is not inlined).
+static __device__ __noinline__ bool member_fp64(const CaseDev* __restrict__ Cg, const double* __restrict__ Yx,
+                                                const double* __restrict__ Yy, const double* __restrict__ Yz,
+                                                int i, int j) {
+    const CaseDev& C = *Cg;
     double d[3] = {__dsub_rn(Yx[i], Yx[j]), __dsub_rn(Yy[i], Yy[j]), __dsub_rn(Yz[i], Yz[j])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -309,8 +311,11 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
 // the FP64 snapshot inside a relative guard band, so the pair set equals the
 // FP64 rule exactly.  f(j, sj, rx, ry, rz, r2, code) receives r_ij = r_i - r_j
 // and the geometry-cell offset packed as code = (dx+1) | (dy+1) << 2 | (dz+1) << 4.
+// C may be a parameter-block copy of the case; Cg is the same case in the
+// global table, for the rare FP64 re-check.
 template <class F>
-__device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32_t* __restrict__ cstart,
+__device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const CaseDev* Cg,
+                                                  const uint32_t* __restrict__ cstart,
                                                   const float4* __restrict__ snap,
                                                   const double* __restrict__ Yx,
                                                   const double* __restrict__ Yy,
@@ -324,7 +329,7 @@ __device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const uint32
         bool in;
         if (r2 >= C.R2hi) in = false;
         else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
-        else in = member_fp64(C, Yx, Yy, Yz, i, j);
+        else in = member_fp64(Cg, Yx, Yy, Yz, i, j);
         if (in) f(j, sj, rx, ry, rz, r2, (int)code);
     });
 }

@@ -474,7 +474,7 @@ __global__ void k_segments(Bufs B) {
 }
 
 // --------------------------------------------------------- pair passes ----
-#define PAIR_ARGS C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2]
+#define PAIR_ARGS B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2]
 
 constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
 
@@ -546,7 +546,8 @@ struct CellVis {
     __device__ __forceinline__ bool lead() const { return true; }
     template <int PART, class F>
     __device__ __forceinline__ void run(F&& f) const {
-        for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i],
+        // the overflow kernels read the case table: C is the global entry
+        for_each_neighbor(C, &C, PAIR_ARGS, i, si, B.CELLK[i],
                           [&](int j, float4 sj, float rx, float ry, float rz, float r2, int) {
                               const bool fj = tag_kind(__float_as_uint(sj.w)) == KIND_FLUID;
                               if ((fj && (PART & PART_FLUID)) || (!fj && (PART & PART_WALL)))
@@ -557,18 +558,27 @@ struct CellVis {
 
 __device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && !(cnt & NB_OVF); }
 
+// The constants of a particle's case: with ONE (a single resident case) the
+// copy in the kernel's parameter block, otherwise the case table.
+template <bool ONE>
+__device__ __forceinline__ const CaseDev& case_dev(const Bufs& B, uint32_t tag) {
+    if constexpr (ONE) return B.one;
+    else return B.cases[tag_case(tag)];
+}
+
 // Pass D: the advection step's neighbour search (27-cell loop, exact FP64
 // membership) writes every particle's partner list, and fluid particles get
 // their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
 // runs over all partners (fluid and wall) plus the particle itself.  Static
 // walls of fixed temperature have no pair sums of their own and get no list.
+template <bool ONE>
 __global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
     const uint32_t kind = tag_kind(tag);
-    const CaseDev& C = B.cases[tag_case(tag)];
+    const CaseDev& C = case_dev<ONE>(B, tag);
     const MatDev& Mi = C.mat[tag_mat(tag)];
     if ((kind == KIND_STATIC && Mi.fixed_T) || !B.st[tag_case(tag)].active) {
         B.NBC[i] = 0u;
@@ -578,7 +588,8 @@ __global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
     uint32_t* nb = B.NB + i;
     float sum = C.w0;
     uint32_t nf = 0, nw = 0;
-    for_each_neighbor(PAIR_ARGS, i, si, B.CELLK[i], [&](int j, float4 sj, float, float, float, float r2, int code) {
+    for_each_neighbor(C, B.cases + tag_case(tag), PAIR_ARGS, i, si, B.CELLK[i],
+                      [&](int j, float4 sj, float, float, float, float r2, int code) {
         sum += kernel_W(C, r2 * rsqrtf(fmaxf(r2, 1e-30f)));  // r from the reciprocal root estimate
         const uint32_t e = (uint32_t)j | ((uint32_t)code << 26);
         const bool room = nf + nw < (uint32_t)NB_CAP;
@@ -753,7 +764,7 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     }
 }
 
-template <bool UNI, int BATCH, int TPP, bool VH = false>
+template <bool UNI, int BATCH, int TPP, bool ONE, bool VH = false>
 __global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
@@ -766,7 +777,7 @@ __global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
     if (!B.st[tag_case(tag)].active) return;
-    const CaseDev& C = B.cases[tag_case(tag)];
+    const CaseDev& C = case_dev<ONE>(B, tag);
     vt_particle<UNI, ListVis<BATCH, TPP>, VH>(B, par, i, si, tag, C, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
 }
 
@@ -908,7 +919,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
     B.TORQ[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
 }
 
-template <bool UNI, int BATCH, int TPP>
+template <bool UNI, int BATCH, int TPP, bool ONE>
 __global__ void __launch_bounds__(256) k_passM(Bufs B, int par) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
@@ -921,7 +932,7 @@ __global__ void __launch_bounds__(256) k_passM(Bufs B, int par) {
         const CaseState& S = B.st[tag_case(tag)];
         const int first = S.nsub == 0;  // first sub-step of the advection step
         if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
-            const CaseDev& C = B.cases[tag_case(tag)];
+            const CaseDev& C = case_dev<ONE>(B, tag);
             m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub}, &c, &vb);
         } else if (!S.active && first && tag_kind(tag) == KIND_FLUID && sub == 0) {
             // a case that does not advance still needs its work positions in the new order
@@ -999,7 +1010,7 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
     B.DR[1 - par][i] = drho;
 }
 
-template <bool UNI, int BATCH, int TPP>
+template <bool UNI, int BATCH, int TPP, bool ONE>
 __global__ void __launch_bounds__(256) k_passC(Bufs B, int par) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
@@ -1010,7 +1021,7 @@ __global__ void __launch_bounds__(256) k_passC(Bufs B, int par) {
     const uint32_t tag = __float_as_uint(si.w);
     const CaseState& S = B.st[tag_case(tag)];
     if (!S.active) return;
-    const CaseDev& C = B.cases[tag_case(tag)];
+    const CaseDev& C = case_dev<ONE>(B, tag);
     c_particle<UNI>(B, par, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
 }
 
@@ -1395,28 +1406,35 @@ static inline int pair_block(const Bufs& B) {
 
 cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
     if (B.fp64) return launch_passD64(B, par, s);
-    k_passD<<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
+    if (B.one_case >= 0) k_passD<true><<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
+    else k_passD<false><<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
     return cudaGetLastError();
 }
 
 
 // Pair-pass variant: list entries loaded together (B.tune_batch), threads per
-// particle (B.tune_tpp) and block size (B.tune_block).
-#define DISPATCH_PASS(KERNEL, UNI, S, ...)                                                          \
+// particle (B.tune_tpp), block size (B.tune_block) and, for a single resident
+// case, its constants from the parameter block (B.one_case >= 0).
+#define DISPATCH_BT(KERNEL, UNI, ONE, S, ...)                                                      \
     do {                                                                                           \
         const int tpp_ = B.tune_tpp == 2 ? 2 : 1;                                                  \
         const int blk_ = pair_block(B);                                                            \
         const int grd_ = grid_1to1(B.n * tpp_, blk_);                                              \
         switch (B.tune_batch * 4 + tpp_) {                                                         \
-        case 1 * 4 + 1: KERNEL<UNI, 1, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 2 * 4 + 1: KERNEL<UNI, 2, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 4 * 4 + 1: KERNEL<UNI, 4, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 1 * 4 + 2: KERNEL<UNI, 1, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 2 * 4 + 2: KERNEL<UNI, 2, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 4 * 4 + 2: KERNEL<UNI, 4, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        case 8 * 4 + 2: KERNEL<UNI, 8, 2><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;              \
-        default: KERNEL<UNI, 8, 1><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;                     \
+        case 1 * 4 + 1: KERNEL<UNI, 1, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 2 * 4 + 1: KERNEL<UNI, 2, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 4 * 4 + 1: KERNEL<UNI, 4, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 1 * 4 + 2: KERNEL<UNI, 1, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 2 * 4 + 2: KERNEL<UNI, 2, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 4 * 4 + 2: KERNEL<UNI, 4, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        case 8 * 4 + 2: KERNEL<UNI, 8, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
+        default: KERNEL<UNI, 8, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;                \
         }                                                                                          \
+    } while (0)
+#define DISPATCH_PASS(KERNEL, UNI, S, ...)                                                         \
+    do {                                                                                           \
+        if (B.one_case >= 0) DISPATCH_BT(KERNEL, UNI, true, S, __VA_ARGS__);                       \
+        else DISPATCH_BT(KERNEL, UNI, false, S, __VA_ARGS__);                                      \
     } while (0)
 
 cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
@@ -1425,10 +1443,10 @@ cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
         // cases with viscous-dissipation heating: one variant (8 entries per load, 1 thread per particle)
         const int blk = pair_block(B);
         if (B.uni_fluid) {
-            k_passVT<true, 8, 1, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT<true, 8, 1, false, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
             k_passVT_ovf<true, true><<<kOvfGrid, 128, 0, s>>>(B, par);
         } else {
-            k_passVT<false, 8, 1, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT<false, 8, 1, false, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
             k_passVT_ovf<false, true><<<kOvfGrid, 128, 0, s>>>(B, par);
         }
         return cudaGetLastError();

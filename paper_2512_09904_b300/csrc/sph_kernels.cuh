@@ -57,6 +57,11 @@ struct Bufs {
     // FP64 pair arithmetic (fp64 = 1): particle state in FP64 beside the
     // FP32 arrays above, which then only carry tags, snapshot offsets and lists
     int fp64;
+    // a single resident case (slot one_case >= 0): a copy of its constants in
+    // the parameter block, read by the pair passes as constant-bank operands
+    // instead of per-pair L1 loads from the case table; one_case = -1 otherwise
+    int one_case;
+    CaseDev one;
     double4_32a* V64[2];  // (vx, vy, vz, rho - rho0)
     double* DR64[2];
     double4_32a* VH64;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void visit64(const CaseDev& C, const Bufs& B, int i, 
             for (uint32_t q = 0; q < ((cnt >> 8) & 255u); ++q)
                 emit((int)(B.NB[(size_t)(NB_CAP - 1 - q) * stride + i] & NB_JMASK));
     } else {
-        for_each_neighbor(C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2], i, B.SNAP[i], B.CELLK[i],
+        for_each_neighbor(C, &C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2], i, B.SNAP[i], B.CELLK[i],
                           [&](int j, float4, float, float, float, float, int) { emit(j); });
     }
 }
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_passD64(Bufs B, int par) {
     uint32_t* nb = B.NB + i;
     double sum = C.w0_64;
     uint32_t nf = 0, nw = 0;
-    for_each_neighbor(C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2], i, si, B.CELLK[i],
+    for_each_neighbor(C, &C, B.CSTART, B.SNAP, B.Y[0], B.Y[1], B.Y[2], i, si, B.CELLK[i],
                       [&](int j, float4 sj, float, float, float, float, int code) {
                           double rx, ry, rz;
                           sum += W64(C, sqrt(geom64(C, B, i, j, rx, ry, rz)));
