@@ -125,13 +125,13 @@ struct CaseState {
 // dW/dr = -(5 alpha / h) q (1 - q/2)^3, q = r/h.
 __device__ __forceinline__ float kernel_W(const CaseDev& C, float r) {
     float q = r * C.inv_h;
-    float t = 1.0f - 0.5f * q;
+    float t = fmaf(-0.5f, q, 1.0f);
     float t2 = t * t;
-    return C.kw * t2 * t2 * (1.0f + 2.0f * q);
+    return C.kw * t2 * t2 * fmaf(2.0f, q, 1.0f);
 }
 __device__ __forceinline__ float kernel_dW(const CaseDev& C, float r) {
     float q = r * C.inv_h;
-    float t = 1.0f - 0.5f * q;
+    float t = fmaf(-0.5f, q, 1.0f);
     return C.kdw * q * t * t * t;
 }
 
@@ -167,7 +167,7 @@ static __device__ __noinline__ bool member_fp64(const CaseDev* __restrict__ Cg, 
 // margin, so the clipping stays conservative.
 __device__ __forceinline__ float row_half_width(const CaseDev& C, float d2) {
     const float e2 = C.R2hi - d2;
-    return e2 * rsqrtf(e2) + C.Rmargin;
+    return fmaf(e2, rsqrtf(e2), C.Rmargin);
 }
 
 // Distance from a point at offset o inside its sort cell (width w) to the
@@ -191,9 +191,9 @@ __device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* _
     const int sx = cl % nx, sy = (cl / nx) % ny, sz = cl / (nx * ny);
     const float wx = C.scellwf[0], wy = C.scellwf[1], wz = C.scellwf[2];
     // position of i inside its sort cell
-    const float ox = si.x - (float)(sx & 1) * wx;
-    const float oy = si.y - (float)(sy & 1) * wy;
-    const float oz = si.z - (float)(sz & 1) * wz;
+    const float ox = fmaf(-(float)(sx & 1), wx, si.x);
+    const float oy = fmaf(-(float)(sy & 1), wy, si.y);
+    const float oz = fmaf(-(float)(sz & 1), wz, si.z);
     const bool px = C.periodic & 1, py = C.periodic & 2, pz = C.periodic & 4;
     const float R2 = C.R2hi;
 #pragma unroll 1
@@ -248,9 +248,9 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
                                                    uint32_t key_i, F&& f) {
     if (C.periodic) {
         for_each_run(C, cstart, si, key_i, [&](int a, int b, int dcx, int dcy, int dcz) {
-            const float ox = si.x - (float)dcx * C.gcellwf[0];
-            const float oy = si.y - (float)dcy * C.gcellwf[1];
-            const float oz = si.z - (float)dcz * C.gcellwf[2];
+            const float ox = fmaf(-(float)dcx, C.gcellwf[0], si.x);
+            const float oy = fmaf(-(float)dcy, C.gcellwf[1], si.y);
+            const float oz = fmaf(-(float)dcz, C.gcellwf[2], si.z);
             const uint32_t code = (uint32_t)((dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4));
             for (int j = a; j < b; ++j) f(j, ox, oy, oz, code);
         });
@@ -260,9 +260,9 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
     const int cl = (int)key_i - C.cell_base;
     const int sx = cl % nx, sy = (cl / nx) % ny, sz = cl / (nx * ny);
     const float wx = C.scellwf[0], wy = C.scellwf[1], wz = C.scellwf[2];
-    const float cx = si.x - (float)(sx & 1) * wx;
-    const float cy = si.y - (float)(sy & 1) * wy;
-    const float cz = si.z - (float)(sz & 1) * wz;
+    const float cx = fmaf(-(float)(sx & 1), wx, si.x);
+    const float cy = fmaf(-(float)(sy & 1), wy, si.y);
+    const float cz = fmaf(-(float)(sz & 1), wz, si.z);
     const float R2 = C.R2hi, gw = C.gcellwf[0];
 #pragma unroll 1
     for (int dz = -2; dz <= 2; ++dz) {
@@ -271,7 +271,7 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
         const float gz = slab_gap(dz, wz, cz);
         if (gz * gz >= R2) continue;
         const int dcz = ((sz + dz) >> 1) - (sz >> 1);
-        const float oz = si.z - (float)dcz * C.gcellwf[2];
+        const float oz = fmaf(-(float)dcz, C.gcellwf[2], si.z);
 #pragma unroll 1
         for (int dy = -2; dy <= 2; ++dy) {
             const int y = sy + dy;
@@ -285,9 +285,9 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
             if (xl > xh) continue;
             const int row = C.cell_base + (z * ny + y) * nx;
             const int dcy = ((sy + dy) >> 1) - (sy >> 1);
-            const float oy = si.y - (float)dcy * C.gcellwf[1];
+            const float oy = fmaf(-(float)dcy, C.gcellwf[1], si.y);
             const int dcx = (xl >> 1) - (sx >> 1);
-            float ox = si.x - (float)dcx * gw;
+            float ox = fmaf(-(float)dcx, gw, si.x);
             uint32_t code = (uint32_t)((dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4));
             const int end = (int)cstart[row + xh + 1];
             int xb = (xl & ~1) + 2;  // first sort cell of the next geometry cell

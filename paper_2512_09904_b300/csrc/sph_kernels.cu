@@ -590,7 +590,9 @@ __global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
     uint32_t nf = 0, nw = 0;
     for_each_neighbor(C, B.cases + tag_case(tag), PAIR_ARGS, i, si, B.CELLK[i],
                       [&](int j, float4 sj, float, float, float, float r2, int code) {
-        sum += kernel_W(C, r2 * rsqrtf(fmaxf(r2, 1e-30f)));  // r from the reciprocal root estimate
+        // r from the reciprocal root estimate; the add is kept unfused so that
+        // every variant of the kernel rounds the sum alike
+        sum = __fadd_rn(sum, kernel_W(C, r2 * rsqrtf(fmaxf(r2, 1e-30f))));
         const uint32_t e = (uint32_t)j | ((uint32_t)code << 26);
         const bool room = nf + nw < (uint32_t)NB_CAP;
         if (tag_kind(__float_as_uint(sj.w)) == KIND_FLUID) {
@@ -832,11 +834,11 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
             const float4 vj = __ldg(VH + j);
             const float rho_j = Mj.rho0 + vj.w;
-            const float p_j = C.c02 * vj.w;
             // U_L - U_R = -(v_i - v_j).e_ij
             const float dU = -inv_r * dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz);
             const float beta = fminf(3.f * fmaxf(dU, 0.f), C.c0);
-            const float pstar = fmaf(0.5f, p_i + p_j, __fdividef(rho_i * rho_j * beta * dU, rho_i + rho_j));
+            // p_i + p_j with p_j = c0^2 (rho_j - rho0) fused
+            const float pstar = fmaf(0.5f, fmaf(C.c02, vj.w, p_i), __fdividef(rho_i * rho_j * beta * dU, rho_i + rho_j));
             const float coef = __fdividef(Mj.mass, rho_j) * pstar * dW * inv_r;
             ax = fmaf(coef, rx, ax);
             ay = fmaf(coef, ry, ay);
@@ -854,7 +856,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             const float rhoR = fmaf(PR, C.inv_c02, Mi.rho0);
             const float dUw = -2.f * dot3f(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z);
             const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
-            const float pstar = __fdividef(fmaf(rho_i, PR, rhoR * p_i) + rho_i * rhoR * beta * dUw, rho_i + rhoR);
+            const float pstar = __fdividef(fmaf(rho_i * rhoR * beta, dUw, fmaf(rho_i, PR, rhoR * p_i)), rho_i + rhoR);
             const float coef = C.vol * pstar * dW * inv_r;
             ax = fmaf(coef, rx, ax);
             ay = fmaf(coef, ry, ay);
@@ -865,9 +867,9 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         az = vis.sum(az);
         const float k = -2.f / rho_i;
         const float4 av = B.AV[i];
-        const float nvx = vi.x + dt * (k * ax + av.x + C.g[0]);
-        const float nvy = vi.y + dt * (k * ay + av.y + C.g[1]);
-        const float nvz = vi.z + dt * (k * az + av.z + C.g[2]);
+        const float nvx = fmaf(dt, fmaf(k, ax, av.x) + C.g[0], vi.x);
+        const float nvy = fmaf(dt, fmaf(k, ay, av.y) + C.g[1], vi.y);
+        const float nvz = fmaf(dt, fmaf(k, az, av.z) + C.g[2], vi.z);
         const float sp = sqrtf(dot3f(nvx, nvy, nvz, nvx, nvy, nvz));
         *case_out = (int)tag_case(tag);
         *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
@@ -879,8 +881,8 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double x = Xs[a][i];
-            x = x + hd * (double)vo[a];
-            x = x + hd * (double)vn[a];
+            x = __dadd_rn(x, __dmul_rn(hd, (double)vo[a]));
+            x = __dadd_rn(x, __dmul_rn(hd, (double)vn[a]));
             B.X[a][i] = x;
         }
         if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[tag_case(tag)].err, ERR_NAN);
@@ -904,7 +906,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         const float rhoR = fmaf(PR, C.inv_c02, Mj.rho0);
         const float dUw = -2.f * dot3f(nwi.x, nwi.y, nwi.z, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z);
         const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
-        const float pstar = __fdividef(fmaf(rho_j, PR, rhoR * p_j) + rho_j * rhoR * beta * dUw, rho_j + rhoR);
+        const float pstar = __fdividef(fmaf(rho_j * rhoR * beta, dUw, fmaf(rho_j, PR, rhoR * p_j)), rho_j + rhoR);
         // a_jw = -2 V_w / rho_j p* dW e_jw with e_jw = -r_ij / r; force on wall = -m_j a_jw
         const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * pstar * dW * inv_r;
         fx = fmaf(cf, rx, fx);
