@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -133,7 +134,8 @@ struct Engine {
     double* d_field = nullptr;
     std::vector<HostCase> cases;
     std::vector<CaseState> st_h;
-    std::vector<CaseDev> cdev_h;  // host copies of the case table (for the single-case parameter copy)
+    std::vector<CaseDev> cdev_h;  // host copies of the case table
+    PairTab tab{};                // pair constants of the resident cases, passed to the pair passes
     RangeAlloc ids, cells;
     bool need_prepare = false;
     int64_t graph_steps = 0;  // advection steps launched so far
@@ -415,6 +417,13 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.mat64[m].cp = M.cp;
         C.mat64[m].inv_rho0_cp = 1.0 / (M.rho0 * M.cp);
     }
+    // the fluid particles' material (the pair passes' single-material path
+    // reads it when every fluid particle of every resident case shares one)
+    for (size_t i = 0; i < c->kind.size(); ++i)
+        if (c->kind[i] == 0) {
+            C.fluid = C.mat[c->mat[i]];
+            break;
+        }
     int nb = 0;
     for (int b = 0; b < MAX_BODY; ++b) {
         BodyDev& Bd = C.body[b];
@@ -576,6 +585,42 @@ static cudaError_t mark(Engine& E, int cls, int sub) {
     return cudaEventRecordWithFlags(E.ev[k], E.cap, cudaEventRecordExternal);
 }
 
+// The pair constants of a case (host copy C) whose case-table entry is at
+// device address dev.
+static PairConst pair_const(const CaseDev& C, const CaseDev* dev) {
+    PairConst P{};
+    for (int a = 0; a < 3; ++a) {
+        P.gcellwf[a] = C.gcellwf[a];
+        P.scellwf[a] = C.scellwf[a];
+        P.inv_scellwf[a] = C.inv_scellwf[a];
+        P.g[a] = C.g[a];
+        P.ncell[a] = C.ncell[a];
+    }
+    P.Rmargin = C.Rmargin;
+    P.R2lo = C.R2lo;
+    P.R2hi = C.R2hi;
+    P.R2eps = C.R2eps;
+    P.inv_h = C.inv_h;
+    P.w0 = C.w0;
+    P.kw = C.kw;
+    P.kdw = C.kdw;
+    P.inv_sigma0 = C.inv_sigma0;
+    P.vol = C.vol;
+    P.inv_contact_full = C.inv_contact_full;
+    P.c0 = C.c0;
+    P.c02 = C.c02;
+    P.inv_c0 = C.inv_c0;
+    P.inv_c02 = C.inv_c02;
+    P.cell_base = C.cell_base;
+    P.periodic = C.periodic;
+    P.free_surface = C.free_surface;
+    P.visc_heat = C.visc_heat;
+    P.fluid = C.fluid;
+    P.mat = reinterpret_cast<const MatDev*>(reinterpret_cast<const char*>(dev) + offsetof(CaseDev, mat));
+    P.body = reinterpret_cast<const BodyDev*>(reinterpret_cast<const char*>(dev) + offsetof(CaseDev, body));
+    return P;
+}
+
 static sph_status capture(Engine& E) {
     // capture runs nothing; it needs a stream other than the legacy default one
     if (!E.cap) E_CUDA(E, cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking));
@@ -590,9 +635,10 @@ static sph_status capture(Engine& E) {
     E.B.visc_heat = 0;
     for (const HostCase& H : E.cases)
         if (H.used && H.visc_heat) E.B.visc_heat = 1;
-    // exactly one case holds slots (none retiring): the pair passes take its
-    // constants from their parameter block
+    // the pair passes' constants: entry 0 for a single resident case, else
+    // one entry per case slot (when the slots fit the table)
     E.B.one_case = -1;
+    E.tab = PairTab{};
     {
         int used = 0, k1 = -1;
         for (int k = 0; k < E.c_cap; ++k)
@@ -602,7 +648,10 @@ static sph_status capture(Engine& E) {
             }
         if (used == 1) {
             E.B.one_case = k1;
-            E.B.one = E.cdev_h[k1];
+            E.tab.c[0] = pair_const(E.cdev_h[k1], E.B.cases + k1);
+        } else if (E.c_cap <= PAIRTAB_MAX) {
+            for (int k = 0; k < E.c_cap; ++k)
+                if (E.cases[k].used) E.tab.c[k] = pair_const(E.cdev_h[k], E.B.cases + k);
         }
     }
     {
@@ -642,9 +691,9 @@ static sph_status capture(Engine& E) {
         if (e == cudaSuccess) e = launch_adv_begin(E.B, E.cap);
         if (e == cudaSuccess) e = launch_sort(E.B, p, E.cap);
         if (e == cudaSuccess) e = mark(E, SPH_PROF_SORT, -1);
-        if (e == cudaSuccess) e = launch_passD(E.B, p, E.cap);
+        if (e == cudaSuccess) e = launch_passD(E.B, p, E.tab, E.cap);
         if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_D, -1);
-        if (e == cudaSuccess) e = launch_passVT(E.B, p, E.cap);
+        if (e == cudaSuccess) e = launch_passVT(E.B, p, E.tab, E.cap);
         if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_VT, -1);
         if (E.prof) {
             // profiling: kcap unrolled sub-step slots with event records between
@@ -652,9 +701,9 @@ static sph_status capture(Engine& E) {
             for (int k = 0; k < E.kcap_max && e == cudaSuccess; ++k) {
                 e = launch_sub_begin(E.B, E.cap);
                 if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
-                if (e == cudaSuccess) e = launch_passM(E.B, p, E.cap);
+                if (e == cudaSuccess) e = launch_passM(E.B, p, E.tab, E.cap);
                 if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_M, k);
-                if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap);
+                if (e == cudaSuccess) e = launch_passC(E.B, p, E.tab, E.cap);
                 if (e == cudaSuccess) e = mark(E, SPH_PROF_PASS_C, k);
                 if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap);
                 if (e == cudaSuccess) e = mark(E, SPH_PROF_CONTROL, k);
@@ -682,8 +731,8 @@ static sph_status capture(Engine& E) {
                                                   cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
                     e = launch_sub_begin(E.B, E.cap2);
-                    if (e == cudaSuccess) e = launch_passM(E.B, p, E.cap2);
-                    if (e == cudaSuccess) e = launch_passC(E.B, p, E.cap2);
+                    if (e == cudaSuccess) e = launch_passM(E.B, p, E.tab, E.cap2);
+                    if (e == cudaSuccess) e = launch_passC(E.B, p, E.tab, E.cap2);
                     if (e == cudaSuccess) e = launch_sub_end(E.B, E.cap2);
                     if (e == cudaSuccess) e = launch_sub_cond(E.B, h, E.cap2);
                     cudaGraph_t bg = nullptr;

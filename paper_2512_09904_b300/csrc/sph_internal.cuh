@@ -90,9 +90,35 @@ struct CaseDev {
     int free_surface, kcap, n_body, fp64;
     int visc_heat;  // add the viscous-dissipation heating 2 mu S:S (extension; off in the paper)
     int vstar_lit;  // Eq. (13) with its printed sign (FP64 pairs only; off by default)
+    MatDev fluid;   // the material of the case's fluid particles, when they all share one
     MatDev mat[MAX_MAT];
     MatDev64 mat64[MAX_MAT];
     BodyDev body[MAX_BODY];
+};
+
+// The constants the pair passes read per pair, for one case: a table of them
+// over the resident cases fits a kernel's parameter block, where they are
+// constant-bank operands instead of loads from the global case table.
+// Materials and rigid bodies (read once per particle) stay in the case table.
+// Field names follow CaseDev's, so the pair code takes either.
+struct PairConst {
+    float gcellwf[3], scellwf[3], inv_scellwf[3];
+    float Rmargin, R2lo, R2hi, R2eps;
+    float inv_h, w0, kw, kdw, inv_sigma0, vol, inv_contact_full;
+    float c0, c02, inv_c0, inv_c02;
+    float g[3];
+    int ncell[3];
+    int cell_base, periodic, free_surface, visc_heat;
+    MatDev fluid;         // the material of the case's fluid particles, when they all share one
+    const MatDev* mat;    // the case's materials in the case table
+    const BodyDev* body;  // the case's rigid bodies in the case table
+};
+
+// Pair-pass constants of up to PAIRTAB_MAX cases, indexed by case slot (one
+// resident case: at index 0), passed by value to the pair passes.
+constexpr int PAIRTAB_MAX = 64;
+struct PairTab {
+    PairConst c[PAIRTAB_MAX];
 };
 
 struct CaseState {
@@ -123,13 +149,15 @@ struct CaseState {
 // ---------------------------------------------------------------- kernel ---
 // Wendland C2 (3-D, support 2h): W = alpha (1 - q/2)^4 (1 + 2q),
 // dW/dr = -(5 alpha / h) q (1 - q/2)^3, q = r/h.
-__device__ __forceinline__ float kernel_W(const CaseDev& C, float r) {
+template <class CC>
+__device__ __forceinline__ float kernel_W(const CC& C, float r) {
     float q = r * C.inv_h;
     float t = fmaf(-0.5f, q, 1.0f);
     float t2 = t * t;
     return C.kw * t2 * t2 * fmaf(2.0f, q, 1.0f);
 }
-__device__ __forceinline__ float kernel_dW(const CaseDev& C, float r) {
+template <class CC>
+__device__ __forceinline__ float kernel_dW(const CC& C, float r) {
     float q = r * C.inv_h;
     float t = fmaf(-0.5f, q, 1.0f);
     return C.kdw * q * t * t * t;
@@ -165,7 +193,8 @@ static __device__ __noinline__ bool member_fp64(const CaseDev* __restrict__ Cg, 
 // distance d2 (< R2) from a row's slab, plus Rmargin.  The square root is the
 // hardware reciprocal estimate: its relative error (~1e-7) is far inside the
 // margin, so the clipping stays conservative.
-__device__ __forceinline__ float row_half_width(const CaseDev& C, float d2) {
+template <class CC>
+__device__ __forceinline__ float row_half_width(const CC& C, float d2) {
     const float e2 = C.R2hi - d2;
     return fmaf(e2, rsqrtf(e2), C.Rmargin);
 }
@@ -183,8 +212,8 @@ __device__ __forceinline__ float slab_gap(int d, float w, float o) {
 // dcz) gets a slot range and its particles' geometry-cell offset from i's.
 // The clipping is conservative (guard-band radius plus Rmargin): every
 // partner of the FP64 rule is among the candidates.
-template <class F>
-__device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* __restrict__ cstart, float4 si,
+template <class CC, class F>
+__device__ __forceinline__ void for_each_run(const CC& C, const uint32_t* __restrict__ cstart, float4 si,
                                              uint32_t key_i, F&& run) {
     const int nx = C.ncell[0], ny = C.ncell[1], nz = C.ncell[2];
     const int cl = (int)key_i - C.cell_base;
@@ -243,8 +272,8 @@ __device__ __forceinline__ void for_each_run(const CaseDev& C, const uint32_t* _
 // axes a clipped row is one contiguous slot range, walked in a single loop
 // that steps the geometry-cell offset at the first slot of each next cell:
 // the threads of a warp then diverge per row, not per row and cell.
-template <class F>
-__device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint32_t* __restrict__ cstart, float4 si,
+template <class CC, class F>
+__device__ __forceinline__ void for_each_candidate(const CC& C, const uint32_t* __restrict__ cstart, float4 si,
                                                    uint32_t key_i, F&& f) {
     if (C.periodic) {
         for_each_run(C, cstart, si, key_i, [&](int a, int b, int dcx, int dcy, int dcz) {
@@ -313,8 +342,8 @@ __device__ __forceinline__ void for_each_candidate(const CaseDev& C, const uint3
 // and the geometry-cell offset packed as code = (dx+1) | (dy+1) << 2 | (dz+1) << 4.
 // C may be a parameter-block copy of the case; Cg is the same case in the
 // global table, for the rare FP64 re-check.
-template <class F>
-__device__ __forceinline__ void for_each_neighbor(const CaseDev& C, const CaseDev* Cg,
+template <class CC, class F>
+__device__ __forceinline__ void for_each_neighbor(const CC& C, const CaseDev* Cg,
                                                   const uint32_t* __restrict__ cstart,
                                                   const float4* __restrict__ snap,
                                                   const double* __restrict__ Yx,

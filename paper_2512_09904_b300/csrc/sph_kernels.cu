@@ -11,6 +11,8 @@
 // another block, so no kernel can hang.
 #include <cstdio>
 
+#include <type_traits>
+
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -483,8 +485,8 @@ constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
 // The list entries of a batch are loaded together so that BATCH independent
 // loads of the (DRAM-resident) list stream are in flight per thread.  With
 // TPP threads per particle, thread `sub` takes list slots sub, sub + TPP, ...
-template <int BATCH, int TPP, class F>
-__device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i, float4 si, int k0, int ks,
+template <int BATCH, int TPP, class CC, class F>
+__device__ __forceinline__ void list_walk(const CC& C, const Bufs& B, int i, float4 si, int k0, int ks,
                                           int cnt, int sub, F&& f) {
     const size_t stride = (size_t)B.nb_stride;
     const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
@@ -514,9 +516,9 @@ __device__ __forceinline__ void list_walk(const CaseDev& C, const Bufs& B, int i
 // Neighbours of a particle from its list (the common case), walked by TPP
 // adjacent threads; sum() adds the threads' partial sums (the same value on
 // each) and lead() marks the thread that stores the particle's results.
-template <int BATCH, int TPP = 1>
+template <int BATCH, int TPP, class CC>
 struct ListVis {
-    const CaseDev& C;
+    const CC& C;
     const Bufs& B;
     int i;
     float4 si;
@@ -558,12 +560,28 @@ struct CellVis {
 
 __device__ __forceinline__ bool listed(uint32_t cnt) { return (cnt & NB_HAS) && !(cnt & NB_OVF); }
 
-// The constants of a particle's case: with ONE (a single resident case) the
-// copy in the kernel's parameter block, otherwise the case table.
-template <bool ONE>
-__device__ __forceinline__ const CaseDev& case_dev(const Bufs& B, uint32_t tag) {
-    if constexpr (ONE) return B.one;
-    else return B.cases[tag_case(tag)];
+// Where the pair passes read a particle's case constants: the global case
+// table, or the table of pair constants in the kernel's parameter block
+// (indexed by case slot), or its entry 0 when a single case is resident.
+enum { CM_GLOBAL = 0, CM_ONE = 1, CM_TAB = 2 };
+// the pair passes' constant argument: the whole table only where it is read
+template <int CM>
+using PairArg = std::conditional_t<CM == CM_TAB, PairTab, PairConst>;
+template <int CM, class F>
+__device__ __forceinline__ void with_case(const Bufs& B, const PairArg<CM>& T, uint32_t tag, F&& f) {
+    if constexpr (CM == CM_GLOBAL) f(B.cases[tag_case(tag)]);
+    else if constexpr (CM == CM_ONE) f(T);
+    else f(T.c[tag_case(tag)]);
+}
+template <int CM>
+static inline const PairArg<CM>& pair_arg(const PairTab& T) {
+    if constexpr (CM == CM_TAB) return T;
+    else return T.c[0];
+}
+template <int BATCH, int TPP, class CC>
+__device__ __forceinline__ ListVis<BATCH, TPP, CC> list_vis(const CC& C, const Bufs& B, int i, float4 si,
+                                                           uint32_t cnt, int sub) {
+    return ListVis<BATCH, TPP, CC>{C, B, i, si, cnt, sub};
 }
 
 // Pass D: the advection step's neighbour search (27-cell loop, exact FP64
@@ -571,14 +589,9 @@ __device__ __forceinline__ const CaseDev& case_dev(const Bufs& B, uint32_t tag) 
 // their density re-initialised, Eq. (14) (free surface) or Eq. (15); sum W
 // runs over all partners (fluid and wall) plus the particle itself.  Static
 // walls of fixed temperature have no pair sums of their own and get no list.
-template <bool ONE>
-__global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B.n) return;
-    const float4 si = B.SNAP[i];
-    const uint32_t tag = __float_as_uint(si.w);
+template <class CC>
+__device__ __forceinline__ void d_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag, const CC& C) {
     const uint32_t kind = tag_kind(tag);
-    const CaseDev& C = case_dev<ONE>(B, tag);
     const MatDev& Mi = C.mat[tag_mat(tag)];
     if ((kind == KIND_STATIC && Mi.fixed_T) || !B.st[tag_case(tag)].active) {
         B.NBC[i] = 0u;
@@ -617,6 +630,15 @@ __global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par) {
     V[i].w = C.free_surface ? fmaxf(d, rr) : rr;
 }
 
+template <int CM>
+__global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par, const PairArg<CM> T) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const float4 si = B.SNAP[i];
+    const uint32_t tag = __float_as_uint(si.w);
+    with_case<CM>(B, T, tag, [&](const auto& C) { d_particle(B, par, i, si, tag, C); });
+}
+
 __device__ __forceinline__ float axial_torque(const BodyDev& Bd, const double* __restrict__ Yx,
                                               const double* __restrict__ Yy, const double* __restrict__ Yz,
                                               int i, float fx, float fy, float fz) {
@@ -630,11 +652,13 @@ __device__ __forceinline__ float harmonic2(float a, float b) {
     return s > 0.f ? __fdividef(2.f * a * b, s) : 0.f;
 }
 
-// UNI: every fluid particle of the case has the same material, so a fluid
-// partner's material equals the particle's own (no per-pair table loads).
-template <bool UNI>
-__device__ __forceinline__ const MatDev& fluid_mat(const CaseDev& C, const MatDev& Mi, uint32_t tj) {
-    return UNI ? Mi : C.mat[tag_mat(tj)];
+// UNI: every fluid particle of a case has the same material, the case's
+// `fluid` entry (a constant of the pair table), so neither a fluid particle's
+// own material nor its fluid partners' need a table load.
+template <bool UNI, class CC>
+__device__ __forceinline__ const MatDev& fluid_mat(const CC& C, uint32_t tj) {
+    if constexpr (UNI) return C.fluid;
+    else return C.mat[tag_mat(tj)];
 }
 
 // Pass VT for one particle: viscous acceleration (Eq. 10 second term; wall
@@ -644,17 +668,18 @@ __device__ __forceinline__ const MatDev& fluid_mat(const CaseDev& C, const MatDe
 // paper's thermal model omits; per case by its flag), S the symmetric part of
 // the velocity gradient sum_j V_j (v_j - v_i) (x) grad_i W_ij over fluid and
 // wall partners, added to dT/dt as Phi / (rho c_p).
-template <bool UNI, class Vis, bool VH = false>
+template <bool UNI, class Vis, bool VH = false, class CC>
 __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag,
-                                            const CaseDev& C, const Vis& vis) {
+                                            const CC& C, const Vis& vis) {
     const uint32_t kind = tag_kind(tag);
     const MatDev& Mi = C.mat[tag_mat(tag)];
     const float4* __restrict__ V = B.V[1 - par];
     const float* __restrict__ T32 = B.T32;
     const float Ti = T32[i];
     if (kind == KIND_FLUID) {
+        const MatDev& Mf = fluid_mat<UNI>(C, tag);
         const float4 vi = V[i];
-        const float rho_i = Mi.rho0 + vi.w;
+        const float rho_i = Mf.rho0 + vi.w;
         float ax = 0.f, ay = 0.f, az = 0.f, dT = 0.f;
         float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         const bool vh = VH && C.visc_heat;
@@ -665,18 +690,18 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
 #pragma unroll
                 for (int b = 0; b < 3; ++b) G[a][b] = fmaf(g * dv[a], rr[b], G[a][b]);
         };
-        const float Kii = 2.f * harmonic2(Mi.k, Mi.k), eii = harmonic2(Mi.mu, Mi.mu);
+        const float Kii = 2.f * harmonic2(Mf.k, Mf.k), eii = harmonic2(Mf.mu, Mf.mu);
         vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
-            const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
+            const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
             const float4 vj = __ldg(V + j);
             const float Vj = __fdividef(Mj.mass, Mj.rho0 + vj.w);
-            const float cv = 2.f * Vj * (UNI ? eii : harmonic2(Mi.mu, Mj.mu)) * inv_r * dW;
+            const float cv = 2.f * Vj * (UNI ? eii : harmonic2(Mf.mu, Mj.mu)) * inv_r * dW;
             ax = fmaf(cv, vi.x - vj.x, ax);
             ay = fmaf(cv, vi.y - vj.y, ay);
             az = fmaf(cv, vi.z - vj.z, az);
-            const float K = UNI ? Kii : 2.f * harmonic2(Mi.k, Mj.k);
+            const float K = UNI ? Kii : 2.f * harmonic2(Mf.k, Mj.k);
             dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
             if (VH && vh) grad(Vj * dW * inv_r, vj, rx, ry, rz);
         });
@@ -685,11 +710,11 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
             const float dW = kernel_dW(C, r2 * inv_r);
             const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
             const float4 vw = __ldg(V + j);
-            const float cv = 2.f * C.vol * Mi.mu * inv_r * dW;  // the wall takes the fluid's viscosity
+            const float cv = 2.f * C.vol * Mf.mu * inv_r * dW;  // the wall takes the fluid's viscosity
             ax = fmaf(cv, vi.x - vw.x, ax);
             ay = fmaf(cv, vi.y - vw.y, ay);
             az = fmaf(cv, vi.z - vw.z, az);
-            const float K = 2.f * harmonic2(Mi.k, Mj.k);
+            const float K = 2.f * harmonic2(Mf.k, Mj.k);
             dT = fmaf(C.vol * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
             if (VH && vh) grad(C.vol * dW * inv_r, vw, rx, ry, rz);
         });
@@ -708,14 +733,14 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
                     const float sab = 0.5f * (G[a][b] + G[b][a]);
                     ss = fmaf(sab, sab, ss);
                 }
-            dT = fmaf(2.f * Mi.mu, ss, dT);  // Phi, divided by rho_i c_p with the conduction sum below
+            dT = fmaf(2.f * Mf.mu, ss, dT);  // Phi, divided by rho_i c_p with the conduction sum below
         }
         ax = vis.sum(ax);
         ay = vis.sum(ay);
         az = vis.sum(az);
         dT = vis.sum(dT);
         const float inv_rho = 1.0f / rho_i;
-        if (vis.lead()) B.AV[i] = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, dT * inv_rho / Mi.cp);
+        if (vis.lead()) B.AV[i] = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, dT * inv_rho / Mf.cp);
         return;
     }
     const bool thermal = !Mi.fixed_T;
@@ -766,8 +791,8 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     }
 }
 
-template <bool UNI, int BATCH, int TPP, bool ONE, bool VH = false>
-__global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
+template <bool UNI, int BATCH, int TPP, int CM, bool VH = false>
+__global__ void __launch_bounds__(256) k_passVT(Bufs B, int par, const PairArg<CM> T) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
     if (i >= B.n) return;
@@ -779,8 +804,10 @@ __global__ void __launch_bounds__(256) k_passVT(Bufs B, int par) {
     const float4 si = B.SNAP[i];
     const uint32_t tag = __float_as_uint(si.w);
     if (!B.st[tag_case(tag)].active) return;
-    const CaseDev& C = case_dev<ONE>(B, tag);
-    vt_particle<UNI, ListVis<BATCH, TPP>, VH>(B, par, i, si, tag, C, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
+    with_case<CM>(B, T, tag, [&](const auto& C) {
+        const auto vis = list_vis<BATCH, TPP>(C, B, i, si, cnt, sub);
+        vt_particle<UNI, decltype(vis), VH>(B, par, i, si, tag, C, vis);
+    });
 }
 
 template <bool UNI, bool VH = false>
@@ -813,17 +840,17 @@ __global__ void k_halfkick(Bufs B, int par) {
 // problem (Eqs. 16-19) with half-kicked densities and the EoS (Eq. 2),
 // velocity kick, both half drifts of the position (FP64).  Rigid-body
 // particles record the pressure torque of their fluid partners.
-template <bool UNI, class Vis>
+template <bool UNI, class Vis, class CC>
 __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, int i, float4 si, uint32_t tag,
-                                           const CaseDev& C, const CaseState& S, const Vis& vis, int* case_out,
+                                           const CC& C, const CaseState& S, const Vis& vis, int* case_out,
                                            unsigned* vbits_out) {
     const uint32_t kind = tag_kind(tag);
     const float4* __restrict__ VH = B.VH;
     float4* Vout = B.V[par];
     const float hdt = S.hdtf, dt = S.dtf;
-    const MatDev& Mi = C.mat[tag_mat(tag)];
     const float4 vi = VH[i];
     if (kind == KIND_FLUID) {
+        const MatDev& Mi = fluid_mat<UNI>(C, tag);
         const float dh_i = vi.w;
         const float rho_i = Mi.rho0 + dh_i;
         const float p_i = C.c02 * dh_i;
@@ -831,7 +858,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
             const float dW = kernel_dW(C, r2 * inv_r);
-            const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
+            const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
             const float4 vj = __ldg(VH + j);
             const float rho_j = Mj.rho0 + vj.w;
             // U_L - U_R = -(v_i - v_j).e_ij
@@ -896,7 +923,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
     vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
-        const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
+        const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
         const float4 vj = __ldg(VH + j);
         const float rho_j = Mj.rho0 + vj.w;
         const float p_j = C.c02 * vj.w;
@@ -921,8 +948,8 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
     B.TORQ[B.ID[1 - par][i]] = axial_torque(Bd, B.Y[0], B.Y[1], B.Y[2], i, fx, fy, fz);
 }
 
-template <bool UNI, int BATCH, int TPP, bool ONE>
-__global__ void __launch_bounds__(256) k_passM(Bufs B, int par) {
+template <bool UNI, int BATCH, int TPP, int CM>
+__global__ void __launch_bounds__(256) k_passM(Bufs B, int par, const PairArg<CM> T) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
     int c = -1;
@@ -934,8 +961,9 @@ __global__ void __launch_bounds__(256) k_passM(Bufs B, int par) {
         const CaseState& S = B.st[tag_case(tag)];
         const int first = S.nsub == 0;  // first sub-step of the advection step
         if (S.active && (listed(cnt) || !(cnt & NB_HAS))) {
-            const CaseDev& C = case_dev<ONE>(B, tag);
-            m_particle<UNI>(B, par, first, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub}, &c, &vb);
+            with_case<CM>(B, T, tag, [&](const auto& C) {
+                m_particle<UNI>(B, par, first, i, si, tag, C, S, list_vis<BATCH, TPP>(C, B, i, si, cnt, sub), &c, &vb);
+            });
         } else if (!S.active && first && tag_kind(tag) == KIND_FLUID && sub == 0) {
             // a case that does not advance still needs its work positions in the new order
             B.X[0][i] = B.Y[0][i];
@@ -967,9 +995,9 @@ __global__ void __launch_bounds__(128) k_passM_ovf(Bufs B, int par) {
 
 // Pass C for one particle: Riemann continuity (Eq. 10 first line with v* of
 // Eq. 13) and the wall problem of Eqs. (16)-(17); second half kick.
-template <bool UNI, class Vis>
+template <bool UNI, class Vis, class CC>
 __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4 si, uint32_t tag,
-                                           const CaseDev& C, const CaseState& S, const Vis& vis) {
+                                           const CC& C, const CaseState& S, const Vis& vis) {
     const float4* __restrict__ Vin = B.V[par];
     float4* Vout = B.V[1 - par];
     const float4 vi = Vin[i];
@@ -977,13 +1005,13 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
         if (vis.lead()) Vout[i] = vi;
         return;
     }
-    const MatDev& Mi = C.mat[tag_mat(tag)];
+    const MatDev& Mi = fluid_mat<UNI>(C, tag);
     const float rho_i = Mi.rho0 + vi.w;
     float d = 0.f;
     vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
         const float inv_r = rsqrtf(r2);
         const float dW = kernel_dW(C, r2 * inv_r);
-        const MatDev& Mj = fluid_mat<UNI>(C, Mi, __float_as_uint(sj.w));
+        const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
         const float4 vj = __ldg(Vin + j);
         const float rho_j = Mj.rho0 + vj.w;
         // U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)), with
@@ -1012,8 +1040,8 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
     B.DR[1 - par][i] = drho;
 }
 
-template <bool UNI, int BATCH, int TPP, bool ONE>
-__global__ void __launch_bounds__(256) k_passC(Bufs B, int par) {
+template <bool UNI, int BATCH, int TPP, int CM>
+__global__ void __launch_bounds__(256) k_passC(Bufs B, int par, const PairArg<CM> T) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / TPP, sub = g % TPP;
     if (i >= B.n) return;
@@ -1023,8 +1051,9 @@ __global__ void __launch_bounds__(256) k_passC(Bufs B, int par) {
     const uint32_t tag = __float_as_uint(si.w);
     const CaseState& S = B.st[tag_case(tag)];
     if (!S.active) return;
-    const CaseDev& C = case_dev<ONE>(B, tag);
-    c_particle<UNI>(B, par, i, si, tag, C, S, ListVis<BATCH, TPP>{C, B, i, si, cnt, sub});
+    with_case<CM>(B, T, tag, [&](const auto& C) {
+        c_particle<UNI>(B, par, i, si, tag, C, S, list_vis<BATCH, TPP>(C, B, i, si, cnt, sub));
+    });
 }
 
 template <bool UNI>
@@ -1245,7 +1274,7 @@ template <class F>
 __device__ __forceinline__ void visit_any(const CaseDev& C, const Bufs& B, int i, float4 si, F&& f) {
     const uint32_t cnt = B.NBC[i];
     auto g = [&](int j, float4, float, float, float, float) { f(j); };
-    if (listed(cnt)) ListVis<1, 1>{C, B, i, si, cnt}.template run<PART_ALL>(g);
+    if (listed(cnt)) list_vis<1, 1>(C, B, i, si, cnt, 0).template run<PART_ALL>(g);
     else CellVis{C, B, i, si}.template run<PART_ALL>(g);
 }
 
@@ -1406,49 +1435,62 @@ static inline int pair_block(const Bufs& B) {
     return (B.tune_block == 64 || B.tune_block == 256) ? B.tune_block : 128;
 }
 
-cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s) {
+// Case-constant source of the pair passes (see with_case).
+static inline int case_mode(const Bufs& B) {
+    if (B.one_case >= 0) return CM_ONE;
+    return B.ncases <= PAIRTAB_MAX ? CM_TAB : CM_GLOBAL;
+}
+
+cudaError_t launch_passD(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
     if (B.fp64) return launch_passD64(B, par, s);
-    if (B.one_case >= 0) k_passD<true><<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
-    else k_passD<false><<<grid_1to1(B.n, pair_block(B)), pair_block(B), 0, s>>>(B, par);
+    const int blk = pair_block(B), grd = grid_1to1(B.n, blk);
+    switch (case_mode(B)) {
+    case CM_ONE: k_passD<CM_ONE><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_ONE>(T)); break;
+    case CM_TAB: k_passD<CM_TAB><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_TAB>(T)); break;
+    default: k_passD<CM_GLOBAL><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T)); break;
+    }
     return cudaGetLastError();
 }
 
 
 // Pair-pass variant: list entries loaded together (B.tune_batch), threads per
-// particle (B.tune_tpp), block size (B.tune_block) and, for a single resident
-// case, its constants from the parameter block (B.one_case >= 0).
-#define DISPATCH_BT(KERNEL, UNI, ONE, S, ...)                                                      \
+// particle (B.tune_tpp), block size (B.tune_block) and the source of the case
+// constants (case_mode).
+#define DISPATCH_BT(KERNEL, UNI, CM, S, ...)                                                       \
     do {                                                                                           \
         const int tpp_ = B.tune_tpp == 2 ? 2 : 1;                                                  \
         const int blk_ = pair_block(B);                                                            \
         const int grd_ = grid_1to1(B.n * tpp_, blk_);                                              \
         switch (B.tune_batch * 4 + tpp_) {                                                         \
-        case 1 * 4 + 1: KERNEL<UNI, 1, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 2 * 4 + 1: KERNEL<UNI, 2, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 4 * 4 + 1: KERNEL<UNI, 4, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 1 * 4 + 2: KERNEL<UNI, 1, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 2 * 4 + 2: KERNEL<UNI, 2, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 4 * 4 + 2: KERNEL<UNI, 4, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        case 8 * 4 + 2: KERNEL<UNI, 8, 2, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;         \
-        default: KERNEL<UNI, 8, 1, ONE><<<grd_, blk_, 0, S>>>(__VA_ARGS__); break;                \
+        case 1 * 4 + 1: KERNEL<UNI, 1, 1, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 2 * 4 + 1: KERNEL<UNI, 2, 1, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 4 * 4 + 1: KERNEL<UNI, 4, 1, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 1 * 4 + 2: KERNEL<UNI, 1, 2, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 2 * 4 + 2: KERNEL<UNI, 2, 2, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 4 * 4 + 2: KERNEL<UNI, 4, 2, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        case 8 * 4 + 2: KERNEL<UNI, 8, 2, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break; \
+        default: KERNEL<UNI, 8, 1, CM><<<grd_, blk_, 0, S>>>(__VA_ARGS__, pair_arg<CM>(T)); break;        \
         }                                                                                          \
     } while (0)
 #define DISPATCH_PASS(KERNEL, UNI, S, ...)                                                         \
     do {                                                                                           \
-        if (B.one_case >= 0) DISPATCH_BT(KERNEL, UNI, true, S, __VA_ARGS__);                       \
-        else DISPATCH_BT(KERNEL, UNI, false, S, __VA_ARGS__);                                      \
+        switch (case_mode(B)) {                                                                    \
+        case CM_ONE: DISPATCH_BT(KERNEL, UNI, CM_ONE, S, __VA_ARGS__); break;                      \
+        case CM_TAB: DISPATCH_BT(KERNEL, UNI, CM_TAB, S, __VA_ARGS__); break;                      \
+        default: DISPATCH_BT(KERNEL, UNI, CM_GLOBAL, S, __VA_ARGS__); break;                       \
+        }                                                                                          \
     } while (0)
 
-cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s) {
+cudaError_t launch_passVT(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
     if (B.fp64) return launch_passVT64(B, par, s);
     if (B.visc_heat) {
         // cases with viscous-dissipation heating: one variant (8 entries per load, 1 thread per particle)
         const int blk = pair_block(B);
         if (B.uni_fluid) {
-            k_passVT<true, 8, 1, false, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT<true, 8, 1, CM_GLOBAL, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T));
             k_passVT_ovf<true, true><<<kOvfGrid, 128, 0, s>>>(B, par);
         } else {
-            k_passVT<false, 8, 1, false, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par);
+            k_passVT<false, 8, 1, CM_GLOBAL, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T));
             k_passVT_ovf<false, true><<<kOvfGrid, 128, 0, s>>>(B, par);
         }
         return cudaGetLastError();
@@ -1468,7 +1510,7 @@ cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_passM(const Bufs& B, int par, cudaStream_t s) {
+cudaError_t launch_passM(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
     if (B.fp64) return launch_passM64(B, par, s);
     k_halfkick<<<grid_stride_grid(B.n, 256), 256, 0, s>>>(B, par);
     if (B.uni_fluid) {
@@ -1481,7 +1523,7 @@ cudaError_t launch_passM(const Bufs& B, int par, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s) {
+cudaError_t launch_passC(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
     if (B.fp64) return launch_passC64(B, par, s);
     if (B.uni_fluid) {
         DISPATCH_PASS(k_passC, true, s, B, par);

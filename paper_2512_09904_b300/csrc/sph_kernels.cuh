@@ -57,11 +57,9 @@ struct Bufs {
     // FP64 pair arithmetic (fp64 = 1): particle state in FP64 beside the
     // FP32 arrays above, which then only carry tags, snapshot offsets and lists
     int fp64;
-    // a single resident case (slot one_case >= 0): a copy of its constants in
-    // the parameter block, read by the pair passes as constant-bank operands
-    // instead of per-pair L1 loads from the case table; one_case = -1 otherwise
+    // the single resident case (its pair constants are entry 0 of the pair
+    // passes' PairTab), or -1
     int one_case;
-    CaseDev one;
     double4_32a* V64[2];  // (vx, vy, vz, rho - rho0)
     double* DR64[2];
     double4_32a* VH64;
@@ -76,11 +74,12 @@ struct Bufs {
 cudaError_t launch_vmax_init(const Bufs& B, int par, int lo, int hi, cudaStream_t s);
 cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s);
 cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s);  // hash..reorder + segments
-cudaError_t launch_passD(const Bufs& B, int par, cudaStream_t s);
-cudaError_t launch_passVT(const Bufs& B, int par, cudaStream_t s);
+// pair passes: T holds the pair constants of the resident cases (PairTab)
+cudaError_t launch_passD(const Bufs& B, int par, const PairTab& T, cudaStream_t s);
+cudaError_t launch_passVT(const Bufs& B, int par, const PairTab& T, cudaStream_t s);
 cudaError_t launch_sub_begin(const Bufs& B, cudaStream_t s);
-cudaError_t launch_passM(const Bufs& B, int par, cudaStream_t s);  // first sub-step: decided on the device
-cudaError_t launch_passC(const Bufs& B, int par, cudaStream_t s);
+cudaError_t launch_passM(const Bufs& B, int par, const PairTab& T, cudaStream_t s);  // first sub-step: decided on the device
+cudaError_t launch_passC(const Bufs& B, int par, const PairTab& T, cudaStream_t s);
 cudaError_t launch_sub_end(const Bufs& B, cudaStream_t s);
 cudaError_t launch_adv_end(const Bufs& B, int par, cudaStream_t s);
 cudaError_t launch_reduce_heat(const Bufs& B, int par, cudaStream_t s);
