@@ -72,6 +72,25 @@ def test_alone_equals_mixed_bitwise(sph):
     b.close()
 
 
+def test_case_constant_sources_agree_bitwise(sph):
+    # the pair passes read a case's constants from one parameter-block entry
+    # (a case alone), a per-slot table (batches of up to 64 slots) or the
+    # global case table (more slots): all three give the same bits
+    cs = _cases()
+    steps = 4
+    alone = _alone(sph, cs["gear"], steps)
+    n = sum(c.n_total for c in cs.values())
+    cells = sum(sph.cells_of(c) for c in cs.values()) + 10
+    for max_cases in (4, 80):  # 80 slots > the 64-entry table
+        b = sph.Batch(n, max_cases, cells, history_steps=16, stream=0)
+        slots = {k: b.admit(c, n_steps=0) for k, c in cs.items()}
+        b.step(steps)
+        got = {f: b.fields(slots["gear"], f) for f in ("pos", "vel", "rho", "T")}
+        got["th"] = b.torque_heat(slots["gear"])
+        _same(got, alone)
+        b.close()
+
+
 def test_admit_and_retire_while_others_run(sph):
     cs = _cases()
     ref_gear = _alone(sph, cs["gear"], 5)
