@@ -173,6 +173,16 @@ struct Engine {
             return (E).fail(SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, __LINE__); \
     } while (0)
 
+// One sph_add_* call, staged on the host until the case is admitted: ids
+// first .. first + n - 1, all of one kind (0 fluid, 1 solid), material and body.
+struct PBlock {
+    int kind = 0, body = -1, mat = 0;
+    int64_t n = 0, first = 0;
+    std::vector<double> pos;       // 3n
+    std::vector<double> vel, nrm;  // 3n, or empty: zero
+    std::vector<double> T, rho;    // n, or empty: the material's T_init, rho0
+};
+
 struct sph_ctx {
     sph_config cfg{};
     cudaStream_t stream = nullptr;
@@ -183,10 +193,9 @@ struct sph_ctx {
         double c[3], a[3], omega;
         bool set;
     } bodies[MAX_BODY]{};
-    // host staging, id order
-    std::vector<double> pos, vel, nrm, T, rho;
-    std::vector<int> kind, mat, body;
-    int64_t n_fluid = 0, n_solid = 0;
+    // host staging: one block per sph_add_* call, in id order
+    std::vector<PBlock> blocks;
+    int64_t n_total = 0, n_fluid = 0, n_solid = 0;
     int ncell[3]{};
     double cellw[3]{};
     double sigma0 = 0.0;
@@ -380,13 +389,14 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.kcap = c->kcap;
     double nu = 0.0, Tref = 0.0;
     int nfl = 0;
-    for (size_t i = 0; i < c->kind.size(); ++i)
-        if (c->kind[i] == 0) {
-            const sph_material& M = c->mats[c->mat[i]];
+    auto T_first = [&](const PBlock& P) { return P.T.empty() ? c->mats[P.mat].T_init : P.T[0]; };
+    for (const PBlock& P : c->blocks)
+        if (P.kind == 0) {
+            const sph_material& M = c->mats[P.mat];
             nu = std::max(nu, M.mu / M.rho0);
-            if (nfl++ == 0) Tref = c->T[i];
+            if (nfl++ == 0) Tref = T_first(P);
         }
-    if (nfl == 0 && !c->T.empty()) Tref = c->T[0];
+    if (nfl == 0 && !c->blocks.empty()) Tref = T_first(c->blocks[0]);
     C.nu_max = nu;
     C.T_ref = Tref;
     // Eq. (26): the thermal bound over every conducting material whose
@@ -394,9 +404,9 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     double dtT = INFINITY;
     const double hT = F.h_over_dx * F.dx;
     if (F.cfl_T > 0.0)
-        for (size_t i = 0; i < c->kind.size(); ++i) {
-            const sph_material& M = c->mats[c->mat[i]];
-            if ((c->kind[i] == 0 || !M.fixed_T) && M.k > 0.0)
+        for (const PBlock& P : c->blocks) {
+            const sph_material& M = c->mats[P.mat];
+            if ((P.kind == 0 || !M.fixed_T) && M.k > 0.0)
                 dtT = std::min(dtT, F.cfl_T * M.rho0 * M.cp * hT * hT / M.k);
         }
     C.dt_T = dtT;
@@ -419,9 +429,9 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     }
     // the fluid particles' material (the pair passes' single-material path
     // reads it when every fluid particle of every resident case shares one)
-    for (size_t i = 0; i < c->kind.size(); ++i)
-        if (c->kind[i] == 0) {
-            C.fluid = C.mat[c->mat[i]];
+    for (const PBlock& P : c->blocks)
+        if (P.kind == 0) {
+            C.fluid = C.mat[P.mat];
             break;
         }
     int nb = 0;
@@ -436,10 +446,10 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         }
         Bd.omega = c->bodies[b].omega;
         int64_t lo = -1, hi = -1;
-        for (size_t i = 0; i < c->kind.size(); ++i)
-            if (c->kind[i] == 1 && c->body[i] == b) {
-                if (lo < 0) lo = (int64_t)i;
-                hi = (int64_t)i + 1;
+        for (const PBlock& P : c->blocks)
+            if (P.kind == 1 && P.body == b) {
+                if (lo < 0) lo = P.first;
+                hi = P.first + P.n;
             }
         Bd.id_lo = (int)(H.id_base + (lo < 0 ? 0 : lo));
         Bd.id_hi = (int)(H.id_base + (hi < 0 ? 0 : hi));
@@ -449,17 +459,17 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
 
 static bool single_fluid_material(const sph_ctx* c) {
     int fm = -1;
-    for (size_t i = 0; i < c->kind.size(); ++i)
-        if (c->kind[i] == 0) {
-            if (fm < 0) fm = c->mat[i];
-            else if (c->mat[i] != fm) return false;
+    for (const PBlock& P : c->blocks)
+        if (P.kind == 0) {
+            if (fm < 0) fm = P.mat;
+            else if (P.mat != fm) return false;
         }
     return true;
 }
 
 // Append a staged case's particles to the packed array (sorted in prepare()).
 static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, int* slot_out) {
-    const int64_t n = (int64_t)c->kind.size();
+    const int64_t n = c->n_total;
     if (n == 0) return E.fail(SPH_EINVAL, "case has no particles");
     int slot = -1;
     for (int k = 0; k < E.c_cap; ++k)
@@ -503,25 +513,6 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     S.running = 1;
     S.init_pending = 1;
     S.steps_req = steps_req;
-    // host images of the new particles (slot order = id order)
-    std::vector<double> xs[3];
-    std::vector<float4> v(n), rn(n);
-    std::vector<int> ids(n);
-    std::vector<uint32_t> tags(n);
-    for (int a = 0; a < 3; ++a) xs[a].resize(n);
-    for (int64_t i = 0; i < n; ++i) {
-        const int k = c->kind[i], m = c->mat[i], b = c->body[i];
-        uint32_t kind = k == 0 ? KIND_FLUID : ((b >= 0 && c->bodies[b].set) ? KIND_ROT : KIND_STATIC);
-        tags[i] = make_tag((uint32_t)m, kind, kind == KIND_ROT ? (uint32_t)b : 0u, (uint32_t)slot);
-        ids[i] = (int)(H.id_base + i);
-        for (int a = 0; a < 3; ++a) xs[a][i] = c->pos[3 * i + a];
-        if (k == 0)
-            v[i] = make_float4((float)c->vel[3 * i], (float)c->vel[3 * i + 1], (float)c->vel[3 * i + 2],
-                               (float)(c->rho[i] - c->mats[m].rho0));
-        else
-            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        rn[i] = make_float4((float)c->nrm[3 * i], (float)c->nrm[3 * i + 1], (float)c->nrm[3 * i + 2], 0.f);
-    }
     Bufs& B = E.B;
     const int p = E.parity;
     const int64_t at = B.n;
@@ -529,40 +520,54 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     cudaStream_t s = E.stream;
     E_CUDA(E, cudaMemcpyAsync(B.cases + slot, &C, sizeof C, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemcpyAsync(B.st + slot, &S, sizeof S, cudaMemcpyHostToDevice, s));
-    for (int a = 0; a < 3; ++a) {
-        E_CUDA(E, cudaMemcpyAsync(B.X[a] + at, xs[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-        E_CUDA(E, cudaMemcpyAsync(B.RP[a] + idb, xs[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    }
-    E_CUDA(E, cudaMemcpyAsync(B.V[p] + at, v.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemsetAsync(B.DR[p] + at, 0, sizeof(float) * n, s));
-    E_CUDA(E, cudaMemcpyAsync(B.RN + idb, rn.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
     E_CUDA(E, cudaMemsetAsync(B.TORQ + idb, 0, sizeof(float) * n, s));
     E_CUDA(E, cudaMemsetAsync(B.TORQV + idb, 0, sizeof(float) * n, s));
     E_CUDA(E, cudaMemsetAsync(B.CF + idb, 0, sizeof(double) * n, s));
-    E_CUDA(E, cudaMemcpyAsync(B.T64[p] + at, c->T.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    std::vector<double4_32a> v64, rn64;
     if (B.fp64) {
-        v64.resize(n);
-        rn64.resize(n);
-        for (int64_t i = 0; i < n; ++i) {
-            const bool fl = c->kind[i] == 0;
-            v64[i] = fl ? make_double4_32a(c->vel[3 * i], c->vel[3 * i + 1], c->vel[3 * i + 2],
-                                       c->rho[i] - c->mats[c->mat[i]].rho0)
-                        : make_double4_32a(0.0, 0.0, 0.0, 0.0);
-            rn64[i] = make_double4_32a(c->nrm[3 * i], c->nrm[3 * i + 1], c->nrm[3 * i + 2], 0.0);
-        }
-        E_CUDA(E, cudaMemcpyAsync(B.V64[p] + at, v64.data(), sizeof(double4_32a) * n, cudaMemcpyHostToDevice, s));
         E_CUDA(E, cudaMemsetAsync(B.DR64[p] + at, 0, sizeof(double) * n, s));
-        E_CUDA(E, cudaMemcpyAsync(B.RN64 + idb, rn64.data(), sizeof(double4_32a) * n, cudaMemcpyHostToDevice, s));
         E_CUDA(E, cudaMemsetAsync(B.TORQ64 + idb, 0, sizeof(double) * n, s));
         E_CUDA(E, cudaMemsetAsync(B.TORQV64 + idb, 0, sizeof(double) * n, s));
     }
-    E_CUDA(E, cudaMemcpyAsync(B.ID[p] + at, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-    E_CUDA(E, cudaMemcpyAsync(B.TAG[p] + at, tags.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+    // the staged blocks go up as they are (one device scratch sized for the
+    // largest) and a kernel writes them into the packed layout
+    size_t scratch = 0;
+    for (const PBlock& P : c->blocks)
+        scratch = std::max(scratch, P.pos.size() + P.vel.size() + P.nrm.size() + P.T.size() + P.rho.size());
+    double* d = nullptr;
+    E_CUDA(E, cudaMallocAsync((void**)&d, sizeof(double) * std::max<size_t>(scratch, 1), s));
+    cudaError_t e = cudaSuccess;
+    for (const PBlock& P : c->blocks) {
+        double* q = d;
+        auto up = [&](const std::vector<double>& v) -> const double* {
+            if (v.empty() || e != cudaSuccess) return nullptr;
+            double* dst = q;
+            e = cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s);
+            q += v.size();
+            return dst;
+        };
+        const double* dpos = up(P.pos);
+        const double* dvel = up(P.vel);
+        const double* dnrm = up(P.nrm);
+        const double* dT = up(P.T);
+        const double* drho = up(P.rho);
+        const uint32_t kind = P.kind == 0 ? KIND_FLUID
+                                          : ((P.body >= 0 && c->bodies[P.body].set) ? KIND_ROT : KIND_STATIC);
+        const uint32_t tag = make_tag((uint32_t)P.mat, kind, kind == KIND_ROT ? (uint32_t)P.body : 0u, (uint32_t)slot);
+        const sph_material& M = c->mats[P.mat];
+        if (e == cudaSuccess)
+            e = launch_admit_block(B, p, (int)P.n, (int)(at + P.first), (int)(idb + P.first), tag, P.kind == 0 ? 1 : 0,
+                                   M.rho0, M.T_init, dpos, dvel, dnrm, dT, drho, s);
+        // the scratch is reused by the next block: let this one's kernel finish first
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+    }
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return E.fail(SPH_ECUDA, "admission: %s", cudaGetErrorString(e));
     // reference heat content and initial max speed from the appended block
     E_CUDA(E, launch_block_heat0(B, p, slot, (int)at, (int)n, B.PART, s));
     E_CUDA(E, launch_vmax_init(B, p, (int)at, (int)(at + n), s));
-    // the host images die at return: wait for the copies
+    // the admitted particles are in place before the case can step
     E_CUDA(E, cudaStreamSynchronize(s));
     B.n = (int)(at + n);
     E.cases[slot] = H;
@@ -979,27 +984,30 @@ static sph_status add_common(sph_ctx* c, int kind, int body, int mat, int64_t n,
     if (mat < 0 || mat >= MAX_MAT || !c->mat_set[mat]) return fail(c, SPH_EINVAL, "material %d not set", mat);
     if (kind == 1 && (body < -1 || body >= MAX_BODY)) return fail(c, SPH_EINVAL, "body id %d out of range", body);
     if (kind == 1 && n > 0 && !nrm) return fail(c, SPH_EINVAL, "solid particles need normals");
-    const int64_t n0 = (int64_t)c->kind.size();
+    const int64_t n0 = c->n_total;
     if (n0 + n > (int64_t)MAX_PARTICLES - 1) return fail(c, SPH_EINVAL, "more than 2^26 - 1 particles");
     const sph_material& M = c->mats[mat];
     for (int64_t q = 0; q < 3 * n; ++q)
         if (!std::isfinite(pos[q])) return fail(c, SPH_EINVAL, "non-finite position");
     if (first_id) *first_id = n0;
-    c->pos.insert(c->pos.end(), pos, pos + 3 * n);
-    if (vel) c->vel.insert(c->vel.end(), vel, vel + 3 * n);
-    else c->vel.resize(c->vel.size() + 3 * n, 0.0);
-    if (nrm) c->nrm.insert(c->nrm.end(), nrm, nrm + 3 * n);
-    else c->nrm.resize(c->nrm.size() + 3 * n, 0.0);
-    if (T) c->T.insert(c->T.end(), T, T + n);
-    else c->T.resize(c->T.size() + n, M.T_init);
-    const size_t r0 = c->rho.size();
-    c->rho.resize(r0 + n, M.rho0);
-    if (rho)
-        for (int64_t q = 0; q < n; ++q)
-            if (std::isfinite(rho[q])) c->rho[r0 + q] = rho[q];
-    c->kind.resize(c->kind.size() + n, kind);
-    c->mat.resize(c->mat.size() + n, mat);
-    c->body.resize(c->body.size() + n, kind == 0 ? -1 : body);
+    if (n == 0) return SPH_OK;
+    PBlock P;
+    P.kind = kind;
+    P.body = kind == 0 ? -1 : body;
+    P.mat = mat;
+    P.n = n;
+    P.first = n0;
+    P.pos.assign(pos, pos + 3 * n);
+    if (vel) P.vel.assign(vel, vel + 3 * n);
+    if (nrm) P.nrm.assign(nrm, nrm + 3 * n);
+    if (T) P.T.assign(T, T + n);
+    if (rho) {
+        P.rho.assign(rho, rho + n);
+        for (double& r : P.rho)
+            if (!std::isfinite(r)) r = M.rho0;
+    }
+    c->blocks.push_back(std::move(P));
+    c->n_total += n;
     if (kind == 0) c->n_fluid += n;
     else c->n_solid += n;
     return SPH_OK;
@@ -1036,7 +1044,7 @@ sph_status sph_set_rotation(sph_ctx* c, int b, const double center[3], const dou
 static sph_status single_engine(sph_ctx* c) {
     if (c->started) return SPH_OK;
     if (c->admitted) return fail(c, SPH_ESTATE, "this context was admitted to a batch");
-    if (c->kind.empty()) return fail(c, SPH_ESTATE, "no particles");
+    if (c->n_total == 0) return fail(c, SPH_ESTATE, "no particles");
     Engine* E = new Engine();
     E->stream = c->stream;
     E->B.tune_batch = c->tune_batch;
@@ -1045,7 +1053,7 @@ static sph_status single_engine(sph_ctx* c) {
     E->B.uni_fluid = single_fluid_material(c) ? 1 : 0;
     E->B.fp64 = c->cfg.pair_precision == 1 ? 1 : 0;
     const int64_t nc = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
-    sph_status r = engine_alloc(*E, (int64_t)c->kind.size(), 1, nc, 4096);
+    sph_status r = engine_alloc(*E, c->n_total, 1, nc, 4096);
     int slot = -1;
     if (r == SPH_OK) r = engine_admit(*E, c, 0, &slot);
     if (r == SPH_OK) r = prepare(*E);
@@ -1057,8 +1065,7 @@ static sph_status single_engine(sph_ctx* c) {
     }
     c->eng = E;
     c->started = true;
-    std::vector<double>().swap(c->vel);
-    std::vector<double>().swap(c->rho);
+    std::vector<PBlock>().swap(c->blocks);  // the engine holds the particles now
     return SPH_OK;
 }
 

@@ -32,6 +32,49 @@ static inline int grid_1to1(int n, int block) {
 
 #define GSTRIDE_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// ------------------------------------------------------------- admission ---
+// One staged block of a newly admitted case (ids idb.., all of one kind,
+// material and body) into the packed arrays from slot `at`: positions to the
+// work and reference arrays, velocity and density excess, reference normals,
+// temperatures, ids and tags.  Missing inputs (null): zero velocity and
+// normal, the material's T_init and rho0.
+__global__ void k_admit_block(Bufs B, int par, int n, int at, int idb, uint32_t tag, int fluid, double rho0,
+                              double T_init, const double* __restrict__ pos, const double* __restrict__ vel,
+                              const double* __restrict__ nrm, const double* __restrict__ T,
+                              const double* __restrict__ rho) {
+    GSTRIDE_LOOP(q, n) {
+        const int i = at + q, id = idb + q;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double x = pos[3 * q + a];
+            B.X[a][i] = x;
+            B.RP[a][id] = x;
+        }
+        const double v[3] = {vel && fluid ? vel[3 * q] : 0.0, vel && fluid ? vel[3 * q + 1] : 0.0,
+                             vel && fluid ? vel[3 * q + 2] : 0.0};
+        const double dr = fluid ? (rho ? rho[q] : rho0) - rho0 : 0.0;
+        B.V[par][i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)dr);
+        const double nv[3] = {nrm ? nrm[3 * q] : 0.0, nrm ? nrm[3 * q + 1] : 0.0, nrm ? nrm[3 * q + 2] : 0.0};
+        B.RN[id] = make_float4((float)nv[0], (float)nv[1], (float)nv[2], 0.f);
+        B.T64[par][i] = T ? T[q] : T_init;
+        B.ID[par][i] = id;
+        B.TAG[par][i] = tag;
+        if (B.fp64) {
+            B.V64[par][i] = make_double4_32a(v[0], v[1], v[2], dr);
+            B.RN64[id] = make_double4_32a(nv[0], nv[1], nv[2], 0.0);
+        }
+    }
+}
+
+cudaError_t launch_admit_block(const Bufs& B, int par, int n, int at, int idb, uint32_t tag, int fluid, double rho0,
+                               double T_init, const double* pos, const double* vel, const double* nrm, const double* T,
+                               const double* rho, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_admit_block<<<grid_stride_grid(n, 256), 256, 0, s>>>(B, par, n, at, idb, tag, fluid, rho0, T_init, pos, vel, nrm,
+                                                          T, rho);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- control ---
 // Initial max speed of the particles in slots [lo, hi) (a newly admitted
 // case): warp-aggregated atomics per case.

@@ -72,6 +72,10 @@ struct Bufs {
 
 // launchers (stream-ordered; all return the launch error)
 cudaError_t launch_vmax_init(const Bufs& B, int par, int lo, int hi, cudaStream_t s);
+// a staged block of a new case into the packed arrays (device inputs; null = default)
+cudaError_t launch_admit_block(const Bufs& B, int par, int n, int at, int idb, uint32_t tag, int fluid, double rho0,
+                               double T_init, const double* pos, const double* vel, const double* nrm, const double* T,
+                               const double* rho, cudaStream_t s);
 cudaError_t launch_adv_begin(const Bufs& B, cudaStream_t s);
 cudaError_t launch_sort(const Bufs& B, int par, cudaStream_t s);  // hash..reorder + segments
 // pair passes: T holds the pair constants of the resident cases (PairTab)
