@@ -147,8 +147,11 @@ def sweep_sharded(n_cases=64, steps=50, count_scale=1.0, seed=4):
 
 
 # ---------------------------------------------------------------- serving ---
-def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb=40.0, max_cases=64,
-          steps_per_poll=8, sequential=True):
+def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb=40.0, max_cases=16,
+          steps_per_poll=8, sequential=True, policy="sjf"):
+    """Serving loop over a seeded Poisson trace.  policy: "fifo" admits waiting
+    requests in arrival order, "sjf" the one with the fewest particles first
+    (a case never waits behind a larger one that arrived earlier)."""
     trace = W.serving_trace(n_requests, seed=seed, rate=rate, steps=steps, count_scale=count_scale)
     cases = [_case(r) for r in trace]
     arrivals = np.array([r["arrival"] for r in trace])
@@ -156,7 +159,8 @@ def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb
     cap, cells = batch_capacity(budget_gb * 1e9, max_cases, steps)
     cap = max(cap, max(c.n_total for c in cases))
     out = dict(mode="serve", requests=n_requests, rate_per_s=rate, steps=steps, count_scale=count_scale,
-               budget_gb=budget_gb, n_fluid_range=[int(n_fluid.min()), int(n_fluid.max())],
+               budget_gb=budget_gb, max_cases=max_cases, policy=policy,
+               n_fluid_range=[int(n_fluid.min()), int(n_fluid.max())],
                n_fluid_mean=float(n_fluid.mean()))
 
     b = sph.Batch(cap, max_cases, cells, history_steps=steps)
@@ -173,15 +177,22 @@ def serve(n_requests=64, steps=200, rate=4.0, count_scale=1.0, seed=5, budget_gb
             pending.append(nxt)
             nxt += 1
         ta = time.perf_counter()
-        while pending:  # FIFO admission while the budget allows
+        while pending:  # admission in policy order while the budget allows
+            if policy == "sjf":
+                k = min(range(len(pending)), key=lambda q: (cases[pending[q]].n_total, pending[q]))
+                pending.rotate(-k)  # the chosen request to the front, the others keep their order
             r = pending[0]
             try:
                 slot = b.admit(cases[r], steps)
             except sph.SphError as e:
+                if policy == "sjf" and k:
+                    pending.rotate(k)
                 if e.status == sph.SPH_ENOMEM and resident:
                     break
                 raise
             pending.popleft()
+            if policy == "sjf" and k:
+                pending.rotate(k)
             resident[slot] = r
         tb = time.perf_counter()
         tm["admit"] += tb - ta
@@ -273,7 +284,8 @@ def main(argv=None):
     ap.add_argument("--count-scale", type=float, default=0.0)
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--no-sequential", action="store_true")
-    ap.add_argument("--max-cases", type=int, default=64)
+    ap.add_argument("--max-cases", type=int, default=16, help="resident cases at most (serve)")
+    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf"], help="admission order (serve)")
     a = ap.parse_args(argv)
     import os
     import torch
@@ -294,7 +306,7 @@ def main(argv=None):
         r = sweep(a.cases, a.steps or 50, a.count_scale or 1.0, sequential=not a.no_sequential)
     else:
         r = serve(a.requests, a.steps or 200, a.rate, a.count_scale or 1.0, budget_gb=a.budget_gb,
-                  max_cases=a.max_cases, sequential=not a.no_sequential)
+                  max_cases=a.max_cases, sequential=not a.no_sequential, policy=a.policy)
     print(json.dumps(r), flush=True)
 
 
