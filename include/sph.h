@@ -197,6 +197,9 @@ typedef struct {
     int graph_launches;       /* kernels per advection step of the profiling graph (kcap sub-step slots) */
     int kernels_fixed;        /* kernels per advection step of the stepping graph: kernels_fixed + */
     int kernels_per_substep;  /* kernels_per_substep x (its sub-steps) */
+    int info_bits;            /* 4: since creation, some particle had more partners than its
+                                 128-entry list holds and took the 27-cell loop instead (results
+                                 unchanged; informational) */
 } sph_info;
 
 sph_status sph_get_info(sph_ctx* ctx, sph_info* info);

@@ -1188,6 +1188,7 @@ sph_status sph_get_info(sph_ctx* c, sph_info* info) {
         info->last_dt_ad = S.last_dt_ad;
         info->last_nsub = S.last_nsub;
         info->error_bits = S.err;
+        info->info_bits = S.err_info;
     }
     return SPH_OK;
 }

@@ -44,7 +44,7 @@ class sph_info(C.Structure):
     _fields_ = [("n_fluid", I64), ("n_solid", I64), ("t", D), ("adv_steps", I64), ("substeps", I64),
                 ("last_dt_ad", D), ("last_nsub", C.c_int), ("kcap", C.c_int), ("ncell", C.c_int * 3),
                 ("cell_width", D * 3), ("error_bits", C.c_int), ("graph_launches", C.c_int),
-                ("kernels_fixed", C.c_int), ("kernels_per_substep", C.c_int)]
+                ("kernels_fixed", C.c_int), ("kernels_per_substep", C.c_int), ("info_bits", C.c_int)]
 
 
 class sph_relax_config(C.Structure):

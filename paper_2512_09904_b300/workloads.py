@@ -461,6 +461,25 @@ def periodic_box(n=12, dx=1e-3, seed=7, jitter=0.05, v_amp=0.2, rho_amp=2e-3, rh
 
 
 # --------------------------------------------------------------------------
+# Crowded periodic box: a lattice with extra particles at the cube centres of
+# a central block (locally body-centred, twice the density), where a particle
+# has about 147 partners, more than a 128-entry neighbour list holds; the
+# rest of the box has the lattice's 80.  At rest, g = 0.
+# --------------------------------------------------------------------------
+def crowded_box(n=14, crowd=8, dx=1e-3, seed=17, jitter=0.02, rho0=1000.0, mu=0.02, c0=10.0):
+    rng = np.random.default_rng(seed)
+    idx = _grid((0, 0, 0), (n, n, n))
+    lo = (n - crowd) // 2
+    cidx = _grid((lo, lo, lo), (lo + crowd, lo + crowd, lo + crowd))
+    pos = np.concatenate([(idx + 0.5) * dx, (cidx + 1.0) * dx])
+    pos = pos + _jitter(rng, len(pos), dx, jitter)
+    cfg = _cfg(origin=(0, 0, 0), extent=(n * dx,) * 3, dx=dx, c0=c0, gravity=(0, 0, 0), periodic_mask=0b111)
+    mats = {0: _mat(rho0, mu, 0.6, 4000.0, 300.0)}
+    fluids = [dict(mat=0, pos=pos, vel=None, T=None, rho=None)]
+    return Case("crowded_box", cfg, mats, fluids, [], {}, dict(seed=seed, crowd=crowd))
+
+
+# --------------------------------------------------------------------------
 # Neighbour-search stress input: random points plus pairs placed within a few
 # ulps of the support radius, on both sides of it.
 # --------------------------------------------------------------------------

@@ -64,6 +64,8 @@ CASES = [
     ("periodic_box", lambda: W.periodic_box(n=12), 3),
     ("rotating_cylinder", lambda: W.rotating_cylinder(), 3),
     ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
+    # more partners than the 128-entry lists hold (the 27-cell loop)
+    ("crowded_box", lambda: W.crowded_box(), 2),
     # Eq. (13) with its printed sign (anti-diffusive; a short run)
     ("periodic_box_vstar_literal", lambda: _literal(W.periodic_box(n=12, rho_amp=1e-4)), 2),
 ]

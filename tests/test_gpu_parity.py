@@ -127,7 +127,14 @@ FIELD_CASES = [
     ("periodic_box", lambda: W.periodic_box(n=12), 3),
     ("rotating_cylinder", lambda: W.rotating_cylinder(), 3),
     ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
+    # partners beyond the 128-entry list: those particles take the 27-cell loop
+    ("crowded_box", lambda: W.crowded_box(), 2),
 ]
+# The crowded block sits at twice the rest density (p = c0^2 rho0): each of its
+# ~150 pair forces is some 30 times the net force, so FP32 cancellation leaves
+# ~2e-5 of u_ref in the velocities after one step; the FP64 mode checks the
+# same case at 1e-12 (tests/test_gpu_fp64.py).
+TOL_FACTOR = {"crowded_box": 10.0}
 
 
 @pytest.mark.parametrize("name,make,steps", FIELD_CASES, ids=[c[0] for c in FIELD_CASES])
@@ -144,7 +151,7 @@ def test_field_parity(sph, oracle, name, make, steps):
         err = _compare(ctx, sim, case)
         print(name, k + 1, err)
         for f, e in err.items():
-            assert e <= TOL * (k + 1), (name, k + 1, f, e)
+            assert e <= TOL * TOL_FACTOR.get(name, 1.0) * (k + 1), (name, k + 1, f, e)
 
 
 def test_slab_temperature_parity(sph, oracle):
@@ -310,4 +317,18 @@ def test_gear_bath_5mm_fp32_against_stored_oracle(sph):
     g = ctx.sph_read_torque_heat(0)
     assert g["torque_avg"] * ref["omega"] < 0 and last["torque_avg"] * ref["omega"] < 0
     assert g["heat"] > 0 and last["heat"] > 0
+    ctx.close()
+
+
+def test_list_overflow_is_reported(sph):
+    # the crowded block's particles have ~147 partners (> 128): flagged as
+    # information, not as an error; a plain lattice (80 partners) never is
+    ctx = _ctx(sph, W.crowded_box())
+    ctx.sph_step(1)
+    info = ctx.sph_get_info()
+    assert info["info_bits"] & 4 and info["error_bits"] == 0
+    ctx.close()
+    ctx = _ctx(sph, W.periodic_box(n=12))
+    ctx.sph_step(1)
+    assert ctx.sph_get_info()["info_bits"] == 0
     ctx.close()
