@@ -150,3 +150,18 @@ def test_fma_peak_validates_arguments(sphlib):
     t = C.c_double()
     assert L.sph_fma_peak(None, 0, C.byref(t), None) == sphlib.SPH_EINVAL
     assert L.sph_fma_peak(None, 3, None, None) == sphlib.SPH_EINVAL
+
+
+def test_empty_case_cannot_step(sphlib):
+    # no particles: stepping is a state error, raised before any device work;
+    # an empty add is accepted and adds nothing
+    case = W.periodic_box(n=8)
+    ctx = sphlib.Context(case.config, stream=0)
+    for mid, m in case.materials.items():
+        ctx.sph_set_material(mid, m)
+    assert ctx.sph_add_fluid(0, np.zeros((0, 3))) == 0
+    with pytest.raises(sphlib.SphError) as e:
+        ctx.sph_step(1)
+    assert e.value.status == sphlib.SPH_ESTATE
+    assert ctx.sph_get_info()["n_fluid"] == 0
+    ctx.close()
