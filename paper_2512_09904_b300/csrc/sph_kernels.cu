@@ -242,13 +242,22 @@ __device__ __forceinline__ uint32_t cell_key(const CaseDev& C, const double p[3]
     int cc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // floor((p - o) / w) in FP64: the product with 1/w is within a few ulp
-        // of the quotient, so it decides unless it lies within 1e-9 of an
-        // integer; there the division itself is taken
+        // floor((p - o) / w) of the FP64 quotient.  An FP32 estimate (three
+        // roundings: at most 2e-7 |q| off) decides when its fraction is more
+        // than 1e-6 |q| from an integer; else the FP64 product with 1/w (a few
+        // ulp off) decides unless it lies within 1e-9 of an integer, and there
+        // the division itself is taken.  FP64 arithmetic is the slow pipe.
         const double d = p[a] - C.origin[a];
-        double q = d * C.inv_cellw[a];
-        if (fabs(q - rint(q)) < 1e-9 * fmax(1.0, fabs(q))) q = d / C.cellw[a];
-        double f = floor(q);
+        const float qf = (float)d * C.inv_scellwf[a];
+        const float ff = floorf(qf), mf = 1e-6f * fmaxf(1.0f, fabsf(qf));
+        double f;
+        if (qf - ff > mf && qf - ff < 1.0f - mf) {
+            f = (double)ff;
+        } else {
+            double q = d * C.inv_cellw[a];
+            if (fabs(q - rint(q)) < 1e-9 * fmax(1.0, fabs(q))) q = d / C.cellw[a];
+            f = floor(q);
+        }
         double top = (double)(C.ncell[a] - 1);
         if (!(f >= 0.0)) {
             f = 0.0;
