@@ -351,14 +351,13 @@ __device__ __forceinline__ void for_each_neighbor(const CC& C, const CaseDev* Cg
                                                   const double* __restrict__ Yz, int i, float4 si,
                                                   uint32_t key_i, F&& f) {
     for_each_candidate(C, cstart, si, key_i, [&](int j, float ox, float oy, float oz, uint32_t code) {
-        if (j == i) return;
         const float4 sj = __ldg(snap + j);
         const float rx = ox - sj.x, ry = oy - sj.y, rz = oz - sj.z;
         const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
         bool in;
         if (r2 >= C.R2hi) in = false;
         else if (r2 < C.R2lo && r2 > C.R2eps) in = true;
-        else in = member_fp64(Cg, Yx, Yy, Yz, i, j);
+        else in = j != i && member_fp64(Cg, Yx, Yy, Yz, i, j);  // i itself: r2 = 0 lands here
         if (in) f(j, sj, rx, ry, rz, r2, (int)code);
     });
 }
