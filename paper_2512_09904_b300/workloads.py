@@ -461,6 +461,24 @@ def periodic_box(n=12, dx=1e-3, seed=7, jitter=0.05, v_amp=0.2, rho_amp=2e-3, rh
 
 
 # --------------------------------------------------------------------------
+# Two fluids in a periodic box: water (x < L/2) beside oil, different density,
+# viscosity, conductivity and temperature (the pair passes' general-material
+# path: harmonic means of mu and k, per-partner masses and rest densities).
+# --------------------------------------------------------------------------
+def two_fluid_box(n=12, dx=1e-3, seed=19, jitter=0.05, v_amp=0.1, c0=10.0):
+    rng = np.random.default_rng(seed)
+    idx = _grid((0, 0, 0), (n, n, n))
+    pos = (idx + 0.5) * dx + _jitter(rng, len(idx), dx, jitter)
+    left = pos[:, 0] < 0.5 * n * dx
+    vel = rng.uniform(-v_amp, v_amp, size=(len(idx), 3))
+    cfg = _cfg(origin=(0, 0, 0), extent=(n * dx,) * 3, dx=dx, c0=c0, gravity=(0, 0, 0), periodic_mask=0b111)
+    mats = {0: _mat(1000.0, 0.01, 0.6, 4180.0, 300.0), 1: _mat(870.0, 0.1, 0.15, 2000.0, 320.0)}
+    fluids = [dict(mat=0, pos=pos[left], vel=vel[left], T=None, rho=None),
+              dict(mat=1, pos=pos[~left], vel=vel[~left], T=None, rho=None)]
+    return Case("two_fluid_box", cfg, mats, fluids, [], {}, dict(seed=seed))
+
+
+# --------------------------------------------------------------------------
 # Crowded periodic box: a lattice with extra particles at the cube centres of
 # a central block (locally body-centred, twice the density), where a particle
 # has about 147 partners, more than a 128-entry neighbour list holds; the

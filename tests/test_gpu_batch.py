@@ -144,3 +144,13 @@ def test_admission_refused_when_full(sph):
     b.step(1)
     assert b.info()["n_cases"] == 1
     b.close()
+
+
+def test_batch_refuses_two_fluid_materials(sph):
+    # batched cases run the single-fluid-material pair path
+    case = W.two_fluid_box()
+    b = sph.Batch(case.n_total + 10, 2, sph.cells_of(case) + 10, history_steps=4, stream=0)
+    with pytest.raises(sph.SphError) as e:
+        b.admit(case)
+    assert e.value.status == sph.SPH_EINVAL
+    b.close()

@@ -66,6 +66,7 @@ CASES = [
     ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
     # more partners than the 128-entry lists hold (the 27-cell loop)
     ("crowded_box", lambda: W.crowded_box(), 2),
+    ("two_fluid_box", lambda: W.two_fluid_box(), 3),
     # Eq. (13) with its printed sign (anti-diffusive; a short run)
     ("periodic_box_vstar_literal", lambda: _literal(W.periodic_box(n=12, rho_amp=1e-4)), 2),
 ]

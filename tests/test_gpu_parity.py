@@ -129,6 +129,8 @@ FIELD_CASES = [
     ("dam_break_coarse", lambda: W.dam_break(dx=10e-3), 2),
     # partners beyond the 128-entry list: those particles take the 27-cell loop
     ("crowded_box", lambda: W.crowded_box(), 2),
+    # two fluid materials: the general-material path of every pair pass
+    ("two_fluid_box", lambda: W.two_fluid_box(), 3),
 ]
 # The crowded block sits at twice the rest density (p = c0^2 rho0): each of its
 # ~150 pair forces is some 30 times the net force, so FP32 cancellation leaves
