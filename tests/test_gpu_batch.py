@@ -154,3 +154,24 @@ def test_batch_refuses_two_fluid_materials(sph):
         b.admit(case)
     assert e.value.status == sph.SPH_EINVAL
     b.close()
+
+
+def test_alone_equals_mixed_bitwise_two_threads_per_particle(sph):
+    # the two-thread pair variant adds each list in two halves; alone (one
+    # parameter-block entry) and batched (the per-slot table) still agree
+    cs = _cases()
+    steps = 4
+    ctx = sph.from_case(cs["gear"], stream=0)
+    ctx.sph_set_tuning("tpp", 2)
+    ctx.sph_step(steps)
+    alone = {f: ctx.sph_read_fields(f) for f in ("pos", "vel", "rho", "T")}
+    alone["th"] = ctx.sph_read_torque_heat(0)
+    ctx.close()
+    b = _batch_for(sph, list(cs.values()))
+    b.set_tuning("tpp", 2)
+    slots = {k: b.admit(c, n_steps=0) for k, c in cs.items()}
+    b.step(steps)
+    got = {f: b.fields(slots["gear"], f) for f in ("pos", "vel", "rho", "T")}
+    got["th"] = b.torque_heat(slots["gear"])
+    _same(got, alone)
+    b.close()
