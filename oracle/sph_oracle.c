@@ -23,6 +23,11 @@
  *       pass C  Riemann continuity (Eqs. 10-13) + wall continuity (Eqs. 16-17);
  *               rho += dt/2 drho.
  * Readings of points the paper leaves open are marked READING below.
+ *
+ * Parity unpinned by the paper: the magnitudes of long-run churning torque
+ * and heat-up (the paper prints no values for them).  The torque and force
+ * sums themselves are pinned by sign (drag opposes rotation) and by the still
+ * tank's walls carrying the oil's weight.
  */
 #include "sph_oracle.h"
 
