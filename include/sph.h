@@ -202,6 +202,9 @@ typedef struct {
                                  unchanged; informational) */
 } sph_info;
 
+/* Fill *info (host) with the context's sizes, grid, clock and flags; before the
+ * first step only the static fields are set.  Errors: SPH_EINVAL (NULL),
+ * SPH_ECUDA (reading the step state back). */
 sph_status sph_get_info(sph_ctx* ctx, sph_info* info);
 
 /* Directed neighbour pairs of fluid particles in the current snapshot, by
@@ -239,6 +242,7 @@ enum {
 /* Select a kernel variant; re-captures the step graph if the context has
  * started.  Errors: SPH_EINVAL (unknown key or value), SPH_ECUDA. */
 sph_status sph_set_tuning(sph_ctx* ctx, int key, int value);
+/* The variant in force for `key` into *value (host).  Errors: SPH_EINVAL. */
 sph_status sph_get_tuning(sph_ctx* ctx, int key, int* value);
 
 /* Autotuner result: the variant now in force and the model time it won on,
@@ -355,7 +359,11 @@ int64_t sph_batch_bytes(const sph_batch_config* cfg);
 /* Allocate a batch (all device memory up front).  Errors: SPH_EINVAL,
  * SPH_ENOMEM (message in sph_last_error(NULL)), SPH_ECUDA. */
 sph_status sph_batch_create(const sph_batch_config* cfg, void* cuda_stream, sph_batch** out);
+/* Free the batch and all its device memory; NULL is allowed. */
 sph_status sph_batch_destroy(sph_batch* b);
+/* Text of the batch's last error (empty if none), or with b = NULL of the last
+ * failed call that had no batch (sph_batch_create); the pointer lives until
+ * the next call on the batch. */
 const char* sph_batch_last_error(const sph_batch* b);
 
 /* Copy a staged case (never stepped; one fluid material) into the batch; it
@@ -391,10 +399,12 @@ sph_status sph_batch_retire(sph_batch* b, int slot);
 /* Resident particles and cases, and kernels launched per advection step. */
 sph_status sph_batch_info(sph_batch* b, int64_t* n_particles, int* n_cases, int* kernels_per_step);
 
+/* sph_set_tuning for every case of the batch.  Errors: SPH_EINVAL, SPH_ECUDA. */
 sph_status sph_batch_set_tuning(sph_batch* b, int key, int value);
 
 /* sph_autotune for the resident cases of a batch (one variant for all). */
 sph_status sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tune_report* report);
+/* sph_profile and sph_profile_read for the batch's step graph. */
 sph_status sph_batch_profile(sph_batch* b, int enable);
 sph_status sph_batch_profile_read(sph_batch* b, double* ms, int64_t* launches, int reset);
 
