@@ -148,6 +148,16 @@ sph_status sph_read_torque_heat(sph_ctx* ctx, int body_id, double* torque_axis,
                                 double* torque_time_avg, double* heat_into_fluid,
                                 double* mean_fluid_T);
 
+/* Torque and heat-up history of the context: the last n (<= max_steps, <=
+ * 4096) advection-step records, oldest first, 8 doubles each: simulated time
+ * at the end of the step, torque of body 0 about its axis (as
+ * sph_read_torque_heat), its running time average, heat into fluid, mean
+ * fluid temperature, dt_ad of the step, acoustic sub-steps of the step, the
+ * max fluid speed that set dt_ad.  out: host double[8 * max_steps], owned by the caller; n_out
+ * may be NULL.  Errors: SPH_EINVAL (out NULL, max_steps < 0), SPH_ESTATE
+ * (not started), SPH_ECUDA. */
+sph_status sph_read_curve(sph_ctx* ctx, double* out, int64_t max_steps, int64_t* n_out);
+
 /* Field ids for sph_read_fields (values as double, original id order). */
 enum {
     SPH_FIELD_POS = 0,      /* n*3; solids: at the current simulation time */

@@ -895,6 +895,27 @@ static sph_status read_fields(Engine& E, int slot, int field, void* dst, int64_t
     return SPH_OK;
 }
 
+// The last n (<= max_steps, <= the ring's capacity) advection-step records
+// of case `slot`, oldest first, 8 doubles each.
+static sph_status read_curve(Engine& E, int slot, double* out, int64_t max_steps, int64_t* n_out) {
+    if (!out || max_steps < 0) return E.fail(SPH_EINVAL, "out is NULL or max_steps < 0");
+    const int64_t done = E.st_h[slot].adv_steps;
+    const int64_t cap = E.hist_cap;
+    const int64_t n = std::min(done, std::min(cap, max_steps));
+    if (n > 0) {
+        std::vector<double> ring((size_t)8 * (size_t)cap);
+        E_CUDA(E, cudaMemcpyAsync(ring.data(), E.B.HIST + (size_t)slot * cap * 8, sizeof(double) * 8 * cap,
+                                  cudaMemcpyDeviceToHost, E.stream));
+        E_CUDA(E, cudaStreamSynchronize(E.stream));
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t step = done - n + k;  // 0-based advection step index
+            memcpy(out + 8 * k, ring.data() + 8 * (step % cap), sizeof(double) * 8);
+        }
+    }
+    if (n_out) *n_out = n;
+    return SPH_OK;
+}
+
 static sph_status read_torque_heat(Engine& E, int slot, int b, double* tq, double* tq_avg, double* heat,
                                    double* meanT) {
     if (b < 0 || b >= MAX_BODY) return E.fail(SPH_EINVAL, "body id %d out of range", b);
@@ -1100,6 +1121,11 @@ sph_status sph_step(sph_ctx* c, int n_steps, double* t_out) {
 sph_status sph_read_torque_heat(sph_ctx* c, int b, double* tq, double* tq_avg, double* heat, double* meanT) {
     STARTED_OR_STATE(c);
     return relay(c, read_torque_heat(*c->eng, 0, b, tq, tq_avg, heat, meanT));
+}
+
+sph_status sph_read_curve(sph_ctx* c, double* out, int64_t max_steps, int64_t* n_out) {
+    STARTED_OR_STATE(c);
+    return relay(c, read_curve(*c->eng, 0, out, max_steps, n_out));
 }
 
 sph_status sph_read_fields(sph_ctx* c, int field, void* dst, int64_t n) {
@@ -1504,23 +1530,7 @@ sph_status sph_batch_read_torque_heat(sph_batch* b, int slot, int body, double* 
 sph_status sph_batch_read_curve(sph_batch* b, int slot, double* out, int64_t max_steps, int64_t* n_out) {
     sph_status s = batch_slot(b, slot);
     if (s != SPH_OK) return s;
-    Engine& E = b->eng;
-    if (!out || max_steps < 0) return E.fail(SPH_EINVAL, "out is NULL or max_steps < 0");
-    const int64_t done = E.st_h[slot].adv_steps;
-    const int64_t cap = E.hist_cap;
-    const int64_t n = std::min(done, std::min(cap, max_steps));
-    if (n > 0) {
-        std::vector<double> ring((size_t)8 * (size_t)cap);
-        E_CUDA(E, cudaMemcpyAsync(ring.data(), E.B.HIST + (size_t)slot * cap * 8, sizeof(double) * 8 * cap,
-                                  cudaMemcpyDeviceToHost, E.stream));
-        E_CUDA(E, cudaStreamSynchronize(E.stream));
-        for (int64_t k = 0; k < n; ++k) {
-            const int64_t step = done - n + k;  // 0-based advection step index
-            memcpy(out + 8 * k, ring.data() + 8 * (step % cap), sizeof(double) * 8);
-        }
-    }
-    if (n_out) *n_out = n;
-    return SPH_OK;
+    return read_curve(b->eng, slot, out, max_steps, n_out);
 }
 
 sph_status sph_batch_read_fields(sph_batch* b, int slot, int field, void* host_dst, int64_t n) {

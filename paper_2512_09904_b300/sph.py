@@ -112,6 +112,7 @@ def lib():
         L.sph_batch_poll.argtypes = [vp, C.c_int, PI64, PD, C.POINTER(C.c_int)]
         L.sph_batch_read_torque_heat.argtypes = [vp, C.c_int, C.c_int, PD, PD, PD, PD]
         L.sph_batch_read_curve.argtypes = [vp, C.c_int, PD, I64, PI64]
+        L.sph_read_curve.argtypes = [vp, PD, I64, PI64]
         L.sph_batch_read_fields.argtypes = [vp, C.c_int, C.c_int, vp, I64]
         L.sph_batch_retire.argtypes = [vp, C.c_int]
         L.sph_batch_info.argtypes = [vp, PI64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -126,7 +127,7 @@ def lib():
         L.sph_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(sph_tune_report)]
         L.sph_fma_peak.argtypes = [vp, C.c_int, PD, PD]
         for name in ("sph_create", "sph_destroy", "sph_set_material", "sph_add_fluid", "sph_add_solid",
-                     "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_fields",
+                     "sph_set_rotation", "sph_step", "sph_read_torque_heat", "sph_read_curve", "sph_read_fields",
                      "sph_read_neighbors", "sph_read_cell_order", "sph_get_info", "sph_cell_sort",
                      "sph_profile", "sph_profile_read", "sph_pair_stats", "sph_cell_sort_noalloc",
                      "sph_set_tuning", "sph_get_tuning", "sph_batch_create", "sph_batch_destroy",
@@ -241,6 +242,15 @@ class Context:
         self._check(self._L.sph_read_torque_heat(self._p, int(body), *[C.byref(x) for x in v]),
                     "sph_read_torque_heat")
         return dict(torque=v[0].value, torque_avg=v[1].value, heat=v[2].value, mean_T=v[3].value)
+
+    def sph_read_curve(self, max_steps=4096):
+        """The last advection-step records, oldest first, one row of 8 each:
+        time, torque of body 0, its running average, heat into fluid, mean
+        fluid T, dt_ad, sub-steps, max fluid speed."""
+        out = np.zeros(8 * max(int(max_steps), 1), np.float64)
+        n = C.c_int64()
+        self._check(self._L.sph_read_curve(self._p, _pd(out), int(max_steps), C.byref(n)), "sph_read_curve")
+        return out[:8 * n.value].reshape(n.value, 8)
 
     def sph_read_fields(self, name, out=None):
         fid, k = FIELDS[name]

@@ -120,6 +120,9 @@ def test_reads_before_first_step_are_state_errors(sphlib):
     with pytest.raises(sphlib.SphError) as e:
         ctx.sph_read_torque_heat(0)
     assert e.value.status == sphlib.SPH_ESTATE
+    with pytest.raises(sphlib.SphError) as e:
+        ctx.sph_read_curve(8)
+    assert e.value.status == sphlib.SPH_ESTATE
     ctx.close()
 
 

@@ -196,6 +196,38 @@ def test_rotating_cylinder_torque_heat_parity(sph, oracle):
     assert g["mean_T"] == pytest.approx(r["mean_T"], rel=1e-9)
 
 
+def test_rotating_cylinder_curve_parity(sph, oracle):
+    """The per-step history ring against the oracle stepped one step at a
+    time: time and dt_ad (set by the FP32 max speed, so to 1e-6), the
+    acoustic sub-step count exactly, torque, its average and the heat-up to
+    1e-3 of the series' largest magnitude (FP32 pair sums)."""
+    case = W.rotating_cylinder()
+    n = 12
+    ctx = _ctx(sph, case)
+    sim = oracle.OracleSim(case)
+    ref = []
+    for _ in range(n):
+        sim.step(1)
+        tm, th = sim.time(), sim.torque_heat(0)
+        ref.append([tm["t"], th["torque"], th["torque_avg"], th["heat"], th["mean_T"], tm["dt_ad"], tm["nsub"]])
+    ref = np.array(ref)
+    ctx.sph_step(n)
+    got = ctx.sph_read_curve(4 * n)
+    assert got.shape == (n, 8)
+    assert got[:, 0] == pytest.approx(ref[:, 0], rel=1e-6)
+    assert got[:, 5] == pytest.approx(ref[:, 5], rel=1e-6)
+    assert np.array_equal(got[:, 6], ref[:, 6])
+    for col in (1, 2, 3):
+        assert np.max(np.abs(got[:, col] - ref[:, col])) <= 1e-3 * np.max(np.abs(ref[:, col])), col
+    assert got[:, 4] == pytest.approx(ref[:, 4], rel=1e-9)
+    th = ctx.sph_read_torque_heat(0)
+    assert got[-1, 1] == th["torque"] and got[-1, 2] == th["torque_avg"]
+    assert np.all(got[:, 7] > 0)
+    tail = ctx.sph_read_curve(3)
+    assert np.array_equal(tail, got[-3:])
+    ctx.close()
+
+
 # --------------------------------------------------------- contact factor ---
 @pytest.mark.parametrize("name,make", [
     ("contact_probe", lambda: W.contact_probe(fill="above")),
