@@ -228,6 +228,24 @@ def test_rotating_cylinder_curve_parity(sph, oracle):
     ctx.close()
 
 
+def test_curve_ring_wraps_in_step_order(sph):
+    """After more advection steps than the 4096-record ring holds, the read
+    returns the last 4096 steps oldest first: records taken before the wrap
+    reappear unchanged at their shifted positions."""
+    case = W.rotating_cylinder()
+    ctx = _ctx(sph, case)
+    ctx.sph_step(10)
+    early = ctx.sph_read_curve(10)
+    ctx.sph_step(4090)
+    late = ctx.sph_read_curve(5000)
+    assert late.shape == (4096, 8)
+    assert np.array_equal(late[:6], early[4:])
+    assert np.all(np.diff(late[:, 0]) > 0)
+    th = ctx.sph_read_torque_heat(0)
+    assert late[-1, 2] == th["torque_avg"] and late[-1, 3] == th["heat"]
+    ctx.close()
+
+
 # --------------------------------------------------------- contact factor ---
 @pytest.mark.parametrize("name,make", [
     ("contact_probe", lambda: W.contact_probe(fill="above")),
