@@ -342,6 +342,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.gcellwf[a] = (float)C.gcellw[a];
         C.scellwf[a] = (float)c->cellw[a];
         C.inv_scellwf[a] = (float)(1.0 / c->cellw[a]);
+        C.originf[a] = (float)F.origin[a];
         C.ncell[a] = c->ncell[a];
         C.g[a] = (float)F.gravity[a];
     }

@@ -70,6 +70,7 @@ struct BodyDev {
 struct CaseDev {
     double origin[3], ext[3], cellw[3], gcellw[3], inv_cellw[3];
     float gcellwf[3], scellwf[3], inv_scellwf[3];
+    float originf[3];  // origin rounded to FP32 (the cell hash's estimate)
     float Rmargin;  // slack on the search sphere (FP32 rounding of the clipping)
     int ncell[3];
     int cell_base, ncells;

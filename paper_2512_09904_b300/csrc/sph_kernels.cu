@@ -238,35 +238,84 @@ __global__ void k_sub_cond(Bufs B, cudaGraphConditionalHandle h) {
 }
 
 // ------------------------------------------------------------ cell sort ---
+// x rounded toward zero to FP32 with integer operations only (FP64
+// arithmetic and conversions share the slow FP64 pipe): |error| < 2^-23 |x|
+// in FP32's normal range, magnitudes below it give 0 (error < 2^-126).
+// False for magnitudes above FP32's range, infinities and NaN.
+__device__ __forceinline__ bool f64_to_f32_trunc(double x, float* out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e >= 255) return false;
+    *out = e <= 0 ? 0.0f
+                  : __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    return true;
+}
+
+// (float)x, the FP64 -> FP32 conversion rounding to nearest (ties to
+// even), with integer operations when x lies in FP32's normal range; the
+// conversion instruction (FP64 pipe) only for the rest (zero, subnormal
+// results, overflow, infinities, NaN).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0 || e >= 255) return (float)x;
+    const uint32_t sign = hi & 0x80000000u;
+    // 23 kept mantissa bits, 29 dropped ones; a carry out of the mantissa
+    // moves into the exponent, which is the correct rounding
+    uint32_t f = sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu, half = 0x10000000u;
+    if (rest > half || (rest == half && (f & 1u))) f += 1u;
+    return __uint_as_float(f);
+}
+
 __device__ __forceinline__ uint32_t cell_key(const CaseDev& C, const double p[3], bool* out) {
     int cc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // floor((p - o) / w) of the FP64 quotient.  An FP32 estimate (three
-        // roundings: at most 2e-7 |q| off) decides when its fraction is more
-        // than 1e-6 |q| from an integer; else the FP64 product with 1/w (a few
-        // ulp off) decides unless it lies within 1e-9 of an integer, and there
-        // the division itself is taken.  FP64 arithmetic is the slow pipe.
-        const double d = p[a] - C.origin[a];
-        const float qf = (float)d * C.inv_scellwf[a];
-        const float ff = floorf(qf), mf = 1e-6f * fmaxf(1.0f, fabsf(qf));
-        double f;
-        if (qf - ff > mf && qf - ff < 1.0f - mf) {
-            f = (double)ff;
+        // floor((p - o) / w) of the FP64 quotient.  An FP32 estimate from
+        // FP32 copies of p and o decides when its fraction is farther from an
+        // integer than a bound on its error: 2^-23 |p| + 2^-24 |o| from the
+        // copies and three FP32 roundings, in units of w, well under the
+        // margin below.  Else the FP64 product with 1/w (a few ulp off)
+        // decides unless it lies within 1e-9 of an integer, and there the
+        // division itself is taken.
+        const int top = C.ncell[a] - 1;
+        float pf;
+        bool fast = f64_to_f32_trunc(p[a], &pf);
+        int ci = 0;
+        if (fast) {
+            const float of = C.originf[a], iw = C.inv_scellwf[a];
+            const float qf = (pf - of) * iw;
+            const float ff = floorf(qf);
+            const float mf = 1e-6f * (1.0f + fabsf(qf) + (fabsf(pf) + fabsf(of)) * iw);
+            fast = qf - ff > mf && qf - ff < 1.0f - mf;
+            ci = (int)ff;
+        }
+        if (fast) {
+            if (ci < 0) {
+                ci = 0;
+                *out = true;
+            } else if (ci > top) {
+                ci = top;
+                *out = true;
+            }
         } else {
+            const double d = p[a] - C.origin[a];
             double q = d * C.inv_cellw[a];
             if (fabs(q - rint(q)) < 1e-9 * fmax(1.0, fabs(q))) q = d / C.cellw[a];
-            f = floor(q);
+            double f = floor(q);
+            if (!(f >= 0.0)) {
+                f = 0.0;
+                *out = true;
+            } else if (f > (double)top) {
+                f = (double)top;
+                *out = true;
+            }
+            ci = (int)f;
         }
-        double top = (double)(C.ncell[a] - 1);
-        if (!(f >= 0.0)) {
-            f = 0.0;
-            *out = true;
-        } else if (f > top) {
-            f = top;
-            *out = true;
-        }
-        cc[a] = (int)f;
+        cc[a] = ci;
     }
     return (uint32_t)(C.cell_base + (cc[2] * C.ncell[1] + cc[1]) * C.ncell[0] + cc[0]);
 }
@@ -453,7 +502,7 @@ __global__ void k_reorder(Bufs B, int par) {
         int cc[3] = {cl % C.ncell[0], (cl / C.ncell[0]) % C.ncell[1], cl / (C.ncell[0] * C.ncell[1])};
         float off[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) off[a] = (float)((p[a] - C.origin[a]) - (double)(cc[a] >> 1) * C.gcellw[a]);
+        for (int a = 0; a < 3; ++a) off[a] = f64_to_f32_rn((p[a] - C.origin[a]) - (double)(cc[a] >> 1) * C.gcellw[a]);
         B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
         B.CELLK[d] = key;
         if (fluid) {
@@ -497,7 +546,7 @@ __global__ void k_reorder(Bufs B, int par) {
         }
         const double T = B.T64[in][s];
         B.T64[out][d] = T;
-        B.T32[d] = (float)(T - C.T_ref);
+        B.T32[d] = f64_to_f32_rn(T - C.T_ref);
         B.ID[out][d] = id;
         B.TAG[out][d] = tag;
     }
