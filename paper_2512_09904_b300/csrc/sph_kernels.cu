@@ -270,6 +270,25 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     return __uint_as_float(f);
 }
 
+// (double)x, exact, with integer operations for normal x; the conversion
+// instruction (FP64 pipe) only for zero, subnormals, infinities and NaN.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (double)x;
+    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// (double)g, exact, for an unsigned integer, with integer operations.
+__device__ __forceinline__ double u32_to_f64(uint32_t g) {
+    if (g == 0u) return 0.0;
+    const int lz = __clz(g);  // the leading one is bit 31 - lz; move it to bit 52
+    const unsigned long long m = (unsigned long long)g << (21 + lz);
+    return __longlong_as_double(
+        (long long)(((unsigned long long)(1023 + 31 - lz) << 52) | (m & 0xfffffffffffffull)));
+}
+
 __device__ __forceinline__ uint32_t cell_key(const CaseDev& C, const double p[3], bool* out) {
     int cc[3];
 #pragma unroll
@@ -502,7 +521,8 @@ __global__ void k_reorder(Bufs B, int par) {
         int cc[3] = {cl % C.ncell[0], (cl / C.ncell[0]) % C.ncell[1], cl / (C.ncell[0] * C.ncell[1])};
         float off[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) off[a] = f64_to_f32_rn((p[a] - C.origin[a]) - (double)(cc[a] >> 1) * C.gcellw[a]);
+        for (int a = 0; a < 3; ++a)
+            off[a] = f64_to_f32_rn((p[a] - C.origin[a]) - u32_to_f64((uint32_t)(cc[a] >> 1)) * C.gcellw[a]);
         B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
         B.CELLK[d] = key;
         if (fluid) {
@@ -1003,14 +1023,16 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         *vbits_out = __float_as_uint(sp <= 3.0e38f ? sp : 3.0e38f);
         if (!vis.lead()) return;
         Vout[i] = make_float4(nvx, nvy, nvz, dh_i);
-        const double hd = (double)hdt;
+        // x + hd v with hd and v FP32 values: their product is exact in FP64,
+        // so one fused operation rounds as the product-then-sum does
+        const double hd = f32_to_f64(hdt);
         const double* Xs[3] = {first ? B.Y[0] : B.X[0], first ? B.Y[1] : B.X[1], first ? B.Y[2] : B.X[2]};
         const float vo[3] = {vi.x, vi.y, vi.z}, vn[3] = {nvx, nvy, nvz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double x = Xs[a][i];
-            x = __dadd_rn(x, __dmul_rn(hd, (double)vo[a]));
-            x = __dadd_rn(x, __dmul_rn(hd, (double)vn[a]));
+            x = __fma_rn(hd, f32_to_f64(vo[a]), x);
+            x = __fma_rn(hd, f32_to_f64(vn[a]), x);
             B.X[a][i] = x;
         }
         if (!(sp <= 3.0e38f) || !(fabsf(dh_i) <= 3.0e38f)) atomicOr(&B.st[tag_case(tag)].err, ERR_NAN);
@@ -1177,7 +1199,7 @@ __global__ void k_T_update(Bufs B, int par) {
         const uint32_t tag = B.TAG[cur][i];
         const CaseState& S = B.st[tag_case(tag)];
         if (!S.running || !S.alive) continue;
-        const double r = B.cases[tag_case(tag)].fp64 ? B.AV64[i].w : (double)B.AV[i].w;
+        const double r = B.cases[tag_case(tag)].fp64 ? B.AV64[i].w : f32_to_f64(B.AV[i].w);
         if (r != 0.0) B.T64[cur][i] += S.tau * r;
     }
 }
@@ -1198,8 +1220,8 @@ __global__ void __launch_bounds__(256) k_reduce_chunks(Bufs B, int cur) {
             if (tag_kind(tag) != KIND_FLUID) continue;
             const MatDev& M = C.mat[tag_mat(tag)];
             const double T = B.T64[cur][i];
-            const double mm = (double)M.mass;
-            a += mm * (double)M.cp * T;
+            const double mm = f32_to_f64(M.mass);
+            a += mm * f32_to_f64(M.cp) * T;
             b += mm * T;
             m += mm;
         }
