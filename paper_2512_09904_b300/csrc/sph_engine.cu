@@ -348,6 +348,11 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     }
     C.cell_base = (int)H.cell_base;
     C.ncells = c->ncell[0] * c->ncell[1] * c->ncell[2];
+    C.gcorner_ok = 1;
+    for (int a = 0; a < 3; ++a) C.gcorner_ok &= (c->ncell[a] / 2 <= GCORNER_MAX) ? 1 : 0;
+    if (C.gcorner_ok)
+        for (int a = 0; a < 3; ++a)
+            for (int g = 0; g < c->ncell[a] / 2; ++g) C.gcorner[a][g] = C.origin[a] + (double)g * C.gcellw[a];
     C.periodic = F.periodic_mask;
     C.R2 = R2;
     // FP32 guard band around the cut-off: inside it the FP64 rule decides

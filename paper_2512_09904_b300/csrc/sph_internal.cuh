@@ -22,6 +22,7 @@ namespace sph {
 
 constexpr int MAX_MAT = 16;
 constexpr int MAX_BODY = 4;
+constexpr int GCORNER_MAX = 512;  // geometry cells per axis with a tabulated corner
 constexpr uint32_t KIND_FLUID = 0u, KIND_STATIC = 1u, KIND_ROT = 2u;
 constexpr int ERR_NAN = 1, ERR_ESCAPE = 2, ERR_NB_OVERFLOW = 4;
 
@@ -95,6 +96,11 @@ struct CaseDev {
     MatDev mat[MAX_MAT];
     MatDev64 mat64[MAX_MAT];
     BodyDev body[MAX_BODY];
+    // origin + g w of geometry cell g on each axis (FP64), when every axis
+    // has at most GCORNER_MAX geometry cells: the snapshot offset is then
+    // one FP64 subtraction from the position
+    int gcorner_ok;
+    double gcorner[3][GCORNER_MAX];
 };
 
 // The constants the pair passes read per pair, for one case: a table of them
