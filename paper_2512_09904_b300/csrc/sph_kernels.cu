@@ -252,6 +252,12 @@ __device__ __forceinline__ bool f64_to_f32_trunc(double x, float* out) {
     return true;
 }
 
+// The conversion instructions for the rare operands of the two helpers
+// below, out of line so that they are branched around rather than issued
+// (predicated) for every operand.
+__device__ __noinline__ float f64_to_f32_insn(double x) { return (float)x; }
+__device__ __noinline__ double f32_to_f64_insn(float x) { return (double)x; }
+
 // (float)x, the FP64 -> FP32 conversion rounding to nearest (ties to
 // even), with integer operations when x lies in FP32's normal range; the
 // conversion instruction (FP64 pipe) only for the rest (zero, subnormal
@@ -260,7 +266,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
     const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-    if (e <= 0 || e >= 255) return (float)x;
+    if (e <= 0 || e >= 255) return f64_to_f32_insn(x);
     const uint32_t sign = hi & 0x80000000u;
     // 23 kept mantissa bits, 29 dropped ones; a carry out of the mantissa
     // moves into the exponent, which is the correct rounding
@@ -270,12 +276,13 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     return __uint_as_float(f);
 }
 
-// (double)x, exact, with integer operations for normal x; the conversion
-// instruction (FP64 pipe) only for zero, subnormals, infinities and NaN.
+// (double)x, exact, with integer operations for normal x and zeros; the
+// conversion instruction (FP64 pipe) only for subnormals, infinities and NaN.
 __device__ __forceinline__ double f32_to_f64(float x) {
     const uint32_t u = __float_as_uint(x);
     const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 255u) return (double)x;
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // +-0
+    if (e == 0u || e == 255u) return f32_to_f64_insn(x);
     const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)(u << 29));
 }
