@@ -72,6 +72,24 @@ def test_cell_order_bit_exact(sph, oracle, name, make):
     assert np.array_equal(perm, ref)
 
 
+def test_cell_boundaries_order_and_pairs_bit_exact(sph, oracle):
+    """Particles exactly on sort-cell boundaries and a few ulps either side,
+    in a box whose origin is away from zero: the cell order and the pair
+    sets equal the oracle's FP64 rules."""
+    case = W.cell_boundaries()
+    ctx = _ctx(sph, case, steps=1)
+    info = ctx.sph_get_info()
+    assert info["cell_width"][0] == case.meta["sort_cell_width"]
+    perm = ctx.sph_read_cell_order()
+    f = W.flatten(case)
+    ref, _ = oracle.cell_order(f["pos"], case.config["origin"], info["cell_width"], info["ncell"])
+    assert np.array_equal(perm, ref)
+    counts, lst = ctx.sph_read_neighbors()
+    ref_counts, ref_lst = oracle.neighbors(f["pos"], case.support_radius() ** 2)
+    assert np.array_equal(counts, ref_counts)
+    assert np.array_equal(lst, ref_lst)
+
+
 def test_stateless_cell_sort(sph, oracle):
     import torch
     rng = np.random.default_rng(21)

@@ -136,6 +136,26 @@ def test_cell_order_matches_lexsort(oracle):
     assert np.array_equal(cs, np.searchsorted(key[ref], np.arange(ncell.prod() + 1)))
 
 
+def test_cell_order_on_cell_boundaries_matches_lexsort(oracle):
+    """Points on sort-cell boundaries (and a few ulps either side) of a box
+    with a non-zero origin: the oracle's FP64 floor rule against numpy's."""
+    from paper_2512_09904_b300 import workloads as W
+    case = W.cell_boundaries()
+    pos = W.flatten(case)["pos"]
+    origin = np.asarray(case.config["origin"], np.float64)
+    w = case.meta["sort_cell_width"]
+    n = int(round(case.config["extent"][0] / w))
+    ncell = np.array([n, n, n])
+    cellw = np.full(3, w)
+    q = (pos - origin) / cellw
+    on_edge = np.abs(q - np.rint(q)) < 1e-12
+    assert on_edge.any(axis=1).sum() > 1000  # the boundary cases are there
+    perm, _ = oracle.cell_order(pos, origin, cellw, ncell)
+    c = np.clip(np.floor(q), 0, ncell - 1).astype(np.int64)
+    key = (c[:, 2] * ncell[1] + c[:, 1]) * ncell[0] + c[:, 0]
+    assert np.array_equal(perm, np.lexsort((np.arange(len(pos)), key)))
+
+
 # ------------------------------------------------------------- Riemann ----
 def test_riemann_equal_states(oracle):
     us, ps = oracle.riemann(900.0, 0.3, 120.0, 900.0, 0.3, 120.0, 10.0)
