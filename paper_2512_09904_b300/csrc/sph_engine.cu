@@ -20,7 +20,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
+
+#include <sys/mman.h>
 
 #include "sph.h"
 #include "sph_kernels.cuh"
@@ -175,12 +178,89 @@ struct Engine {
 
 // One sph_add_* call, staged on the host until the case is admitted: ids
 // first .. first + n - 1, all of one kind (0 fluid, 1 solid), material and body.
+// Host staging array of doubles.  Arrays of 2 MB and more sit on
+// transparent huge pages where the kernel offers them: a 50 MB block then
+// takes tens of page faults to fill instead of thousands.
+class HostArray {
+  public:
+    HostArray() = default;
+    HostArray(const HostArray&) = delete;
+    HostArray& operator=(const HostArray&) = delete;
+    HostArray(HostArray&& o) noexcept : p_(o.p_), n_(o.n_) { o.p_ = nullptr, o.n_ = 0; }
+    HostArray& operator=(HostArray&& o) noexcept {
+        if (this != &o) {
+            std::free(p_);
+            p_ = o.p_, n_ = o.n_;
+            o.p_ = nullptr, o.n_ = 0;
+        }
+        return *this;
+    }
+    ~HostArray() { std::free(p_); }
+    bool alloc(size_t n) {
+        std::free(p_);
+        p_ = nullptr, n_ = 0;
+        if (n == 0) return true;
+        const size_t huge = (size_t)2 << 20, bytes = n * sizeof(double);
+        if (bytes >= huge) {
+            p_ = (double*)std::aligned_alloc(huge, (bytes + huge - 1) / huge * huge);
+            if (p_) madvise(p_, bytes, MADV_HUGEPAGE);  // advice only: failure is harmless
+        } else {
+            p_ = (double*)std::malloc(bytes);
+        }
+        if (p_) n_ = n;
+        return p_ != nullptr;
+    }
+    size_t size() const { return n_; }
+    bool empty() const { return n_ == 0; }
+    double* data() { return p_; }
+    const double* data() const { return p_; }
+    const double& operator[](size_t i) const { return p_[i]; }
+
+  private:
+    double* p_ = nullptr;
+    size_t n_ = 0;
+};
+
+// dst = src[0..n), in up to 8 host threads for large arrays.  bad: how
+// non-finite values are treated, 0 kept, 1 counted (the return value is the
+// count), 2 replaced by `fill`.
+static int64_t stage_copy(double* dst, const double* src, size_t n, int bad, double fill) {
+    auto part = [=](size_t lo, size_t hi) -> int64_t {
+        int64_t nb = 0;
+        for (size_t q = lo; q < hi; ++q) {
+            double v = src[q];
+            if (bad != 0 && !std::isfinite(v)) {
+                ++nb;
+                if (bad == 2) v = fill;
+            }
+            dst[q] = v;
+        }
+        return nb;
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nt = n < ((size_t)1 << 20) ? 1 : std::min<size_t>(8, std::max(1u, hw));
+    if (nt == 1) return part(0, n);
+    std::vector<int64_t> cnt(nt, 0);
+    std::vector<std::thread> th;
+    try {
+        for (size_t t = 1; t < nt; ++t) th.emplace_back([&, t] { cnt[t] = part(n * t / nt, n * (t + 1) / nt); });
+    } catch (...) {  // no thread to be had: this thread does the rest
+        const size_t done = th.size() + 1;
+        cnt[0] = part(n * done / nt, n);
+    }
+    cnt[0] += part(0, n / nt);
+    for (auto& x : th) x.join();
+    int64_t s = 0;
+    for (int64_t v : cnt) s += v;
+    return s;
+}
+
 struct PBlock {
     int kind = 0, body = -1, mat = 0;
     int64_t n = 0, first = 0;
-    std::vector<double> pos;       // 3n
-    std::vector<double> vel, nrm;  // 3n, or empty: zero
-    std::vector<double> T, rho;    // n, or empty: the material's T_init, rho0
+    HostArray pos;       // 3n
+    HostArray vel, nrm;  // 3n, or empty: zero
+    HostArray T, rho;    // n, or empty: the material's T_init, rho0
 };
 
 struct sph_ctx {
@@ -543,12 +623,22 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
     double* d = nullptr;
     E_CUDA(E, cudaMallocAsync((void**)&d, sizeof(double) * std::max<size_t>(scratch, 1), s));
     cudaError_t e = cudaSuccess;
+    std::vector<void*> pinned;  // staging arrays page-locked for the copies of one block
     for (const PBlock& P : c->blocks) {
         double* q = d;
-        auto up = [&](const std::vector<double>& v) -> const double* {
+        auto up = [&](const HostArray& v) -> const double* {
             if (v.empty() || e != cudaSuccess) return nullptr;
+            const size_t bytes = sizeof(double) * v.size();
+            // large arrays are page-locked for the copy (full-rate DMA instead
+            // of the driver's pageable staging); the pageable copy remains if
+            // that is refused
+            if (bytes >= ((size_t)2 << 20)) {
+                void* h = const_cast<double*>(v.data());
+                if (cudaHostRegister(h, bytes, cudaHostRegisterDefault) == cudaSuccess) pinned.push_back(h);
+                else (void)cudaGetLastError();
+            }
             double* dst = q;
-            e = cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(dst, v.data(), bytes, cudaMemcpyHostToDevice, s);
             q += v.size();
             return dst;
         };
@@ -564,8 +654,12 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
         if (e == cudaSuccess)
             e = launch_admit_block(B, p, (int)P.n, (int)(at + P.first), (int)(idb + P.first), tag, P.kind == 0 ? 1 : 0,
                                    M.rho0, M.T_init, dpos, dvel, dnrm, dT, drho, s);
-        // the scratch is reused by the next block: let this one's kernel finish first
+        // the scratch is reused by the next block: let this one's kernel finish
+        // first (and, after an error, any copy still in flight)
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        else (void)cudaStreamSynchronize(s);
+        for (void* h : pinned) (void)cudaHostUnregister(h);
+        pinned.clear();
         if (e != cudaSuccess) break;
     }
     cudaFreeAsync(d, s);
@@ -1014,25 +1108,27 @@ static sph_status add_common(sph_ctx* c, int kind, int body, int mat, int64_t n,
     const int64_t n0 = c->n_total;
     if (n0 + n > (int64_t)MAX_PARTICLES - 1) return fail(c, SPH_EINVAL, "more than 2^26 - 1 particles");
     const sph_material& M = c->mats[mat];
-    for (int64_t q = 0; q < 3 * n; ++q)
-        if (!std::isfinite(pos[q])) return fail(c, SPH_EINVAL, "non-finite position");
-    if (first_id) *first_id = n0;
-    if (n == 0) return SPH_OK;
+    if (n == 0) {
+        if (first_id) *first_id = n0;
+        return SPH_OK;
+    }
     PBlock P;
     P.kind = kind;
     P.body = kind == 0 ? -1 : body;
     P.mat = mat;
     P.n = n;
     P.first = n0;
-    P.pos.assign(pos, pos + 3 * n);
-    if (vel) P.vel.assign(vel, vel + 3 * n);
-    if (nrm) P.nrm.assign(nrm, nrm + 3 * n);
-    if (T) P.T.assign(T, T + n);
-    if (rho) {
-        P.rho.assign(rho, rho + n);
-        for (double& r : P.rho)
-            if (!std::isfinite(r)) r = M.rho0;
-    }
+    const size_t n1 = (size_t)n, n3 = 3 * n1;
+    if (!P.pos.alloc(n3) || (vel && !P.vel.alloc(n3)) || (nrm && !P.nrm.alloc(n3)) || (T && !P.T.alloc(n1)) ||
+        (rho && !P.rho.alloc(n1)))
+        return fail(c, SPH_ENOMEM, "host staging of %lld particles", (long long)n);
+    // the positions are checked while they are copied; nothing is kept on failure
+    if (stage_copy(P.pos.data(), pos, n3, 1, 0.0) != 0) return fail(c, SPH_EINVAL, "non-finite position");
+    if (vel) stage_copy(P.vel.data(), vel, n3, 0, 0.0);
+    if (nrm) stage_copy(P.nrm.data(), nrm, n3, 0, 0.0);
+    if (T) stage_copy(P.T.data(), T, n1, 0, 0.0);
+    if (rho) stage_copy(P.rho.data(), rho, n1, 2, M.rho0);
+    if (first_id) *first_id = n0;
     c->blocks.push_back(std::move(P));
     c->n_total += n;
     if (kind == 0) c->n_fluid += n;
