@@ -551,6 +551,28 @@ def cell_boundaries(n_random=3000, n_edge=3000, dx=1e-3, h_over_dx=1.3, box=24,
                 dict(seed=seed, sort_cell_width=w))
 
 
+def long_channel(n_clumps=8, side=6, dx=0.5e-3, length=0.7, seed=14):
+    """Oil clumps (side^3 jittered lattices, a temperature ramp, small random
+    velocities) spread along a channel of `length` m, 12 dx wide and high, no
+    gravity or walls.  At the defaults the channel has 538 geometry cells
+    along x (more than the engine tabulates corners for), so the snapshot
+    offsets take their arithmetic form."""
+    rng = np.random.default_rng(seed)
+    w = 12 * dx
+    lat = _grid((0, 0, 0), (side, side, side)).astype(np.float64)
+    xs = np.linspace(0.02, length - 0.01, n_clumps)
+    pos, T, vel = [], [], []
+    for x0 in xs:
+        p = (lat - (side - 1) / 2.0) * dx + np.array([x0, w / 2, w / 2])
+        pos.append(p + _jitter(rng, len(p), dx, 0.02))
+        T.append(300.0 + 10.0 * lat[:, 0] / (side - 1))
+        vel.append(rng.normal(scale=0.02, size=p.shape))
+    cfg = _cfg(origin=(0, 0, 0), extent=(length, w, w), dx=dx, gravity=(0, 0, 0), c0=10.0, u_ref=1.0)
+    mats = {0: _mat(900.0, 0.02, 0.15, 2000.0, 300.0)}
+    fl = [dict(mat=0, pos=np.concatenate(pos), vel=np.concatenate(vel), T=np.concatenate(T), rho=None)]
+    return Case("long_channel", cfg, mats, fl, [], {}, dict(seed=seed))
+
+
 # --------------------------------------------------------------------------
 # Sweep / serving request streams (parameter grid of the paper's case table).
 # --------------------------------------------------------------------------

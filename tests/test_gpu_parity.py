@@ -40,6 +40,8 @@ NEIGHBOR_CASES = [
     ("gear_bath_coarse", lambda: W.gear_bath(dx=5e-3, omega=600.0)),
     ("slab", lambda: W.slab()),
     ("gear_pair", lambda: W.gear_pair()),
+    # more geometry cells along x than have tabulated corners
+    ("long_channel", lambda: W.long_channel()),
 ]
 
 
@@ -149,6 +151,7 @@ FIELD_CASES = [
     ("crowded_box", lambda: W.crowded_box(), 2),
     # two fluid materials: the general-material path of every pair pass
     ("two_fluid_box", lambda: W.two_fluid_box(), 3),
+    ("long_channel", lambda: W.long_channel(), 3),
 ]
 # The crowded block sits at twice the rest density (p = c0^2 rho0): each of its
 # ~150 pair forces is some 30 times the net force, so FP32 cancellation leaves
