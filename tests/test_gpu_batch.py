@@ -72,6 +72,22 @@ def test_alone_equals_mixed_bitwise(sph):
     b.close()
 
 
+def test_alone_equals_mixed_bitwise_untabulated_corners(sph):
+    """A case whose grid is too long for tabulated geometry-cell corners
+    (snapshot offsets in their arithmetic form) next to one with them."""
+    cs = {"chan": W.long_channel(), "cyl": _cases()["cyl"]}
+    steps = 4
+    alone = {k: _alone(sph, c, steps) for k, c in cs.items()}
+    b = _batch_for(sph, list(cs.values()))
+    slots = {k: b.admit(c, n_steps=0) for k, c in cs.items()}
+    b.step(steps)
+    for k, s in slots.items():
+        got = {f: b.fields(s, f) for f in ("pos", "vel", "rho", "T")}
+        got["th"] = b.torque_heat(s)
+        _same(got, alone[k])
+    b.close()
+
+
 def test_case_constant_sources_agree_bitwise(sph):
     # the pair passes read a case's constants from one parameter-block entry
     # (a case alone), a per-slot table (batches of up to 64 slots) or the
