@@ -114,6 +114,32 @@ def test_add_validates_arguments(sphlib):
     ctx.close()
 
 
+def test_large_blocks_are_checked_while_staged(sphlib):
+    """Blocks of more than 2^20 values are copied and checked by several host
+    threads: a non-finite position anywhere fails the call and stages
+    nothing; non-finite densities are replaced, not refused."""
+    case = W.still_tank(nx=4, ny=4, nz=4, wall_h=6)
+    ctx = sphlib.Context(case.config, stream=0)
+    for mid, m in case.materials.items():
+        ctx.sph_set_material(mid, m)
+    n = 400_000
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0.0, 0.01, size=(n, 3))
+    for where in (0, n // 3, n - 1):
+        bad = pos.copy()
+        bad[where, 2] = np.inf if where % 2 else np.nan
+        with pytest.raises(sphlib.SphError) as e:
+            ctx.sph_add_fluid(0, bad)
+        assert e.value.status == sphlib.SPH_EINVAL
+        assert ctx.sph_get_info()["n_fluid"] == 0
+    rho = np.full(n, 870.0)
+    rho[::7] = np.nan
+    assert ctx.sph_add_fluid(0, pos, rho=rho) == 0
+    assert ctx.sph_add_fluid(0, pos) == n
+    assert ctx.sph_get_info()["n_fluid"] == 2 * n
+    ctx.close()
+
+
 def test_reads_before_first_step_are_state_errors(sphlib):
     case = W.periodic_box(n=8)
     ctx = sphlib.Context(case.config, stream=0)
