@@ -301,14 +301,31 @@ static sph_status fail(sph_ctx* c, sph_status s, const char* fmt, ...) {
 }
 
 // ----------------------------------------------------------------- engine ---
+// The engine's device arrays are requested first and then carved out of one
+// allocation (256-byte aligned each), zeroed by one memset: one cudaMalloc
+// instead of one per array.
+struct ArenaReq {
+    void** slot;
+    size_t bytes;
+};
 template <class T>
-static cudaError_t dalloc(Engine& E, T** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+static void dreq(std::vector<ArenaReq>& R, T** p, size_t count) {
+    R.push_back({(void**)p, sizeof(T) * (count ? count : 1)});
+}
+static cudaError_t arena_alloc(Engine& E, const std::vector<ArenaReq>& R) {
+    auto span = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t total = 0;
+    for (const ArenaReq& r : R) total += span(r.bytes);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
     if (e != cudaSuccess) return e;
-    E.allocs.push_back(q);
-    *p = (T*)q;
-    return cudaMemsetAsync(q, 0, sizeof(T) * (count ? count : 1), E.stream);
+    E.allocs.push_back(base);
+    size_t off = 0;
+    for (const ArenaReq& r : R) {
+        *r.slot = (char*)base + off;
+        off += span(r.bytes);
+    }
+    return cudaMemsetAsync(base, 0, total, E.stream);
 }
 
 static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cells_cap, int hist_cap) {
@@ -331,9 +348,8 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     B.max_chunks = (int)((n + RED_CHUNK - 1) / RED_CHUNK) + c_cap + 1;
     B.hist_cap = hist_cap;
     B.one_case = -1;  // set when a step graph is captured over a single case
-    cudaError_t e = cudaSuccess;
-#define AL(p, cnt) \
-    if (e == cudaSuccess) e = dalloc(E, &(p), (size_t)(cnt))
+    std::vector<ArenaReq> reqs;
+#define AL(p, cnt) dreq(reqs, &(p), (size_t)(cnt))
     AL(B.cases, c_cap);
     AL(B.st, c_cap);
     for (int a = 0; a < 3; ++a) {
@@ -391,6 +407,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
     AL(B.novf, 1);
     AL(B.VH, n);
 #undef AL
+    const cudaError_t e = arena_alloc(E, reqs);
     if (e != cudaSuccess)
         return E.fail(e == cudaErrorMemoryAllocation ? SPH_ENOMEM : SPH_ECUDA, "device allocation: %s",
                       cudaGetErrorString(e));
