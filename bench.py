@@ -89,6 +89,12 @@ def parse():
     return ap.parse_args()
 
 
+def workload_name(dx, omega):
+    """The timed workload's name: the 2.19M-oil gear bath at dx = 1 mm."""
+    size = "2M" if abs(dx - 1e-3) < 1e-12 else f"dx{dx * 1e3:g}mm"
+    return f"gear_bath_{size}_omega{omega:g}"
+
+
 def workload(dx, omega):
     from paper_2512_09904_b300 import workloads as W
     return W.gear_bath(dx=dx, omega=omega, depth_frac=0.5, mu=0.1)
@@ -190,7 +196,8 @@ def run_reference(args, rank):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "gear_bath_coarse_5mm", "n_fluid": case.n_fluid, "n_solid": case.n_solid},
+           "config": {"workload": workload_name(args.dx, args.omega), "dx": args.dx, "omega": args.omega,
+                      "sample": {"dx": 5e-3, "n_fluid": case.n_fluid, "n_solid": case.n_solid}},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -333,7 +340,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "gear_bath_2M_omega600", "n_fluid": case.n_fluid, "n_solid": case.n_solid,
+           "config": {"workload": workload_name(args.dx, args.omega), "n_fluid": case.n_fluid, "n_solid": case.n_solid,
                       "dx": args.dx, "omega": args.omega, "substeps_timed": substeps,
                       "pair_arith": "f32", "integration_and_reductions": "f64",
                       "l2": "inputs larger than L2 (~0.7 GB resident state)",
