@@ -176,8 +176,6 @@ struct Engine {
             return (E).fail(SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, __LINE__); \
     } while (0)
 
-// One sph_add_* call, staged on the host until the case is admitted: ids
-// first .. first + n - 1, all of one kind (0 fluid, 1 solid), material and body.
 // Host staging array of doubles.  Arrays of 2 MB and more sit on
 // transparent huge pages where the kernel offers them: a 50 MB block then
 // takes tens of page faults to fill instead of thousands.
@@ -255,6 +253,8 @@ static int64_t stage_copy(double* dst, const double* src, size_t n, int bad, dou
     return s;
 }
 
+// One sph_add_* call, staged on the host until the case is admitted: ids
+// first .. first + n - 1, all of one kind (0 fluid, 1 solid), material and body.
 struct PBlock {
     int kind = 0, body = -1, mat = 0;
     int64_t n = 0, first = 0;
