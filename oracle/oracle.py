@@ -31,7 +31,8 @@ class OrcConfig(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D),
                 ("gravity", D * 3), ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D),
                 ("free_surface", C.c_int), ("periodic_mask", C.c_int), ("max_substeps", C.c_int),
-                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int), ("cfl_T", D)]
+                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int), ("cfl_T", D),
+                ("wall_pstar_printed", C.c_int)]
 
 
 class OrcRelaxConfig(C.Structure):
@@ -51,7 +52,7 @@ def lib():
         L.orc_dW.restype = D; L.orc_dW.argtypes = [D, D]
         L.orc_sigma0.restype = D; L.orc_sigma0.argtypes = [D, D]
         L.orc_riemann.argtypes = [D, D, D, D, D, D, D, PD, PD]
-        L.orc_wall_riemann.argtypes = [D, D, D, D, D, D, D, PD, PD, PD, PD, PD]
+        L.orc_wall_riemann.argtypes = [D, D, D, D, D, D, D, C.c_int, PD, PD, PD, PD, PD]
         L.orc_timesteps.argtypes = [D, D, D, D, D, D, D, PD, PD]
         L.orc_dt_thermal.restype = D; L.orc_dt_thermal.argtypes = [D, D, D, D, D]
         L.orc_neighbors.restype = I64
@@ -100,9 +101,10 @@ def riemann(rhoL, UL, pL, rhoR, UR, pR, c0):
     return us.value, ps.value
 
 
-def wall_riemann(rho_f, UL, p_f, u_w, g_dot_rfw, rho0, c0):
+def wall_riemann(rho_f, UL, p_f, u_w, g_dot_rfw, rho0, c0, printed=0):
     out = [D() for _ in range(5)]
-    lib().orc_wall_riemann(rho_f, UL, p_f, u_w, g_dot_rfw, rho0, c0, *[C.byref(o) for o in out])
+    lib().orc_wall_riemann(rho_f, UL, p_f, u_w, g_dot_rfw, rho0, c0, int(printed),
+                           *[C.byref(o) for o in out])
     return dict(UR=out[0].value, PR=out[1].value, rhoR=out[2].value, Ustar=out[3].value,
                 pstar=out[4].value)
 
@@ -191,7 +193,8 @@ def cell_order(pos, origin, cellw, ncell):
 
 
 FIELD = dict(pos=(0, 3), vel=(1, 3), rho=(2, 1), p=(3, 1), T=(4, 1), drho=(5, 1), a_visc=(6, 3),
-             dTdt=(7, 1), sigma=(8, 1), normal=(9, 3), wall_vel=(10, 3), contact=(11, 1))
+             dTdt=(7, 1), sigma=(8, 1), normal=(9, 3), wall_vel=(10, 3), contact=(11, 1),
+             rho_reinit=(12, 1))
 
 
 class OracleSim:
@@ -212,6 +215,7 @@ class OracleSim:
         oc.viscous_heating = cfg.get("viscous_heating", 0)
         oc.vstar_literal = cfg.get("vstar_literal", 0)
         oc.cfl_T = cfg.get("cfl_T", 0.5)
+        oc.wall_pstar_printed = cfg.get("wall_pstar_printed", 0)
         self._p = L.orc_create(C.byref(oc))
         for mid, m in case.materials.items():
             om = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])

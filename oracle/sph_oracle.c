@@ -95,18 +95,22 @@ void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR, doub
  * (p_w, rho_w) = (P_R, rho_R) plus the limiter term of Eq. (12) on the same
  * one-sided states, beta = min(3 max(U_L - U_R, 0), c0).  Eq. (19) alone has no
  * term that resists a particle approaching the wall, and with it fluid
- * particles drift into walls at edges and corners. */
+ * particles drift into walls at edges and corners.  printed = 1 keeps Eq. (19)
+ * exactly as printed (no limiter term), for comparison. */
 void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_dot_rfw,
-                      double rho0, double c0, double* UR, double* PR, double* rhoR,
+                      double rho0, double c0, int printed, double* UR, double* PR, double* rhoR,
                       double* Ustar, double* pstar) {
     *UR = -UL + 2.0 * u_w;
     *PR = p_f + rho_f * g_dot_rfw;
     *rhoR = rho0 + *PR / (c0 * c0);
     *Ustar = 0.5 * (UL + *UR) + (p_f - *PR) / (c0 * (rho_f + *rhoR));
+    /* Eq. (19): the density-weighted mean, with (p_w, rho_w) = (P_R, rho_R) */
+    *pstar = (rho_f * *PR + *rhoR * p_f) / (rho_f + *rhoR);
+    if (printed) return;
     double dU = UL - *UR;
     double beta = 3.0 * (dU > 0.0 ? dU : 0.0);
     if (beta > c0) beta = c0;
-    *pstar = (rho_f * *PR + *rhoR * p_f) / (rho_f + *rhoR) + rho_f * *rhoR * beta * dU / (rho_f + *rhoR);
+    *pstar += rho_f * *rhoR * beta * dU / (rho_f + *rhoR);
 }
 
 /* Eq. (25).  READING: |v|max is floored at u_ref = c0/10 (the anticipated
@@ -258,7 +262,7 @@ struct orc_sim {
     int64_t n, cap;
     int *kind, *mat_id, *body_id;
     double *pos, *vel, *rho, *drho, *p, *T, *T0, *mass;
-    double *ref_pos, *ref_nrm, *nrm, *wvel, *av, *dTdt, *acc, *sigma, *snap, *contact;
+    double *ref_pos, *ref_nrm, *nrm, *wvel, *av, *dTdt, *acc, *sigma, *snap, *contact, *rho_D;
     int64_t* nb_start;
     int32_t* nb;
     int64_t nb_cap;
@@ -303,7 +307,7 @@ void orc_destroy(orc_sim* S) {
     if (!S) return;
     void* ptrs[] = {S->kind, S->mat_id, S->body_id, S->pos, S->vel, S->rho, S->drho, S->p, S->T,
                     S->T0, S->mass, S->ref_pos, S->ref_nrm, S->nrm, S->wvel, S->av, S->dTdt,
-                    S->acc, S->sigma, S->snap, S->contact, S->nb_start, S->nb};
+                    S->acc, S->sigma, S->snap, S->contact, S->rho_D, S->nb_start, S->nb};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(S);
 }
@@ -334,6 +338,7 @@ static void grow(orc_sim* S, int64_t need) {
     RE(S->ref_pos, double, 3); RE(S->ref_nrm, double, 3); RE(S->nrm, double, 3);
     RE(S->wvel, double, 3); RE(S->av, double, 3); RE(S->dTdt, double, 1); RE(S->acc, double, 3);
     RE(S->sigma, double, 1); RE(S->snap, double, 3); RE(S->contact, double, 1);
+    RE(S->rho_D, double, 1);
 #undef RE
     S->cap = c;
 }
@@ -370,6 +375,7 @@ int orc_add_particles(orc_sim* S, int64_t n, const int* kind, const int* mat, co
         S->dTdt[i] = 0.0;
         S->sigma[i] = 0.0;
         S->contact[i] = 0.0;
+        S->rho_D[i] = S->rho[i];
     }
     S->n += n;
     return 0;
@@ -501,6 +507,7 @@ int orc_step(orc_sim* S, int n_adv) {
             double r0 = S->mat[S->mat_id[i]].rho0;
             double rr = r0 * s / S->sigma0;
             S->rho[i] = C->free_surface ? (S->rho[i] > rr ? S->rho[i] : rr) : rr;
+            S->rho_D[i] = S->rho[i];
         }
 
         /* ---- pass V: viscous acceleration, Eq. (10) and Eq. (18) ---------- */
@@ -656,7 +663,7 @@ int orc_step(orc_sim* S, int n_adv) {
                         double UL = -dot3(S->nrm + 3 * j, S->vel + 3 * i);
                         double uw = -dot3(S->nrm + 3 * j, S->wvel + 3 * j);
                         double UR, PR, rhoR;
-                        orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, &UR, &PR, &rhoR, &Ustar, &pstar);
+                        orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, C->wall_pstar_printed, &UR, &PR, &rhoR, &Ustar, &pstar);
                     }
                     double c = -2.0 * fluid_volume(S, j) / rho_i * pstar * dW;
                     for (int k = 0; k < 3; ++k) a[k] += c * e[k];
@@ -679,7 +686,7 @@ int orc_step(orc_sim* S, int n_adv) {
                     double g_rfw = -dot3(C->gravity, rv);
                     double UL = -dot3(S->nrm + 3 * j, S->vel + 3 * i);
                     double uw = -dot3(S->nrm + 3 * j, S->wvel + 3 * j);
-                    orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, &UR, &PR, &rhoR, &Ustar, &pstar);
+                    orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, C->wall_pstar_printed, &UR, &PR, &rhoR, &Ustar, &pstar);
                     double c = -2.0 * S->vol / rho_i * pstar * dW;
                     double F[3];
                     for (int k = 0; k < 3; ++k) F[k] = -S->mass[i] * c * e[k];
@@ -733,7 +740,7 @@ int orc_step(orc_sim* S, int n_adv) {
                         double UL = -dot3(nw, S->vel + 3 * i);
                         double uw = -dot3(nw, S->wvel + 3 * j);
                         double UR, PR, rhoR;
-                        orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, &UR, &PR, &rhoR, &Ustar, &pstar);
+                        orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, C->wall_pstar_printed, &UR, &PR, &rhoR, &Ustar, &pstar);
                         d += 2.0 * rho_i * S->vol * (Ustar - UL) * dot3(nw, e) * dW;
                     }
                 }
@@ -779,6 +786,7 @@ int orc_get_field(const orc_sim* S, int field, double* out) {
     case 9: memcpy(out, S->nrm, sizeof(double) * 3 * (size_t)n); return 0;
     case 10: memcpy(out, S->wvel, sizeof(double) * 3 * (size_t)n); return 0;
     case 11: memcpy(out, S->contact, sizeof(double) * (size_t)n); return 0;
+    case 12: memcpy(out, S->rho_D, sizeof(double) * (size_t)n); return 0;
     default: return -1;
     }
 }

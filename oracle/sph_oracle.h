@@ -37,6 +37,10 @@ typedef struct {
     int vstar_literal;           /* 1: Eq. (13)'s interface velocity with its printed sign,
                                     v* = (U* - U~) e_ij + v~ (default 0: v* = -(U* - U~) e_ij + v~) */
     double cfl_T;                /* Eq. (26) coefficient (0.5 printed); 0: no thermal bound */
+    int wall_pstar_printed;      /* 1: the wall interface pressure exactly as Eq. (19) prints it,
+                                    the density-weighted mean of the fluid and mirror pressures
+                                    (default 0: that mean plus Eq. (12)'s limiter term on the
+                                    same one-sided states) */
 } orc_config;
 
 typedef struct { double rho0, mu, k, cp, T_init; int fixed_T; } orc_material;
@@ -50,9 +54,10 @@ double orc_sigma0(double dx, double h);/* sum of W over an exact cubic lattice i
 /* fluid-fluid Riemann (Sec. 2.3): returns U*, p* for states (rho,U,p) L/R */
 void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR, double pR,
                  double c0, double* Ustar, double* pstar);
-/* wall one-sided Riemann (Sec. 2.5): right state and interface values */
+/* wall one-sided Riemann (Sec. 2.5): right state and interface values;
+ * printed = 1 gives Eq. (19)'s p* without the limiter term */
 void orc_wall_riemann(double rho_f, double UL, double p_f, double u_w, double g_dot_rfw,
-                      double rho0, double c0, double* UR, double* PR, double* rhoR,
+                      double rho0, double c0, int printed, double* UR, double* PR, double* rhoR,
                       double* Ustar, double* pstar);
 void orc_timesteps(double h, double vmax, double u_ref, double nu_max, double c0,
                    double cfl_ad, double cfl_ac, double* dt_ad, double* dt_ac);
@@ -85,7 +90,9 @@ int orc_add_particles(orc_sim*, int64_t n, const int* kind, const int* mat, cons
 int orc_step(orc_sim*, int n_adv);
 /* fields (id order): 0 pos[3], 1 vel[3], 2 rho, 3 p, 4 T, 5 drho, 6 a_visc[3], 7 dTdt,
  * 8 sigma (kernel sum of pass D), 9 wall normal[3], 10 wall velocity[3],
- * 11 contact factor of rigid-body particles (Sec. 2.7; 0 for the others) */
+ * 11 contact factor of rigid-body particles (Sec. 2.7; 0 for the others),
+ * 12 fluid density right after pass D of the last advection step (Eq. 14 / 15;
+ *    the material rho0 for solids) */
 int orc_get_field(const orc_sim*, int field, double* out);
 
 /* --- physics-driven particle relaxation (Sec. 2.2), a pre-processing step --- */

@@ -616,3 +616,155 @@ def test_thermal_bound_coefficient_at_h13(oracle):
     sim, _, _ = _slab_bounded(oracle, 1.3, 0.2)
     T = sim.field("T")
     assert T.min() >= -1e-12 and T.max() <= 1.0 + 1e-12
+
+
+# ------------------------------------- density re-initialisation (Sec. 2.4) ---
+def _lattice_sum(oracle, h, dx, keep=lambda c: True):
+    """Kernel sum over the integer lattice points p of spacing dx with
+    |p dx| < 2h, the origin (the particle itself) included, restricted to
+    the points whose z offset c passes `keep`: an independent count of the
+    lattice, with the pinned kernel as the only shared piece."""
+    m = int(math.ceil(2 * h / dx)) + 1
+    s = 0.0
+    for c in range(-m, m + 1):
+        if not keep(c):
+            continue
+        for b in range(-m, m + 1):
+            for a in range(-m, m + 1):
+                r = dx * math.sqrt(a * a + b * b + c * c)
+                if r < 2 * h:
+                    s += oracle.W(r, h)
+    return s
+
+
+def _reinit_case(free_surface, rho_fn, n=10, m=6, layers=3, rho0=1000.0):
+    """An exact oil lattice n x n x m (periodic in x and y, at rest, g = 0) on
+    `layers` wall layers that continue the lattice below it (z < 0); the top
+    layer k = m - 1 is a plane free surface.  rho_fn(k, flat index) gives the
+    initial density rho* per particle."""
+    idx = W._grid((0, 0, 0), (n, n, m))
+    pos = (idx + 0.5) * DX
+    rho = np.array([rho_fn(int(k), q) for q, k in enumerate(idx[:, 2])], np.float64)
+    widx = W._grid((0, 0, -layers), (n, n, 0))
+    wpos = (widx + 0.5) * DX
+    nrm = np.tile([0.0, 0.0, 1.0], (len(wpos), 1))
+    cfg = W._cfg(origin=(0.0, 0.0, -(layers + 1) * DX), extent=(n * DX, n * DX, (m + layers + 6) * DX),
+                 dx=DX, gravity=(0, 0, 0), periodic_mask=3, free_surface=free_surface, max_substeps=1)
+    mats = {0: W._mat(rho0, 0.0, 0.0, 2000.0, 300.0), 1: W._mat(7850.0, 0.0, 0.0, 460.0, 300.0, fixed_T=1)}
+    case = W.Case("reinit", cfg, mats, [dict(mat=0, pos=pos, vel=None, T=None, rho=rho)],
+                  [dict(body=-1, mat=1, pos=wpos, normal=nrm, T=None)])
+    return case, idx
+
+
+def test_reinit_kernel_sum_counts_self_and_walls(oracle):
+    # sigma = sum_j W_ij over fluid and wall partners plus the particle itself:
+    # on an exact lattice every layer below the free surface (the bottom one
+    # beside the wall included) sees the full lattice sum, and the surface
+    # layer sees the lattice sum over z offsets <= 0
+    case, idx = _reinit_case(0, lambda k, q: 1000.0)
+    h = 1.3 * DX
+    full = _lattice_sum(oracle, h, DX)
+    assert oracle.sigma0(DX, h) == pytest.approx(full, rel=1e-13)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    sig = sim.field("sigma")[:case.n_fluid]
+    k = idx[:, 2]
+    m = k.max() + 1
+    assert np.allclose(sig[k <= m - 3], full, rtol=1e-13, atol=0)
+    for layer in (m - 2, m - 1):
+        part = _lattice_sum(oracle, h, DX, keep=lambda c, t=layer: t + c <= m - 1)
+        assert np.allclose(sig[k == layer], part, rtol=1e-13, atol=0)
+    # the self term and the wall partners are both visible: dropping either
+    # would move the bottom layer's sum by at least W(0) or by a wall row
+    assert oracle.W(0.0, h) > 1e-3 * full
+
+
+def test_reinit_eq15_replaces_density(oracle):
+    # Eq. (15) (no free surface): rho = rho0 sumW / sumW0 whatever rho* was;
+    # interior and wall-side particles get rho0 exactly, surface particles the
+    # half-lattice fraction of it
+    rho0 = 1000.0
+    case, idx = _reinit_case(0, lambda k, q: rho0 * (1.03 if q % 2 else 0.95), rho0=rho0)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    r = sim.field("rho_reinit")[:case.n_fluid]
+    k = idx[:, 2]
+    m = k.max() + 1
+    h = 1.3 * DX
+    full = _lattice_sum(oracle, h, DX)
+    assert np.allclose(r[k <= m - 3], rho0, rtol=1e-13, atol=0)
+    top = _lattice_sum(oracle, h, DX, keep=lambda c: c <= 0)
+    assert np.allclose(r[k == m - 1], rho0 * top / full, rtol=1e-13, atol=0)
+    assert 0.5 < top / full < 0.9  # the centre plane and self weigh most
+
+
+def test_reinit_eq14_keeps_larger_and_raises_smaller(oracle):
+    # Eq. (14) (free surface): rho = max(rho*, rho0 sumW / sumW0)
+    rho0 = 1000.0
+    m = 6
+
+    def rho_star(k, q):
+        if k == m - 1:  # surface: one far below its lattice value, one at rho0
+            return 0.3 * rho0 if q % 2 else rho0
+        return rho0 * (1.01 if q % 2 else 0.99)
+
+    case, idx = _reinit_case(1, rho_star, m=m, rho0=rho0)
+    rs = np.array([rho_star(int(k), q) for q, k in enumerate(idx[:, 2])])
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    r = sim.field("rho_reinit")[:case.n_fluid]
+    k, odd = idx[:, 2], np.arange(len(idx)) % 2 == 1
+    inner = k <= m - 3
+    assert np.all(r[inner & odd] == rs[inner & odd])                      # 1.01 rho0 kept
+    assert np.allclose(r[inner & ~odd], rho0, rtol=1e-13, atol=0)        # 0.99 rho0 raised
+    h = 1.3 * DX
+    frac = _lattice_sum(oracle, h, DX, keep=lambda c: c <= 0) / _lattice_sum(oracle, h, DX)
+    surf = k == m - 1
+    assert np.allclose(r[surf & odd], rho0 * frac, rtol=1e-13, atol=0)   # 0.3 rho0 raised
+    assert np.all(r[surf & ~odd] == rho0)                                 # rho0 kept
+
+
+def test_reinit_eq15_still_tank_runs_and_keeps_mass(oracle):
+    # the Eq. (15) branch through whole advection steps on the tank with walls:
+    # densities stay finite and near rho0 in the interior, mass is exact
+    case = W.still_tank(nx=10, ny=10, nz=6, wall_h=10)
+    case.config = dict(case.config, free_surface=0)
+    sim = oracle.OracleSim(case)
+    sim.step(3)
+    fl = W.flatten(case)["kind"] == 0
+    rho0 = case.materials[0]["rho0"]
+    r = sim.field("rho")[fl]
+    assert np.all(np.isfinite(r)) and np.abs(r / rho0 - 1).max() < 0.5
+    assert np.all(np.isfinite(sim.field("vel")[fl]))
+
+
+# ------------------------------------------------ Eq. (19) as printed ---
+def test_wall_pstar_printed_is_density_weighted_mean(oracle):
+    # with the switch on, p* is Eq. (19) exactly: (rho_f P_R + rho_R p_f) / (rho_f + rho_R),
+    # also for a particle approaching the wall fast (where the default adds
+    # the limiter term and gives the water-hammer pressure)
+    rho, c0, U = 900.0, 10.0, 3.0
+    s = oracle.wall_riemann(rho, U, 0.0, 0.0, 0.0, rho, c0, printed=1)
+    assert s["pstar"] == 0.0
+    p_f, g_r = 120.0, 9.81 * 2e-3
+    PR = p_f + rho * g_r
+    rhoR = rho + PR / c0 ** 2
+    s = oracle.wall_riemann(rho, U, p_f, 0.0, g_r, rho, c0, printed=1)
+    assert s["pstar"] == pytest.approx((rho * PR + rhoR * p_f) / (rho + rhoR), rel=1e-14)
+    d = oracle.wall_riemann(rho, U, p_f, 0.0, g_r, rho, c0, printed=0)
+    beta = min(3 * 2 * U, c0)
+    assert d["pstar"] - s["pstar"] == pytest.approx(rho * rhoR * beta * 2 * U / (rho + rhoR), rel=1e-12)
+    assert d["Ustar"] == s["Ustar"]  # the switch touches the pressure only
+
+
+def test_wall_pstar_printed_weakens_the_wall(oracle):
+    # oil thrown at a still wall: without the limiter term the wall pushes back
+    # less, so the oil's speed into the wall falls less in one advection step
+    def impact(printed):
+        case, idx = _reinit_case(1, lambda k, q: 1000.0)
+        case.fluids[0]["vel"] = np.tile([0.0, 0.0, -1.0], (case.n_fluid, 1))
+        case.config = dict(case.config, wall_pstar_printed=printed, max_substeps=0)
+        sim = oracle.OracleSim(case)
+        sim.step(1)
+        return sim.field("vel")[:case.n_fluid][idx[:, 2] == 0, 2].mean()
+    assert impact(1) < impact(0) < 0.0
