@@ -83,6 +83,14 @@ typedef struct {
                                     0.5 keeps the Cleary update stable at h = 1.0 dx but not at
                                     h = 1.3 dx in 3-D, where about 0.2 is needed.  Negative or
                                     NaN: SPH_EINVAL. */
+    int wall_pstar_printed;      /* 0 (default): the wall interface pressure of the one-sided
+                                    problem (Sec. 2.5) is Eq. (19)'s density-weighted mean of
+                                    the fluid and mirror pressures plus Eq. (12)'s limiter term
+                                    rho_f rho_R beta (U_L - U_R) / (rho_f + rho_R) on the same
+                                    states, so that a particle approaching a wall meets a
+                                    rising pressure; 1: Eq. (19) exactly as printed, without
+                                    that term (for study; needs pair_precision = 1).  Other
+                                    values, or 1 with FP32 pairs: SPH_EINVAL. */
 } sph_config;
 
 /* Material table entry (Sec. 2.6 and the paper's property tables). */
@@ -95,17 +103,27 @@ typedef struct {
     int fixed_T;    /* solids only: 1 = temperature held (heat source/sink) */
 } sph_material;
 
-/* Create a single-case context.  cfg: host, copied.  cuda_stream: a
- * cudaStream_t or NULL.  *out receives the context.
- * Errors: SPH_EINVAL (non-positive dx/h/extent, periodic axis with < 3 cells),
- * SPH_ECUDA. */
+/* Create a single-case context: the problem of Sec. 2.1 (weakly compressible
+ * flow, Eq. 1, closed by the linear EoS of Eq. 2 with sound speed c0) on the
+ * particle spacing dx and smoothing length h, stepped by the dual criteria of
+ * Sec. 2.8 (Eq. 25 with cfl_ad, cfl_ac; Eq. 26 with cfl_T) and re-initialised
+ * by Eq. (14) or (15) (Sec. 2.4, free_surface).  cfg: host, copied.
+ * cuda_stream: a cudaStream_t or NULL.  *out receives the context, owned by
+ * the caller until sph_destroy.
+ * Errors: SPH_EINVAL (non-positive dx/h/extent, periodic axis with < 3 cells,
+ * a switch out of range), SPH_ECUDA. */
 sph_status sph_create(const sph_config* cfg, void* cuda_stream, sph_ctx** out);
 
 /* Free the context and all its device memory.  NULL is accepted. */
 sph_status sph_destroy(sph_ctx* ctx);
 
-/* Set material `material_id` (0..15).  Must precede the particles that use it
- * and the first step.  Errors: SPH_EINVAL, SPH_ESTATE. */
+/* Set material `material_id` (0..15): the reference density rho0 of Eq. (2),
+ * the dynamic viscosity eta of Eq. (10) and Eq. (18), and the conductivity k
+ * and specific heat c_p of the Cleary conduction, Eq. (22) (Sec. 2.6); the
+ * paper's values are its Table 3 (slabs) and Table 6 (lubricant and gears).
+ * mat: host, copied.  Must precede the particles that use it and the first
+ * step.  Errors: SPH_EINVAL (id out of range, NULL, rho0 or c_p not
+ * positive, k or eta negative), SPH_ESTATE. */
 sph_status sph_set_material(sph_ctx* ctx, int material_id, const sph_material* mat);
 
 /* Append n fluid particles of material `material_id`.
@@ -124,8 +142,12 @@ sph_status sph_add_fluid(sph_ctx* ctx, int material_id, int64_t n, const double*
 sph_status sph_add_solid(sph_ctx* ctx, int body_id, int material_id, int64_t n, const double* pos,
                          const double* normal, const double* T, int64_t* first_id);
 
-/* Prescribed rigid rotation of body `body_id` (0..3): angle omega*t about the
- * unit axis through center.  Errors: SPH_EINVAL, SPH_ESTATE. */
+/* Prescribed rigid rotation of body `body_id` (0..3), as the gears of the
+ * paper's gearbox runs are driven at set shaft speeds (Sec. 4.1, Table 5):
+ * angle omega*t (rad/s) about the unit axis through center (host double[3]
+ * each, m, copied); the body's dummy particles move with it and their wall
+ * velocity omega x (r - center) enters the wall problem of Sec. 2.5.
+ * Errors: SPH_EINVAL (id out of range, axis not unit), SPH_ESTATE. */
 sph_status sph_set_rotation(sph_ctx* ctx, int body_id, const double center[3], const double axis[3],
                             double omega);
 
@@ -133,7 +155,9 @@ sph_status sph_set_rotation(sph_ctx* ctx, int body_id, const double center[3], c
  * *sim_time_out (may be NULL) receives the simulated time.  The first call
  * uploads the particles and builds the step's CUDA graph.
  * Errors: SPH_EUNSTABLE (state no longer finite or a fluid particle left the
- * box; the context stays readable), SPH_ENOMEM, SPH_ECUDA. */
+ * box; the case is frozen after the advection step that found it, so later
+ * calls leave its state unchanged and return SPH_EUNSTABLE again, and the
+ * context stays readable), SPH_ENOMEM, SPH_ECUDA. */
 sph_status sph_step(sph_ctx* ctx, int n_advection_steps, double* sim_time_out);
 
 /* Churning torque and heat-up.  torque_axis: torque of the fluid on body
@@ -177,7 +201,12 @@ enum {
 };
 
 /* Copy field `field` of all n particles (n must equal the particle count)
- * into host_dst (double, n or n*3 values).  Errors: SPH_EINVAL, SPH_ESTATE. */
+ * into host_dst (host double, n or n*3 values, owned by the caller), in
+ * particle id order: the state of Eq. (1) (positions, velocities, densities
+ * and the EoS pressure of Eq. 2), the temperature of Eq. (4), the rates of
+ * the last step (continuity, Eq. 10; viscous acceleration; conduction,
+ * Eq. 22) and the contact factor of Eq. (24).
+ * Errors: SPH_EINVAL (unknown field, n mismatch, NULL), SPH_ESTATE. */
 sph_status sph_read_fields(sph_ctx* ctx, int field, void* host_dst, int64_t n);
 
 /* Neighbour pairs of the last advection step's frozen snapshot (pair
@@ -384,7 +413,10 @@ const char* sph_batch_last_error(const sph_batch* b);
 sph_status sph_batch_admit(sph_batch* b, sph_ctx* staged, int64_t n_steps, int* slot);
 
 /* Advance every running case n advection steps (finished cases stay
- * resident, unchanged, until retired).  Errors: SPH_ECUDA. */
+ * resident, unchanged, until retired).  A case that turns unstable (NaN/Inf
+ * state or a fluid particle out of its box) is frozen after the advection
+ * step that found it and polls as SPH_BATCH_UNSTABLE; the other cases go on
+ * as if it were not there.  Errors: SPH_ECUDA. */
 sph_status sph_batch_step(sph_batch* b, int n_advection_steps);
 
 /* Steps done, simulated time and state (SPH_BATCH_*) of a resident case. */
@@ -427,14 +459,17 @@ sph_status sph_batch_profile_read(sph_batch* b, double* ms, int64_t* launches, i
  *
  * Same arguments, layout and result as sph_cell_sort.  Scratch lives in one
  * fixed device array of about 12 SPH_NOALLOC_MAX_N + 4 SPH_NOALLOC_MAX_CELLS
- * bytes (16 MiB), which every GPU that loads this library holds until the
- * process exits.  The call allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine.
+ * bytes (16 MiB).  It occupies a device from the first call there (from the
+ * library's load instead when CUDA_MODULE_LOADING=EAGER) until the process
+ * exits.  The call allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.
  *  - n > SPH_NOALLOC_MAX_N or more than SPH_NOALLOC_MAX_CELLS cells:
  *    SPH_EINVAL, with the reason in sph_last_error(NULL).
  *  - The first call on a device looks up the scratch array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
- *    outside any stream capture.  A failed lookup returns SPH_ECUDA.
+ *    outside any stream capture.  A failed lookup returns SPH_ECUDA.  The
+ *    address is kept for the process: resetting the device (cudaDeviceReset
+ *    or a primary-context reset) after the first call is not supported.
  *  - All calls share the one array (it keeps the last call's contents; the
  *    per-cell counters are cleared by each call).  Calls whose work overlaps
  *    on the GPU (different streams, or different host threads) race on it:

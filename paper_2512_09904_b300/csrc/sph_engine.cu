@@ -485,6 +485,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.fp64 = F.pair_precision == 1 ? 1 : 0;
     C.visc_heat = F.viscous_heating ? 1 : 0;
     C.vstar_lit = F.vstar_literal ? 1 : 0;
+    C.wall_printed = F.wall_pstar_printed ? 1 : 0;
     C.u_ref = F.u_ref;
     C.cfl_ad = F.cfl_ad;
     C.cfl_ac = F.cfl_ac;
@@ -1061,7 +1062,9 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
     if (!(cfg->dx > 0) || !(cfg->h_over_dx > 0) || !(cfg->c0 > 0) || !(cfg->u_ref > 0) || !(cfg->cfl_ad > 0) ||
         !(cfg->cfl_ac > 0) || (cfg->pair_precision != 0 && cfg->pair_precision != 1) ||
         (cfg->viscous_heating != 0 && cfg->viscous_heating != 1) ||
-        (cfg->vstar_literal != 0 && !(cfg->vstar_literal == 1 && cfg->pair_precision == 1)) || !(cfg->cfl_T >= 0))
+        (cfg->vstar_literal != 0 && !(cfg->vstar_literal == 1 && cfg->pair_precision == 1)) ||
+        (cfg->wall_pstar_printed != 0 && !(cfg->wall_pstar_printed == 1 && cfg->pair_precision == 1)) ||
+        !(cfg->cfl_T >= 0))
         return SPH_EINVAL;
     sph_ctx* c = new sph_ctx();
     c->cfg = *cfg;
@@ -1539,6 +1542,7 @@ sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], c
         sph::set_stateless_error("sph_cell_sort: n >= 2^31");
         return SPH_EINVAL;
     }
+    // the running product is checked after every factor, so it never overflows
     int64_t nc = 1;
     for (int a = 0; a < 3; ++a) {
         if (ncell[a] < 1 || !(cellw[a] > 0)) {
@@ -1546,10 +1550,10 @@ sph_status sph_cell_sort(const double* pos, int64_t n, const double origin[3], c
             return SPH_EINVAL;
         }
         nc *= ncell[a];
-    }
-    if (nc > ((int64_t)1 << 30)) {
-        sph::set_stateless_error("sph_cell_sort: more than 2^30 cells");
-        return SPH_EINVAL;
+        if (nc > ((int64_t)1 << 30)) {
+            sph::set_stateless_error("sph_cell_sort: more than 2^30 cells");
+            return SPH_EINVAL;
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = scan_blocks((int)nc) + 1;

@@ -92,6 +92,7 @@ struct CaseDev {
     int free_surface, kcap, n_body, fp64;
     int visc_heat;  // add the viscous-dissipation heating 2 mu S:S (extension; off in the paper)
     int vstar_lit;  // Eq. (13) with its printed sign (FP64 pairs only; off by default)
+    int wall_printed;  // Eq. (19) without the limiter term (FP64 pairs only; off by default)
     MatDev fluid;   // the material of the case's fluid particles, when they all share one
     MatDev mat[MAX_MAT];
     MatDev64 mat64[MAX_MAT];

@@ -1301,6 +1301,10 @@ __global__ void k_adv_end_cases(Bufs B) {
         h[7] = B.cases[c].fp64 ? __longlong_as_double((long long)S.vmax64_bits) : (double)__uint_as_float(S.vmax_bits);
     }
     if (S.steps_req > 0 && S.adv_steps >= S.steps_req) S.running = 0;
+    // an unstable case (NaN/Inf state, or a fluid particle out of the box) is
+    // frozen after the step that found it: later steps leave its state as it
+    // was, readable, and the other cases of a batch go on unaffected
+    if (S.err) S.running = 0;
 }
 
 // ------------------------------------------------------------- readback ---

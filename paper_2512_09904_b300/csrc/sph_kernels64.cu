@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(128) k_passM64(Bufs B, int par) {
             const double PR = p_i + rho_i * g_rfw;
             const double rhoR = Mi.rho0 + PR * C.inv_c02_64;
             const double dUw = -2.0 * dot3(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z);
-            const double beta = fmin(3.0 * fmax(dUw, 0.0), C.c0_64);
+            // Eq. (19) plus the limiter term of Eq. (12); wall_printed: Eq. (19) alone
+            const double beta = C.wall_printed ? 0.0 : fmin(3.0 * fmax(dUw, 0.0), C.c0_64);
             const double pstar = (rho_i * PR + rhoR * p_i + rho_i * rhoR * beta * dUw) / (rho_i + rhoR);
             const double coef = C.vol64 * pstar * dW * inv_r;
             ax += coef * rx;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(128) k_passM64(Bufs B, int par) {
         const double PR = p_j + rho_j * g_rfw;
         const double rhoR = Mj.rho0 + PR * C.inv_c02_64;
         const double dUw = -2.0 * dot3(nwi.x, nwi.y, nwi.z, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z);
-        const double beta = fmin(3.0 * fmax(dUw, 0.0), C.c0_64);
+        const double beta = C.wall_printed ? 0.0 : fmin(3.0 * fmax(dUw, 0.0), C.c0_64);
         const double pstar = (rho_j * PR + rhoR * p_j + rho_j * rhoR * beta * dUw) / (rho_j + rhoR);
         const double cf = -Mj.mass * (2.0 * C.vol64 / rho_j) * pstar * dW * inv_r;
         fx += cf * rx;

@@ -5,8 +5,10 @@
 // allocation fails there), a latency-critical loop that cannot afford the
 // implicit device synchronisation of cudaMalloc/cudaFree, or a host that
 // forbids allocations outside its own memory manager.  For them this file
-// keeps the sort's scratch in a fixed device array that every GPU loading the
-// library holds until the process exits.
+// keeps the sort's scratch in a fixed device array, placed on a device when
+// this library's module is loaded there (at the first call on that device
+// under lazy module loading, the default; at library load with
+// CUDA_MODULE_LOADING=EAGER) and held until the process exits.
 #include <mutex>
 
 #include "sph.h"
@@ -33,6 +35,8 @@ uint32_t* g_addr[kMaxDevices] = {};
 // Device address of g_scratch on the current device, looked up once per
 // device.  In host code the name g_scratch is only a host-side stand-in, so
 // the address must come from cudaGetSymbolAddress with the device current.
+// The cached address is not refreshed: a device reset (cudaDeviceReset, or a
+// primary-context reset) after the first call is not supported.
 cudaError_t scratch_address(uint32_t** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -58,6 +62,11 @@ extern "C" sph_status sph_cell_sort_noalloc(const double* pos, int64_t n, const 
         sph::set_stateless_error("sph_cell_sort_noalloc: null grid argument");
         return SPH_EINVAL;
     }
+    static const char* too_big =
+        "sph_cell_sort_noalloc: n or the cell count exceeds the fixed scratch "
+        "(SPH_NOALLOC_MAX_N / SPH_NOALLOC_MAX_CELLS); use sph_cell_sort";
+    // the running product is checked after every factor, so it stays below
+    // kMaxCells * INT_MAX and never overflows
     int64_t nc = 1;
     for (int a = 0; a < 3; ++a) {
         if (ncell[a] < 1 || !(cellw[a] > 0)) {
@@ -65,11 +74,13 @@ extern "C" sph_status sph_cell_sort_noalloc(const double* pos, int64_t n, const 
             return SPH_EINVAL;
         }
         nc *= ncell[a];
+        if (nc > (int64_t)kMaxCells) {
+            sph::set_stateless_error(too_big);
+            return SPH_EINVAL;
+        }
     }
-    if (n > (int64_t)kMaxN || nc > (int64_t)kMaxCells) {
-        sph::set_stateless_error(
-            "sph_cell_sort_noalloc: n or the cell count exceeds the fixed scratch "
-            "(SPH_NOALLOC_MAX_N / SPH_NOALLOC_MAX_CELLS); use sph_cell_sort");
+    if (n > (int64_t)kMaxN) {
+        sph::set_stateless_error(too_big);
         return SPH_EINVAL;
     }
     if (n < 0 || (n > 0 && (!pos || !perm)) || !cell_start) {

@@ -33,7 +33,8 @@ class sph_config(C.Structure):
     _fields_ = [("origin", D * 3), ("extent", D * 3), ("dx", D), ("h_over_dx", D), ("gravity", D * 3),
                 ("c0", D), ("u_ref", D), ("cfl_ad", D), ("cfl_ac", D), ("free_surface", C.c_int),
                 ("periodic_mask", C.c_int), ("max_substeps", C.c_int), ("pair_precision", C.c_int),
-                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int), ("cfl_T", D)]
+                ("viscous_heating", C.c_int), ("vstar_literal", C.c_int), ("cfl_T", D),
+                ("wall_pstar_printed", C.c_int)]
 
 
 class sph_material(C.Structure):
@@ -181,6 +182,7 @@ def config_from_dict(cfg: dict) -> sph_config:
     c.viscous_heating = cfg.get("viscous_heating", 0)
     c.vstar_literal = cfg.get("vstar_literal", 0)
     c.cfl_T = cfg.get("cfl_T", 0.5)
+    c.wall_pstar_printed = cfg.get("wall_pstar_printed", 0)
     return c
 
 

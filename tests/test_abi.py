@@ -87,6 +87,12 @@ def test_create_validates_config(sphlib):
         with pytest.raises(sphlib.SphError) as e:
             sphlib.Context(dict(cfg, **bad), stream=0)
         assert e.value.status == sphlib.SPH_EINVAL
+    # Eq. (19) as printed: FP64 pairs only
+    sphlib.Context(dict(cfg, pair_precision=1, wall_pstar_printed=1), stream=0).close()
+    for bad in (dict(wall_pstar_printed=1), dict(pair_precision=1, wall_pstar_printed=-1)):
+        with pytest.raises(sphlib.SphError) as e:
+            sphlib.Context(dict(cfg, **bad), stream=0)
+        assert e.value.status == sphlib.SPH_EINVAL
 
 
 def test_add_validates_arguments(sphlib):
@@ -194,3 +200,18 @@ def test_empty_case_cannot_step(sphlib):
     assert e.value.status == sphlib.SPH_ESTATE
     assert ctx.sph_get_info()["n_fluid"] == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("fn", ["sph_cell_sort", "sph_cell_sort_noalloc"])
+def test_cell_sort_rejects_grids_whose_cell_count_overflows(sphlib, fn):
+    # three factors of 2^31 - 1 would overflow a 64-bit product; the count is
+    # checked after each factor, so the call returns SPH_EINVAL before any
+    # device work (n = 0 needs no positions; the output pointer is never used)
+    L = sphlib.lib()
+    f = getattr(L, fn)
+    big = (C.c_int * 3)(2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1)
+    o = (C.c_double * 3)(0.0, 0.0, 0.0)
+    w = (C.c_double * 3)(1.0, 1.0, 1.0)
+    rc = f(None, 0, o, w, big, None, C.c_void_p(16), None)
+    assert rc == sphlib.SPH_EINVAL
+    assert "cell" in L.sph_last_error(None).decode()

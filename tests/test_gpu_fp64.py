@@ -36,6 +36,16 @@ def _literal(case):
     return case
 
 
+def _eq15(case):
+    case.config = dict(case.config, free_surface=0)
+    return case
+
+
+def _wall_printed(case):
+    case.config = dict(case.config, wall_pstar_printed=1)
+    return case
+
+
 def _scales(case):
     cfg = case.config
     rho0 = max(m["rho0"] for m in case.materials.values())
@@ -44,17 +54,19 @@ def _scales(case):
                 T=max(max(Ts) - min(Ts), 1.0))
 
 
-def _errors(ctx, sim, case):
+def _errors(ctx, ref, case):
+    # ref: the oracle's fields after the same step (an OracleSim or a dict of arrays)
+    field = ref.field if hasattr(ref, "field") else ref.__getitem__
     f = W.flatten(case)
     sel = f["kind"] == 0
     rho0 = np.array([case.materials[m]["rho0"] for m in f["mat"]])
     sc = _scales(case)
     out = {}
     for k in ("pos", "vel", "T"):
-        g, r = ctx.sph_read_fields(k)[sel], sim.field(k)[sel]
+        g, r = ctx.sph_read_fields(k)[sel], field(k)[sel]
         out[k] = float(np.max(np.abs(g - r) / np.maximum(np.abs(r), sc[k])))
     g = ctx.sph_read_fields("rho")[sel] - rho0[sel]
-    r = sim.field("rho")[sel] - rho0[sel]
+    r = field("rho")[sel] - rho0[sel]
     out["drho_rel"] = float(np.max(np.abs(g - r) / np.maximum(np.abs(r), sc["drho_rel"])))
     return out
 
@@ -69,22 +81,31 @@ CASES = [
     ("two_fluid_box", lambda: W.two_fluid_box(), 3),
     # Eq. (13) with its printed sign (anti-diffusive; a short run)
     ("periodic_box_vstar_literal", lambda: _literal(W.periodic_box(n=12, rho_amp=1e-4)), 2),
+    # density re-initialisation by Eq. (15)
+    ("still_tank_small_eq15", lambda: _eq15(W.still_tank(nx=12, ny=12, nz=8, wall_h=12)), 3),
+    ("periodic_box_eq15", lambda: _eq15(W.periodic_box(n=12)), 3),
+    # Eq. (19) exactly as printed (no limiter term in the wall pressure)
+    ("still_tank_small_wall_printed", lambda: _wall_printed(W.still_tank(nx=12, ny=12, nz=8, wall_h=12)), 3),
+    ("gear_bath_5mm_wall_printed", lambda: _wall_printed(W.gear_bath(dx=5e-3, omega=600.0)), 2),
+    # the benchmarked geometry, the two-shaft train and the dam-break twin
+    ("gear_bath_5mm", lambda: W.gear_bath(dx=5e-3, omega=600.0), 3),
+    ("gear_pair", lambda: W.gear_pair(), 3),
+    ("dam_break_5mm", lambda: W.dam_break(dx=5e-3), 2),
 ]
 
 
 @pytest.mark.parametrize("name,make,steps", CASES, ids=[c[0] for c in CASES])
-def test_fp64_field_parity(sph, oracle, name, make, steps):
+def test_fp64_field_parity(sph, oracle_run, name, make, steps):
     case = _fp64(make())
     ctx = sph.from_case(case, stream=0)
-    sim = oracle.OracleSim(case)
+    ref = oracle_run(name, make(), steps)
     for k in range(steps):
         ctx.sph_step(1)
-        sim.step(1)
-        gi, oi = ctx.sph_get_info(), sim.time()
+        gi, oi = ctx.sph_get_info(), ref[k]["time"]
         assert gi["last_nsub"] == oi["nsub"]
         assert gi["t"] == pytest.approx(oi["t"], rel=1e-12)
-        err = _errors(ctx, sim, case)
-        print(name, k + 1, err)
+        err = _errors(ctx, ref[k], case)
+        print(f"FIELD_ERR64 {name} step={k + 1} " + " ".join(f"{f}={e:.2e}" for f, e in err.items()))
         # the printed sign of Eq. (13) is anti-diffusive: it amplifies the
         # rounding difference of the two summation orders (a density bump
         # grows ~40x per advection step, see the oracle pin), hence 100x

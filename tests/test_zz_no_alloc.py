@@ -25,20 +25,40 @@ def env():
     return torch, sph
 
 
-def _sort(torch, sph, fn, pos, origin, cellw, ncell):
+def _device_memory_in_use(torch):
+    """(bytes the driver reports in use on the device, bytes in use in the
+    device's default stream-ordered pool): a cudaMalloc or a
+    cudaMallocAsync inside the call would move one of them."""
+    from cuda.bindings import runtime as rt
+    free, total = torch.cuda.mem_get_info()
+    err, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    assert err == rt.cudaError_t.cudaSuccess
+    err, used = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    return total - free, int(used)
+
+
+def _sort(torch, sph, fn, pos, origin, cellw, ncell, check_noalloc=False):
     n = len(pos)
     d_pos = torch.tensor(pos, dtype=torch.float64, device="cuda")
     d_perm = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
     d_cs = torch.full((int(np.prod(ncell)) + 1,), -7, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    before = _device_memory_in_use(torch)
     fn(d_pos.data_ptr(), n, origin, cellw, ncell, d_perm.data_ptr(), d_cs.data_ptr(),
        torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+    if check_noalloc:
+        assert _device_memory_in_use(torch) == before
     return d_perm.cpu().numpy()[:n], d_cs.cpu().numpy()
 
 
 def test_noalloc_matches_allocating_sort_twice(env):
     torch, sph = env
     rng = np.random.default_rng(404)
+    # the first call on the device may load the library's module there (lazy
+    # loading), which places the fixed scratch array: take it before measuring
+    _sort(torch, sph, sph.sph_cell_sort_noalloc, np.zeros((1, 3)), np.zeros(3), np.ones(3), (1, 1, 1))
     # two different calls in a row: the second must not see the first's leftovers
     calls = [(300001, (64, 40, 30), 1.0), (120000, (17, 90, 11), 2.5)]
     for n, ncell, L in calls:
@@ -46,7 +66,7 @@ def test_noalloc_matches_allocating_sort_twice(env):
         origin = np.zeros(3)
         cellw = L / np.asarray(ncell, np.float64)
         ref = _sort(torch, sph, sph.sph_cell_sort, pos, origin, cellw, ncell)
-        got = _sort(torch, sph, sph.sph_cell_sort_noalloc, pos, origin, cellw, ncell)
+        got = _sort(torch, sph, sph.sph_cell_sort_noalloc, pos, origin, cellw, ncell, check_noalloc=True)
         assert np.array_equal(got[0], ref[0])
         assert np.array_equal(got[1], ref[1])
 
