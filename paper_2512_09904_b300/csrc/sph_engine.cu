@@ -462,6 +462,8 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     const double alpha = 21.0 / (16.0 * M_PI * h * h * h);
     C.kw = (float)alpha;
     C.kdw = (float)(-5.0 * alpha / h);
+    C.nhinv = (float)(-0.5 / h);
+    C.kdwh = (float)(-5.0 * alpha / (h * h));
     C.w0 = (float)alpha;
     C.inv_sigma0 = (float)(1.0 / c->sigma0);
     C.inv_contact_full = (float)(1.0 / (F.dx * F.dx * F.dx * (c->sigma0 - alpha)));
@@ -727,6 +729,8 @@ static PairConst pair_const(const CaseDev& C, const CaseDev* dev) {
     P.w0 = C.w0;
     P.kw = C.kw;
     P.kdw = C.kdw;
+    P.nhinv = C.nhinv;
+    P.kdwh = C.kdwh;
     P.inv_sigma0 = C.inv_sigma0;
     P.vol = C.vol;
     P.inv_contact_full = C.inv_contact_full;

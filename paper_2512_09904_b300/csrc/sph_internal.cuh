@@ -79,6 +79,7 @@ struct CaseDev {
     double R2;                    // (2h)^2 in FP64: the membership rule
     float R2lo, R2hi, R2eps;      // FP32 guard band around the rule
     float h, inv_h, w0, kw, kdw;  // W(0), alpha, -5 alpha / h
+    float nhinv, kdwh;            // -1 / (2h) and kdw / h: (dW/dr) / r = kdwh (1 - r / 2h)^3
     float inv_sigma0, vol;
     float inv_contact_full;  // 1 / (dx^3 (sigma0 - W(0))): the fully immersed kernel volume sum
     float c0, c02, inv_c0, inv_c02;
@@ -113,6 +114,7 @@ struct PairConst {
     float gcellwf[3], scellwf[3], inv_scellwf[3];
     float Rmargin, R2lo, R2hi, R2eps;
     float inv_h, w0, kw, kdw, inv_sigma0, vol, inv_contact_full;
+    float nhinv, kdwh;
     float c0, c02, inv_c0, inv_c02;
     float g[3];
     int ncell[3];
@@ -171,6 +173,15 @@ __device__ __forceinline__ float kernel_dW(const CC& C, float r) {
     return C.kdw * q * t * t * t;
 }
 
+// (dW/dr) / r as a function of r: (5 alpha / h) q (1 - q/2)^3 / r with
+// q / r = 1 / h, so kdwh (1 - r / 2h)^3, kdwh = kdw / h.  The pair passes
+// need dW/dr only times the unit vector r_ij / r, i.e. this times r_ij.
+template <class CC>
+__device__ __forceinline__ float kernel_dW_over_r(const CC& C, float r) {
+    const float t = fmaf(C.nhinv, r, 1.0f);
+    return C.kdwh * (t * t) * t;
+}
+
 __device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, float by, float bz) {
     return fmaf(az, bz, fmaf(ay, by, ax * bx));
 }
@@ -178,10 +189,12 @@ __device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, f
 // Exact pair-membership rule on the FP64 snapshot: 0 < r^2 < R2 with
 // r^2 = ((dx*dx + dy*dy) + dz*dz) in round-to-nearest, no contraction, and
 // the minimum image on periodic axes.  Cg is the case in the global case
-// table (never a copy in a kernel's parameter block: the call is not inlined).
-static __device__ __noinline__ bool member_fp64(const CaseDev* __restrict__ Cg, const double* __restrict__ Yx,
-                                                const double* __restrict__ Yy, const double* __restrict__ Yz,
-                                                int i, int j) {
+// table (the periodic box and R2 are read from there only on this rare
+// path).  Inlined: as an out-of-line call its register save made the
+// search loop of pass D spill.
+static __device__ __forceinline__ bool member_fp64(const CaseDev* __restrict__ Cg, const double* __restrict__ Yx,
+                                                   const double* __restrict__ Yy, const double* __restrict__ Yz,
+                                                   int i, int j) {
     const CaseDev& C = *Cg;
     double d[3] = {__dsub_rn(Yx[i], Yx[j]), __dsub_rn(Yy[i], Yy[j]), __dsub_rn(Yz[i], Yz[j])};
 #pragma unroll

@@ -771,7 +771,7 @@ __device__ __forceinline__ void d_particle(const Bufs& B, int par, int i, float4
 }
 
 template <int CM>
-__global__ void __launch_bounds__(256, 5) k_passD(Bufs B, int par, const PairArg<CM> T) {
+__global__ void __launch_bounds__(256, 4) k_passD(Bufs B, int par, const PairArg<CM> T) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B.n) return;
     const float4 si = B.SNAP[i];
@@ -832,31 +832,29 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
         };
         const float Kii = 2.f * harmonic2(Mf.k, Mf.k), eii = harmonic2(Mf.mu, Mf.mu);
         vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
-            const float inv_r = rsqrtf(r2);
-            const float dW = kernel_dW(C, r2 * inv_r);
+            const float s = kernel_dW_over_r(C, r2 * rsqrtf(r2));  // dW/dr / r
             const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
             const float4 vj = __ldg(V + j);
-            const float Vj = __fdividef(Mj.mass, Mj.rho0 + vj.w);
-            const float cv = 2.f * Vj * (UNI ? eii : harmonic2(Mf.mu, Mj.mu)) * inv_r * dW;
+            const float Vs = __fdividef(Mj.mass, Mj.rho0 + vj.w) * s;  // V_j dW/dr / r
+            const float cv = 2.f * (UNI ? eii : harmonic2(Mf.mu, Mj.mu)) * Vs;
             ax = fmaf(cv, vi.x - vj.x, ax);
             ay = fmaf(cv, vi.y - vj.y, ay);
             az = fmaf(cv, vi.z - vj.z, az);
             const float K = UNI ? Kii : 2.f * harmonic2(Mf.k, Mj.k);
-            dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
-            if (VH && vh) grad(Vj * dW * inv_r, vj, rx, ry, rz);
+            dT = fmaf(K * (Ti - __ldg(T32 + j)), Vs, dT);
+            if (VH && vh) grad(Vs, vj, rx, ry, rz);
         });
         vis.template run<PART_WALL>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
-            const float inv_r = rsqrtf(r2);
-            const float dW = kernel_dW(C, r2 * inv_r);
+            const float Vs = C.vol * kernel_dW_over_r(C, r2 * rsqrtf(r2));  // V_w dW/dr / r
             const MatDev& Mj = C.mat[tag_mat(__float_as_uint(sj.w))];
             const float4 vw = __ldg(V + j);
-            const float cv = 2.f * C.vol * Mf.mu * inv_r * dW;  // the wall takes the fluid's viscosity
+            const float cv = 2.f * Mf.mu * Vs;  // the wall takes the fluid's viscosity
             ax = fmaf(cv, vi.x - vw.x, ax);
             ay = fmaf(cv, vi.y - vw.y, ay);
             az = fmaf(cv, vi.z - vw.z, az);
             const float K = 2.f * harmonic2(Mf.k, Mj.k);
-            dT = fmaf(C.vol * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
-            if (VH && vh) grad(C.vol * dW * inv_r, vw, rx, ry, rz);
+            dT = fmaf(K * (Ti - __ldg(T32 + j)), Vs, dT);
+            if (VH && vh) grad(Vs, vw, rx, ry, rz);
         });
         if (VH && vh) {
             // r_ij = r_i - r_j and grad_i W = W' r_ij / r, so the sums above carry
@@ -888,8 +886,8 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
     const float4 vw = V[i];
     float dT = 0.f, fx = 0.f, fy = 0.f, fz = 0.f, cf = 0.f;
     vis.template run<PART_ALL>([&](int j, float4 sj, float, float, float, float r2) {
-        const float inv_r = rsqrtf(r2);
-        const float dW = kernel_dW(C, r2 * inv_r);
+        const float r = r2 * rsqrtf(r2);
+        const float s = kernel_dW_over_r(C, r);  // dW/dr / r
         const uint32_t tj = __float_as_uint(sj.w);
         const MatDev& Mj = C.mat[tag_mat(tj)];
         const bool fj = tag_kind(tj) == KIND_FLUID;
@@ -903,17 +901,17 @@ __device__ __forceinline__ void vt_particle(const Bufs& B, int par, int i, float
         }
         if (thermal) {
             const float K = 2.f * harmonic2(Mi.k, Mj.k);
-            dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)) * inv_r, dW, dT);
+            dT = fmaf(Vj * K * (Ti - __ldg(T32 + j)), s, dT);
         }
         if (rot && fj) {
             // force of fluid j on this wall particle: -m_j a_jw, with
             // a_jw = 2 V_w / rho_j mu_j (v_j - v_w) / r dW/dr
-            const float c = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * Mj.mu * inv_r * dW;
+            const float c = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * Mj.mu * s;
             fx = fmaf(c, vj.x - vw.x, fx);
             fy = fmaf(c, vj.y - vw.y, fy);
             fz = fmaf(c, vj.z - vw.z, fz);
             // contact factor (Eq. 24): lubricant volume weighted by W
-            cf = fmaf(Vj, kernel_W(C, r2 * inv_r), cf);
+            cf = fmaf(Vj, kernel_W(C, r), cf);
         }
     });
     dT = vis.sum(dT);
@@ -997,23 +995,25 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         float ax = 0.f, ay = 0.f, az = 0.f;
         vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
             const float inv_r = rsqrtf(r2);
-            const float dW = kernel_dW(C, r2 * inv_r);
+            const float s = kernel_dW_over_r(C, r2 * inv_r);  // dW/dr / r
             const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
             const float4 vj = __ldg(VH + j);
             const float rho_j = Mj.rho0 + vj.w;
             // U_L - U_R = -(v_i - v_j).e_ij
             const float dU = -inv_r * dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz);
             const float beta = fminf(3.f * fmaxf(dU, 0.f), C.c0);
-            // p_i + p_j with p_j = c0^2 (rho_j - rho0) fused
-            const float pstar = fmaf(0.5f, fmaf(C.c02, vj.w, p_i), __fdividef(rho_i * rho_j * beta * dU, rho_i + rho_j));
-            const float coef = __fdividef(Mj.mass, rho_j) * pstar * dW * inv_r;
+            // V_j p* with V_j = m_j / rho_j and p* = (p_i + p_j)/2 + rho_i rho_j
+            // beta dU / (rho_i + rho_j), over the one reciprocal of
+            // rho_j (rho_i + rho_j); p_i + p_j with p_j = c0^2 (rho_j - rho0) fused
+            const float srho = rho_i + rho_j;
+            const float num = fmaf(rho_i * rho_j, beta * dU, 0.5f * fmaf(C.c02, vj.w, p_i) * srho);
+            const float coef = __fdividef(Mj.mass * num, rho_j * srho) * s;
             ax = fmaf(coef, rx, ax);
             ay = fmaf(coef, ry, ay);
             az = fmaf(coef, rz, az);
         });
         vis.template run<PART_WALL>([&](int j, float4, float rx, float ry, float rz, float r2) {
-            const float inv_r = rsqrtf(r2);
-            const float dW = kernel_dW(C, r2 * inv_r);
+            const float s = kernel_dW_over_r(C, r2 * rsqrtf(r2));  // dW/dr / r
             // one-sided wall problem: P_R = p_f + rho_f g.r_fw, r_fw = -r_ij;
             // U_L - U_R = 2 (U_L - u_w) = -2 n.(v_f - v_w)
             const float4 nw = __ldg(B.NRM + j);
@@ -1024,7 +1024,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
             const float dUw = -2.f * dot3f(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z);
             const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
             const float pstar = __fdividef(fmaf(rho_i * rhoR * beta, dUw, fmaf(rho_i, PR, rhoR * p_i)), rho_i + rhoR);
-            const float coef = C.vol * pstar * dW * inv_r;
+            const float coef = C.vol * pstar * s;
             ax = fmaf(coef, rx, ax);
             ay = fmaf(coef, ry, ay);
             az = fmaf(coef, rz, az);
@@ -1063,8 +1063,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
     const float4 nwi = B.NRM[i];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
-        const float inv_r = rsqrtf(r2);
-        const float dW = kernel_dW(C, r2 * inv_r);
+        const float s = kernel_dW_over_r(C, r2 * rsqrtf(r2));  // dW/dr / r
         const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
         const float4 vj = __ldg(VH + j);
         const float rho_j = Mj.rho0 + vj.w;
@@ -1077,7 +1076,7 @@ __device__ __forceinline__ void m_particle(const Bufs& B, int par, int first, in
         const float beta = fminf(3.f * fmaxf(dUw, 0.f), C.c0);
         const float pstar = __fdividef(fmaf(rho_j * rhoR * beta, dUw, fmaf(rho_j, PR, rhoR * p_j)), rho_j + rhoR);
         // a_jw = -2 V_w / rho_j p* dW e_jw with e_jw = -r_ij / r; force on wall = -m_j a_jw
-        const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * pstar * dW * inv_r;
+        const float cf = -Mj.mass * __fdividef(2.f * C.vol, rho_j) * pstar * s;
         fx = fmaf(cf, rx, fx);
         fy = fmaf(cf, ry, fy);
         fz = fmaf(cf, rz, fz);
@@ -1151,20 +1150,21 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
     const float rho_i = Mi.rho0 + vi.w;
     float d = 0.f;
     vis.template run<PART_FLUID>([&](int j, float4 sj, float rx, float ry, float rz, float r2) {
-        const float inv_r = rsqrtf(r2);
-        const float dW = kernel_dW(C, r2 * inv_r);
+        const float r = r2 * rsqrtf(r2);
+        const float s = kernel_dW_over_r(C, r);  // dW/dr / r
         const MatDev& Mj = fluid_mat<UNI>(C, __float_as_uint(sj.w));
         const float4 vj = __ldg(Vin + j);
         const float rho_j = Mj.rho0 + vj.w;
-        // U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)), with
-        // U_R - U_L = (v_i - v_j).e and p_i - p_j = c0^2 (drho_i - drho_j)
-        const float du = fmaf(0.5f * inv_r, dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz),
-                              __fdividef(C.c0 * (vi.w - vj.w), rho_i + rho_j));
-        d = fmaf(__fdividef(Mj.mass, rho_j) * du, dW, d);
+        const float srho = rho_i + rho_j;
+        // V_j (U* - U_L) dW/dr with U* - U_L = (U_R - U_L)/2 + (p_i - p_j) / (c0 (rho_i + rho_j)),
+        // U_R - U_L = (v_i - v_j).e, p_i - p_j = c0^2 (drho_i - drho_j) and V_j = m_j / rho_j:
+        // m_j s ((v_i - v_j).r_ij (rho_i + rho_j) / 2 + c0 (drho_i - drho_j) r) / (rho_j (rho_i + rho_j))
+        const float num = fmaf(0.5f * srho, dot3f(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, rx, ry, rz),
+                               C.c0 * (vi.w - vj.w) * r);
+        d = fmaf(__fdividef(Mj.mass * num, rho_j * srho), s, d);
     });
     vis.template run<PART_WALL>([&](int j, float4, float rx, float ry, float rz, float r2) {
-        const float inv_r = rsqrtf(r2);
-        const float dW = kernel_dW(C, r2 * inv_r);
+        const float s = kernel_dW_over_r(C, r2 * rsqrtf(r2));  // dW/dr / r
         const float4 nw = __ldg(B.NRM + j);
         const float4 vw = __ldg(Vin + j);
         const float g_rfw = -dot3f(C.g[0], C.g[1], C.g[2], rx, ry, rz);
@@ -1173,7 +1173,7 @@ __device__ __forceinline__ void c_particle(const Bufs& B, int par, int i, float4
         // U*_w - U_L = n.(v_f - v_w) + (p_f - P_R) / (c0 (rho_f + rho_R))
         const float du = dot3f(nw.x, nw.y, nw.z, vi.x - vw.x, vi.y - vw.y, vi.z - vw.z) -
                          __fdividef(rho_i * g_rfw * C.inv_c0, rho_i + rhoR);
-        d = fmaf(C.vol * du * dot3f(nw.x, nw.y, nw.z, rx, ry, rz) * inv_r, dW, d);
+        d = fmaf(C.vol * du * dot3f(nw.x, nw.y, nw.z, rx, ry, rz), s, d);
     });
     d = vis.sum(d);
     if (!vis.lead()) return;
