@@ -625,24 +625,29 @@ __device__ __forceinline__ void list_walk(const CC& C, const Bufs& B, int i, flo
     const uint32_t* __restrict__ nb = B.NB + (size_t)k0 * stride + i;
     const ptrdiff_t step = ks * (ptrdiff_t)stride;
     const float sx = si.x + C.gcellwf[0], sy = si.y + C.gcellwf[1], sz = si.z + C.gcellwf[2];
+    // list entries one batch ahead of their use: the next batch's loads are
+    // in flight while the current batch's partners are gathered and summed
+    uint32_t e[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) e[u] = (sub + TPP * u < cnt) ? __ldg(nb + (sub + TPP * u) * step) : 0u;
     for (int q0 = sub; q0 < cnt; q0 += TPP * BATCH) {
-        // the next batch's list entries (they stream from DRAM) into L2 while
-        // this batch is worked on; longer distances measured slower
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int q = q0 + TPP * (2 * BATCH + u);
+            if (q < cnt) asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + q * step));
+        }
+        uint32_t en[BATCH];
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             const int q = q0 + TPP * (BATCH + u);
-            if (q < cnt) asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + q * step));
+            en[u] = q < cnt ? __ldg(nb + q * step) : 0u;
         }
-        uint32_t e[BATCH];
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u) e[u] = (q0 + TPP * u < cnt) ? __ldg(nb + (q0 + TPP * u) * step) : 0u;
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             if (q0 + TPP * u < cnt) {
                 const int j = (int)(e[u] & NB_JMASK);
                 const uint32_t d = e[u] >> 26;
                 const float4 sj = __ldg(B.SNAP + j);
-                // r_ij = off_i - off_j - dc w with dc = field - 1
                 const float rx = fmaf(-(float)(d & 3u), C.gcellwf[0], sx) - sj.x;
                 const float ry = fmaf(-(float)((d >> 2) & 3u), C.gcellwf[1], sy) - sj.y;
                 const float rz = fmaf(-(float)(d >> 4), C.gcellwf[2], sz) - sj.z;
@@ -650,6 +655,8 @@ __device__ __forceinline__ void list_walk(const CC& C, const Bufs& B, int i, flo
                 f(j, sj, rx, ry, rz, r2);
             }
         }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) e[u] = en[u];
     }
 }
 
