@@ -317,6 +317,19 @@ def gear_pair(dx=2.5e-3, omega=300.0, depth_frac=0.5, mu=0.1, seed=13, jitter=0.
                 dict(omega=omega, omega2=omega2, dx=dx, z_fill=z_fill, seed=seed))
 
 
+def perturbed(case, seed, amp=1e-9):
+    """The case with every fluid position moved by a seeded normal offset of
+    standard deviation amp x dx per coordinate (far below FP32 rounding of the
+    pair geometry at the default): a sibling trajectory for measuring how
+    fast a splashing flow forgets its initial state."""
+    rng = np.random.default_rng(seed)
+    sd = amp * case.config["dx"]
+    for f in case.fluids:
+        f["pos"] = f["pos"] + rng.normal(0.0, sd, size=f["pos"].shape)
+    case.meta = dict(case.meta, perturb_seed=seed, perturb_amp=amp)
+    return case
+
+
 def gear_bath_dx_for(n_fluid_target, depth_frac=0.5, scale=1.5):
     """Lattice spacing that gives about n_fluid_target oil particles."""
     r_p, b = GEAR["r_pitch"], GEAR["face"]

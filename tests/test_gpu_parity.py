@@ -358,6 +358,9 @@ GOLDEN_GEAR = "gear_bath_5mm_1000.json"
 
 
 def _stored_gear(sph, pair_precision):
+    """The stored FP64 oracle run of the gear bath at dx = 5 mm (per-step
+    columns after each of 1000 advection steps) and a context of the same
+    case in the given pair precision."""
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", GOLDEN_GEAR)
@@ -365,44 +368,105 @@ def _stored_gear(sph, pair_precision):
     case = W.gear_bath(dx=ref["dx"], omega=ref["omega"])
     assert (case.n_fluid, case.n_solid) == (ref["n_fluid"], ref["n_solid"])
     case.config = dict(case.config, pair_precision=pair_precision)
-    return ref, sph.from_case(case, stream=0)
+    cols = {k: np.asarray(v, np.float64) for k, v in ref["per_step"].items()}
+    return ref, cols, sph.from_case(case, stream=0)
 
 
 def test_gear_bath_5mm_1000_steps_fp64_against_stored_oracle(sph):
     # the 2M workload's geometry at dx = 5 mm (17.5k oil + 27k solid): the
     # stored FP64 oracle run (tests/golden/make_gear_bath_5mm.py) against the
-    # FP64 pair mode over 1000 advection steps, every 100 steps.  The splash is
-    # chaotic, but in FP64 the two sides stay within round-off growth.
-    ref, ctx = _stored_gear(sph, 1)
-    for rec in ref["records"]:
-        ctx.sph_step(rec["steps"] - ctx.sph_get_info()["adv_steps"])
-        gi, g = ctx.sph_get_info(), ctx.sph_read_torque_heat(0)
-        print(rec["steps"], gi["t"], rec["t"], g["torque_avg"], rec["torque_avg"], g["heat"], rec["heat"])
-        assert gi["t"] == pytest.approx(rec["t"], rel=1e-6)
-        assert g["torque_avg"] == pytest.approx(rec["torque_avg"], rel=1e-4)
-        assert g["heat"] == pytest.approx(rec["heat"], rel=1e-4)
-        assert g["mean_T"] == pytest.approx(rec["mean_T"], abs=1e-8)
+    # FP64 pair mode over 1000 advection steps, every step.  The splash is
+    # chaotic, but in FP64 the two sides stay within round-off growth
+    # (measured: clock 6e-8, torque average 7e-6, heat 2e-5).
+    ref, P, ctx = _stored_gear(sph, 1)
+    ctx.sph_step(ref["steps"])
+    g = ctx.sph_read_curve(ref["steps"])
     ctx.close()
+    assert g.shape[0] == ref["steps"]
+    assert np.array_equal(np.cumsum(g[:, 6]), P["substeps"])
+    assert np.max(np.abs(g[:, 0] - P["t"]) / P["t"]) <= 1e-6
+    assert np.max(np.abs(g[:, 2] - P["torque_avg"]) / np.abs(P["torque_avg"])) <= 1e-4
+    assert np.max(np.abs(g[:, 1] - P["torque"])) <= 1e-4 * np.abs(P["torque"]).max()
+    assert np.max(np.abs(g[:, 3] - P["heat"]) / P["heat"]) <= 1e-4
+    assert np.max(np.abs(g[:, 4] - P["mean_T"])) <= 1e-8
+
+
+def _at_equal_time(curve_t, torque_avg, heat, mean_T, ta, tb):
+    """Torque averaged over [0, tb] and over [ta, tb], heat-up and mean
+    temperature at tb, from per-step records (running integrals linear
+    between steps)."""
+    integral = torque_avg * curve_t
+    i_a, i_b = np.interp(ta, curve_t, integral), np.interp(tb, curve_t, integral)
+    return dict(torque_avg=i_b / tb, torque_window=(i_b - i_a) / (tb - ta),
+                heat=float(np.interp(tb, curve_t, heat)), mean_T=float(np.interp(tb, curve_t, mean_T)))
 
 
 def test_gear_bath_5mm_fp32_against_stored_oracle(sph):
-    # the FP32 pair path on the same case: within 1e-3 of the FP64 oracle over
-    # the first 100 advection steps; later the splash parts the FP32 and FP64
-    # trajectories chaotically (the step follows the fastest particle), so at
-    # 1000 steps only what every valid trajectory shares is checked: the drag
-    # opposes the rotation and the hot gear has heated the oil
-    ref, ctx = _stored_gear(sph, 0)
-    first, last = ref["records"][0], ref["records"][-1]
-    ctx.sph_step(first["steps"])
-    gi, g = ctx.sph_get_info(), ctx.sph_read_torque_heat(0)
-    assert gi["t"] == pytest.approx(first["t"], rel=1e-3)
-    assert g["torque_avg"] == pytest.approx(first["torque_avg"], rel=1e-3)
-    assert g["heat"] / gi["t"] == pytest.approx(first["heat"] / first["t"], rel=1e-3)
-    ctx.sph_step(last["steps"] - first["steps"])
-    g = ctx.sph_read_torque_heat(0)
-    assert g["torque_avg"] * ref["omega"] < 0 and last["torque_avg"] * ref["omega"] < 0
-    assert g["heat"] > 0 and last["heat"] > 0
+    """The FP32 pair path against the stored FP64 oracle run over 1000 steps.
+
+    For the first 100 steps the two agree step by step (measured 1e-5).
+    Then the splash is chaotic: the impulsively started gear flings oil at
+    up to ~c0, the step size follows the fastest particle (Eq. 25), and any
+    perturbation grows.  Moving the oil by 1e-9 dx (far below FP32 rounding)
+    and rerunning the FP64 method moves the results after 1000 steps as much
+    as FP32 arithmetic does (test_gear_bath_5mm_is_chaotic below).  The
+    results are therefore compared at equal simulated time, the end of the
+    shorter run, with bounds set by that spread.  Measured for FP32 against
+    the oracle: torque averaged from the start 4.3e-2, heat-up and mean
+    temperature rise 9.6e-2; FP32 runs of four perturbed siblings reached
+    5.7e-2 and 1.0e-1, FP64 ones 2.4e-2 and 6.0e-2.  The torque averaged
+    after the first revolution is reported, not bounded (FP64 siblings
+    already spread 15-25% in it), beyond its sign."""
+    ref, P, ctx = _stored_gear(sph, 0)
+    omega = ref["omega"]
+    ctx.sph_step(ref["steps"])
+    g = ctx.sph_read_curve(ref["steps"])
     ctx.close()
+    k = 99
+    assert g[k, 0] == pytest.approx(P["t"][k], rel=1e-3)
+    assert g[k, 2] == pytest.approx(P["torque_avg"][k], rel=1e-3)
+    assert g[k, 3] / g[k, 0] == pytest.approx(P["heat"][k] / P["t"][k], rel=1e-3)
+    ta, tb = 2.0 * np.pi / abs(omega), min(g[-1, 0], P["t"][-1])
+    assert tb > 2.0 * ta
+    G = _at_equal_time(g[:, 0], g[:, 2], g[:, 3], g[:, 4], ta, tb)
+    O = _at_equal_time(P["t"], P["torque_avg"], P["heat"], P["mean_T"], ta, tb)
+    T0 = W.gear_bath(dx=ref["dx"], omega=omega).materials[0]["T_init"]
+    err = dict(torque_avg=abs(G["torque_avg"] - O["torque_avg"]) / abs(O["torque_avg"]),
+               torque_window=abs(G["torque_window"] - O["torque_window"]) / abs(O["torque_window"]),
+               heat=abs(G["heat"] - O["heat"]) / O["heat"],
+               mean_T_rise=abs(G["mean_T"] - O["mean_T"]) / (O["mean_T"] - T0))
+    print(f"FP32_LONGRUN t = {tb:.5f} s: " + " ".join(f"{q}={e:.2e}" for q, e in err.items()))
+    assert G["torque_window"] * omega < 0 and O["torque_window"] * omega < 0  # drag opposes rotation
+    assert err["torque_avg"] <= 1e-1
+    assert err["heat"] <= 2e-1 and err["mean_T_rise"] <= 2e-1
+
+
+@pytest.mark.slow
+def test_gear_bath_5mm_is_chaotic(sph):
+    # two FP64 runs of the same gear bath whose oil differs by 1e-9 dx in
+    # position part after the start-up splash: their clocks, heat-up and
+    # post-start-up torque after 1000 steps differ by far more than 1e-3,
+    # so no precision can hold a single trajectory to 1e-3 there; the FP64
+    # mode's agreement with the oracle (above) is the round-off check
+    runs = []
+    for seed in (None, 1):
+        case = W.gear_bath(dx=5e-3, omega=600.0)
+        if seed is not None:
+            W.perturbed(case, seed)
+        case.config = dict(case.config, pair_precision=1)
+        ctx = sph.from_case(case, stream=0)
+        ctx.sph_step(1000)
+        runs.append(ctx.sph_read_curve(1000))
+        ctx.close()
+    a, b = runs
+    ta, tb = 2.0 * np.pi / 600.0, min(a[-1, 0], b[-1, 0])
+    A = _at_equal_time(a[:, 0], a[:, 2], a[:, 3], a[:, 4], ta, tb)
+    Bq = _at_equal_time(b[:, 0], b[:, 2], b[:, 3], b[:, 4], ta, tb)
+    # the first 100 steps still agree closely; the end does not
+    assert b[99, 2] == pytest.approx(a[99, 2], rel=1e-3)
+    print("chaos", A, Bq)
+    assert abs(Bq["torque_window"] - A["torque_window"]) > 1e-2 * abs(A["torque_window"])
+    assert abs(Bq["heat"] - A["heat"]) > 3e-3 * A["heat"]
 
 
 def test_list_overflow_is_reported(sph):
