@@ -435,7 +435,7 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
         C.ext[a] = F.extent[a];
         C.cellw[a] = c->cellw[a];
         C.inv_cellw[a] = 1.0 / c->cellw[a];
-        C.gcellw[a] = 2.0 * c->cellw[a];
+        C.gcellw[a] = split_of(a) * c->cellw[a];
         C.gcellwf[a] = (float)C.gcellw[a];
         C.scellwf[a] = (float)c->cellw[a];
         C.inv_scellwf[a] = (float)(1.0 / c->cellw[a]);
@@ -446,10 +446,10 @@ static void build_case(const sph_ctx* c, const HostCase& H, CaseDev& C) {
     C.cell_base = (int)H.cell_base;
     C.ncells = c->ncell[0] * c->ncell[1] * c->ncell[2];
     C.gcorner_ok = 1;
-    for (int a = 0; a < 3; ++a) C.gcorner_ok &= (c->ncell[a] / 2 <= GCORNER_MAX) ? 1 : 0;
+    for (int a = 0; a < 3; ++a) C.gcorner_ok &= (c->ncell[a] / split_of(a) <= GCORNER_MAX) ? 1 : 0;
     if (C.gcorner_ok)
         for (int a = 0; a < 3; ++a)
-            for (int g = 0; g < c->ncell[a] / 2; ++g) C.gcorner[a][g] = C.origin[a] + (double)g * C.gcellw[a];
+            for (int g = 0; g < c->ncell[a] / split_of(a); ++g) C.gcorner[a][g] = C.origin[a] + (double)g * C.gcellw[a];
     C.periodic = F.periodic_mask;
     C.R2 = R2;
     // FP32 guard band around the cut-off: inside it the FP64 rule decides
@@ -1080,16 +1080,17 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
             delete c;
             return SPH_EINVAL;
         }
-        // geometry cells of width >= 2h, each cut into 2 sort cells of width >= h
+        // geometry cells of width >= 2h, each cut into split_of(a) sort cells
+        // (4 of width >= h/2 along x, 2 of width >= h along y and z)
         int64_t n = (int64_t)std::floor(cfg->extent[a] / R);
         if (n < 1) n = 1;
         if ((cfg->periodic_mask & (1 << a)) && n < 3) {
             delete c;
             return SPH_EINVAL;
         }
-        c->ncell[a] = (int)(2 * n);
-        c->cellw[a] = cfg->extent[a] / (double)(2 * n);
-        total *= 2 * n;
+        c->ncell[a] = (int)(split_of(a) * n);
+        c->cellw[a] = cfg->extent[a] / (double)(split_of(a) * n);
+        total *= split_of(a) * n;
     }
     if (total > (int64_t)1 << 30) {
         delete c;

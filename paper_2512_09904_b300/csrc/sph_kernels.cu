@@ -524,16 +524,18 @@ __global__ void k_reorder(Bufs B, int par) {
         B.Y[1][d] = p[1];
         B.Y[2][d] = p[2];
         int cl = (int)key - C.cell_base;
-        // offsets from the corner of the geometry cell (two sort cells per axis)
-        int cc[3] = {cl % C.ncell[0], (cl / C.ncell[0]) % C.ncell[1], cl / (C.ncell[0] * C.ncell[1])};
+        // offsets from the corner of the geometry cell (SPLIT_X x 2 x 2 sort cells);
+        // cc: the geometry cell per axis
+        int cc[3] = {(cl % C.ncell[0]) / SPLIT_X, ((cl / C.ncell[0]) % C.ncell[1]) >> 1,
+                     (cl / (C.ncell[0] * C.ncell[1])) >> 1};
         float off[3];
         if (C.gcorner_ok) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) off[a] = f64_to_f32_rn(p[a] - C.gcorner[a][cc[a] >> 1]);
+            for (int a = 0; a < 3; ++a) off[a] = f64_to_f32_rn(p[a] - C.gcorner[a][cc[a]]);
         } else {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                off[a] = f64_to_f32_rn((p[a] - C.origin[a]) - u32_to_f64((uint32_t)(cc[a] >> 1)) * C.gcellw[a]);
+                off[a] = f64_to_f32_rn((p[a] - C.origin[a]) - u32_to_f64((uint32_t)cc[a]) * C.gcellw[a]);
         }
         B.SNAP[d] = make_float4(off[0], off[1], off[2], __uint_as_float(tag));
         B.CELLK[d] = key;

@@ -507,10 +507,14 @@ def sph_relax(pos, dx, h_over_dx, phi, phi_origin, phi_spacing, iterations, stre
     return pos, amax[:iterations]
 
 
+# sort cells per geometry cell (width >= 2h) along x, y and z
+SORT_SPLIT = (4, 2, 2)
+
+
 def cells_of(case):
-    """Sort cells of a case (2 per geometry cell of width >= 2h per axis), for batch sizing."""
+    """Sort cells of a case (SORT_SPLIT per geometry cell of width >= 2h), for batch sizing."""
     R = case.support_radius()
     n = 1
-    for e in case.config["extent"]:
-        n *= 2 * max(1, int(np.floor(e / R)))
+    for e, k in zip(case.config["extent"], SORT_SPLIT):
+        n *= k * max(1, int(np.floor(e / R)))
     return n

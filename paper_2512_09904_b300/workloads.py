@@ -533,26 +533,29 @@ def cutoff_pairs(n_random=2000, n_pairs=400, dx=1e-3, h_over_dx=1.3, box=24, see
 
 def cell_boundaries(n_random=3000, n_edge=3000, dx=1e-3, h_over_dx=1.3, box=24,
                     origin=(-0.0123, 0.0456, 1.0), seed=12):
-    """Particles on sort-cell boundaries: one coordinate at origin + k w
-    (FP64, w the engine's sort-cell width extent / (2 floor(extent / 2h)))
-    or a few ulps either side, the others uniform; plus uniform particles.
-    The cell hash's FP32 estimate must hand every such particle to its FP64
+    """Particles on sort-cell boundaries: one coordinate at origin + k w_a
+    (FP64, w_a the engine's sort-cell width along axis a, extent /
+    (s_a floor(extent / 2h)) with s = 4 along x and 2 along y and z) or a
+    few ulps either side, the others uniform; plus uniform particles.  The
+    cell hash's FP32 estimate must hand every such particle to its FP64
     rule.  The origin is away from zero so that |o| enters the estimate's
     error."""
     rng = np.random.default_rng(seed)
     L = box * dx
     o = np.asarray(origin, np.float64)
-    n2 = 2 * int(np.floor(L / (2.0 * h_over_dx * dx)))
-    w = L / n2
+    ng = int(np.floor(L / (2.0 * h_over_dx * dx)))
+    ns = [s * ng for s in (4, 2, 2)]
+    w = [L / n for n in ns]
     lo, hi = o + 1e-3 * L, o + (1.0 - 1e-3) * L
     pts = [rng.uniform(lo, hi, size=(n_random, 3))]
     e = rng.uniform(lo, hi, size=(n_edge, 3))
     axis = rng.integers(0, 3, size=n_edge)
-    k = rng.integers(1, n2, size=n_edge).astype(np.float64)
+    u = rng.random(n_edge)
     ulps = rng.integers(-2, 3, size=n_edge)
     for i in range(n_edge):
         a = axis[i]
-        x = o[a] + k[i] * w
+        k = float(1 + int(u[i] * (ns[a] - 1)))  # 1 .. ns[a] - 1
+        x = o[a] + k * w[a]
         for _ in range(abs(int(ulps[i]))):
             x = np.nextafter(x, np.inf if ulps[i] > 0 else -np.inf)
         e[i, a] = x

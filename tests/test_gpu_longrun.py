@@ -43,12 +43,18 @@ def _run(sph, oracle, case, steps, chunk):
 
 
 def test_rotating_cylinder_1000_steps(sph, oracle):
-    # a heated cylinder (320 K) spinning at 50 rad/s in 300 K oil, periodic box
+    # a heated cylinder (320 K) spinning at 50 rad/s in 300 K oil, periodic
+    # box.  The flow is not chaotic (the clocks agree to 1e-6), but the drag
+    # torque is a small residual: the wall pressure forces are nearly normal
+    # to the cylinder and cancel in the torque, so FP32 rounding of the pair
+    # forces (relative 1e-7) reaches the time-averaged torque at 1e-3 (9e-4
+    # and 1.5e-3 measured for two orders of the pair sums).  The heat-up has
+    # no such cancellation.
     gi, oi, g, r = _run(sph, oracle, W.rotating_cylinder(), 1000, 100)
     print("cylinder", gi["t"], oi["t"], g, r)
     assert gi["adv_steps"] == oi["adv_steps"] == 1000
     assert gi["t"] == pytest.approx(oi["t"], rel=1e-6)
-    assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=1e-3)
+    assert g["torque_avg"] == pytest.approx(r["torque_avg"], rel=3e-3)
     assert g["heat"] == pytest.approx(r["heat"], rel=1e-3)
 
 

@@ -81,7 +81,7 @@ def test_cell_boundaries_order_and_pairs_bit_exact(sph, oracle):
     case = W.cell_boundaries()
     ctx = _ctx(sph, case, steps=1)
     info = ctx.sph_get_info()
-    assert info["cell_width"][0] == case.meta["sort_cell_width"]
+    assert list(info["cell_width"]) == list(case.meta["sort_cell_width"])
     perm = ctx.sph_read_cell_order()
     f = W.flatten(case)
     ref, _ = oracle.cell_order(f["pos"], case.config["origin"], info["cell_width"], info["ncell"])

@@ -143,10 +143,8 @@ def test_cell_order_on_cell_boundaries_matches_lexsort(oracle):
     case = W.cell_boundaries()
     pos = W.flatten(case)["pos"]
     origin = np.asarray(case.config["origin"], np.float64)
-    w = case.meta["sort_cell_width"]
-    n = int(round(case.config["extent"][0] / w))
-    ncell = np.array([n, n, n])
-    cellw = np.full(3, w)
+    cellw = np.asarray(case.meta["sort_cell_width"], np.float64)
+    ncell = np.rint(np.asarray(case.config["extent"]) / cellw).astype(np.int64)
     q = (pos - origin) / cellw
     on_edge = np.abs(q - np.rint(q)) < 1e-12
     assert on_edge.any(axis=1).sum() > 1000  # the boundary cases are there
