@@ -1081,7 +1081,7 @@ sph_status sph_create(const sph_config* cfg, void* stream, sph_ctx** out) {
             return SPH_EINVAL;
         }
         // geometry cells of width >= 2h, each cut into split_of(a) sort cells
-        // (4 of width >= h/2 along x, 2 of width >= h along y and z)
+        // (8 of width >= h/4 along x, 2 of width >= h along y and z)
         int64_t n = (int64_t)std::floor(cfg->extent[a] / R);
         if (n < 1) n = 1;
         if ((cfg->periodic_mask & (1 << a)) && n < 3) {

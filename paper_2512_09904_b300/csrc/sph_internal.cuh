@@ -21,10 +21,10 @@
 namespace sph {
 
 constexpr int MAX_MAT = 16;
-// Sort cells per geometry cell: 4 along x, 2 along y and z.  The search walks
+// Sort cells per geometry cell: 8 along x, 2 along y and z.  The search walks
 // x-contiguous rows of sort cells, so narrow cells along x clip each row to
 // the 2h sphere more tightly (fewer candidates) at no extra cost per row.
-constexpr int SPLIT_X = 4, SPLIT_YZ = 2;
+constexpr int SPLIT_X_SHIFT = 3, SPLIT_X = 1 << SPLIT_X_SHIFT, SPLIT_YZ = 2;
 __host__ __device__ __forceinline__ int split_of(int axis) { return axis == 0 ? SPLIT_X : SPLIT_YZ; }
 constexpr int MAX_BODY = 4;
 constexpr int GCORNER_MAX = 512;  // geometry cells per axis with a tabulated corner
@@ -69,7 +69,7 @@ struct BodyDev {
     int set, pad;
 };
 
-// Two grids per case: sort cells (cellw, ncell: width >= h/2 along x and >= h
+// Two grids per case: sort cells (cellw, ncell: width >= h/4 along x and >= h
 // along y and z, the cell-linked list) and geometry cells of SPLIT_X x
 // SPLIT_YZ x SPLIT_YZ sort cells (gcellw: width >= 2h),
 // to whose corners the FP32 snapshot offsets refer; a partner's geometry
@@ -282,13 +282,13 @@ __device__ __forceinline__ void for_each_run(const CC& C, const uint32_t* __rest
             const int row = C.cell_base + (z * ny + y) * nx;
             const int dcy = ((sy + dy) >> 1) - (sy >> 1);
             // geometry cells along x: floor division by SPLIT_X (arithmetic shift, also below 0)
-            for (int g = xl >> 2; g <= (xh >> 2); ++g) {
+            for (int g = xl >> SPLIT_X_SHIFT; g <= (xh >> SPLIT_X_SHIFT); ++g) {
                 const int a = max(xl, SPLIT_X * g), b = min(xh, SPLIT_X * g + SPLIT_X - 1);
                 if (a > b) continue;
                 // a..b lie in one geometry cell; nx is a multiple of SPLIT_X, so it
                 // stays contiguous when wrapped
                 const int aw = px ? ((a % nx) + nx) % nx : a;
-                run((int)cstart[row + aw], (int)cstart[row + aw + (b - a) + 1], g - (sx >> 2), dcy, dcz);
+                run((int)cstart[row + aw], (int)cstart[row + aw + (b - a) + 1], g - (sx >> SPLIT_X_SHIFT), dcy, dcz);
             }
         }
     }
@@ -344,7 +344,7 @@ __device__ __forceinline__ void for_each_candidate(const CC& C, const uint32_t* 
             const int row = C.cell_base + (z * ny + y) * nx;
             const int dcy = ((sy + dy) >> 1) - (sy >> 1);
             const float oy = fmaf(-(float)dcy, C.gcellwf[1], si.y);
-            const int dcx = (xl >> 2) - (sx >> 2);
+            const int dcx = (xl >> SPLIT_X_SHIFT) - (sx >> SPLIT_X_SHIFT);
             float ox = fmaf(-(float)dcx, gw, si.x);
             uint32_t code = (uint32_t)((dcx + 1) | ((dcy + 1) << 2) | ((dcz + 1) << 4));
             const int end = (int)cstart[row + xh + 1];

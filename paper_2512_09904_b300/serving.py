@@ -57,16 +57,16 @@ def _result(b_or_ctx, slot=None, steps=0):
 
 
 def batch_capacity(budget_bytes, max_cases, history_steps):
-    """Largest particle capacity (sort cells = 4 x particles: a gear bath needs
-    1.1-1.6 per particle) that fits the budget."""
+    """Largest particle capacity (sort cells = 6 x particles: a gear bath needs
+    2.2-3.2 per particle) that fits the budget."""
     lo, hi = 1, 1 << 26
     while lo < hi:
         mid = (lo + hi + 1) // 2
-        if sph.Batch.bytes_for(mid, max_cases, 4 * mid + 1, history_steps) <= budget_bytes:
+        if sph.Batch.bytes_for(mid, max_cases, 6 * mid + 1, history_steps) <= budget_bytes:
             lo = mid
         else:
             hi = mid - 1
-    return lo, 4 * lo + 1
+    return lo, 6 * lo + 1
 
 
 # ----------------------------------------------------------------- sweep ---

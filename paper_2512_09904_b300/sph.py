@@ -508,7 +508,7 @@ def sph_relax(pos, dx, h_over_dx, phi, phi_origin, phi_spacing, iterations, stre
 
 
 # sort cells per geometry cell (width >= 2h) along x, y and z
-SORT_SPLIT = (4, 2, 2)
+SORT_SPLIT = (8, 2, 2)
 
 
 def cells_of(case):

@@ -535,7 +535,7 @@ def cell_boundaries(n_random=3000, n_edge=3000, dx=1e-3, h_over_dx=1.3, box=24,
                     origin=(-0.0123, 0.0456, 1.0), seed=12):
     """Particles on sort-cell boundaries: one coordinate at origin + k w_a
     (FP64, w_a the engine's sort-cell width along axis a, extent /
-    (s_a floor(extent / 2h)) with s = 4 along x and 2 along y and z) or a
+    (s_a floor(extent / 2h)) with s = 8 along x and 2 along y and z) or a
     few ulps either side, the others uniform; plus uniform particles.  The
     cell hash's FP32 estimate must hand every such particle to its FP64
     rule.  The origin is away from zero so that |o| enters the estimate's
@@ -544,7 +544,7 @@ def cell_boundaries(n_random=3000, n_edge=3000, dx=1e-3, h_over_dx=1.3, box=24,
     L = box * dx
     o = np.asarray(origin, np.float64)
     ng = int(np.floor(L / (2.0 * h_over_dx * dx)))
-    ns = [s * ng for s in (4, 2, 2)]
+    ns = [s * ng for s in (8, 2, 2)]
     w = [L / n for n in ns]
     lo, hi = o + 1e-3 * L, o + (1.0 - 1e-3) * L
     pts = [rng.uniform(lo, hi, size=(n_random, 3))]

@@ -52,8 +52,8 @@ def test_create_validates_config(sphlib):
     ctx = sphlib.Context(cfg, stream=0)
     info = ctx.sph_get_info()
     R = 2 * cfg["h_over_dx"] * cfg["dx"]
-    for a, split in enumerate((4, 2, 2)):
-        # sort cells: 4 (x) or 2 (y, z) per geometry cell of width >= 2h
+    for a, split in enumerate((8, 2, 2)):
+        # sort cells: 8 (x) or 2 (y, z) per geometry cell of width >= 2h
         assert info["ncell"][a] == split * int(np.floor(cfg["extent"][a] / R))
         assert info["cell_width"][a] >= R / split
     # default sub-step cap: ceil(cfl_ad / cfl_ac (c0 / u_ref + 1)) + 2
