@@ -19,6 +19,8 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -176,32 +178,90 @@ struct Engine {
             return (E).fail(SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, __LINE__); \
     } while (0)
 
-// Host staging array of doubles.  Arrays of 2 MB and more sit on
-// transparent huge pages where the kernel offers them: a 50 MB block then
-// takes tens of page faults to fill instead of thousands.
+// Page-locked host blocks for staging large particle arrays, kept by the
+// process and handed from one context to the next: a staged array in such a
+// block goes to the device at full DMA rate with no page-locking at admission
+// (locking a large array page by page costs more than its copy).  Blocks are
+// 2 MB multiples; at most kPinnedCap bytes are ever locked, beyond which (or
+// where the runtime refuses, e.g. without a GPU) arrays fall back to
+// ordinary host memory.
+class PinnedPool {
+  public:
+    static PinnedPool& get() {
+        static PinnedPool* p = new PinnedPool();  // never destroyed: blocks live until exit
+        return *p;
+    }
+    // a block of at least `bytes` (its size in *cap), or nullptr
+    void* take(size_t bytes, size_t* cap) {
+        const size_t sz = round_up(bytes);
+        std::lock_guard<std::mutex> lock(mu_);
+        auto it = free_.lower_bound(sz);
+        if (it != free_.end() && it->first <= 2 * sz) {
+            void* p = it->second;
+            *cap = it->first;
+            free_.erase(it);
+            return p;
+        }
+        if (disabled_ || locked_ + sz > kPinnedCap) return nullptr;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, sz, cudaHostAllocPortable) != cudaSuccess) {
+            (void)cudaGetLastError();
+            disabled_ = true;  // no device, or locked memory refused: stay with ordinary memory
+            return nullptr;
+        }
+        locked_ += sz;
+        *cap = sz;
+        return p;
+    }
+    void give(void* p, size_t cap) {
+        std::lock_guard<std::mutex> lock(mu_);
+        free_.emplace(cap, p);
+    }
+
+  private:
+    static constexpr size_t kBlock = (size_t)2 << 20;
+    static constexpr size_t kPinnedCap = (size_t)8 << 30;
+    static size_t round_up(size_t b) { return (b + kBlock - 1) / kBlock * kBlock; }
+    std::mutex mu_;
+    std::multimap<size_t, void*> free_;
+    size_t locked_ = 0;
+    bool disabled_ = false;
+};
+
+// Host staging array of doubles.  Arrays of 2 MB and more come from the
+// page-locked pool when it can serve them, else sit on transparent huge pages
+// where the kernel offers them (a 50 MB block then takes tens of page faults
+// to fill instead of thousands).
 class HostArray {
   public:
     HostArray() = default;
     HostArray(const HostArray&) = delete;
     HostArray& operator=(const HostArray&) = delete;
-    HostArray(HostArray&& o) noexcept : p_(o.p_), n_(o.n_) { o.p_ = nullptr, o.n_ = 0; }
+    HostArray(HostArray&& o) noexcept : p_(o.p_), n_(o.n_), pinned_cap_(o.pinned_cap_) {
+        o.p_ = nullptr, o.n_ = 0, o.pinned_cap_ = 0;
+    }
     HostArray& operator=(HostArray&& o) noexcept {
         if (this != &o) {
-            std::free(p_);
-            p_ = o.p_, n_ = o.n_;
-            o.p_ = nullptr, o.n_ = 0;
+            release();
+            p_ = o.p_, n_ = o.n_, pinned_cap_ = o.pinned_cap_;
+            o.p_ = nullptr, o.n_ = 0, o.pinned_cap_ = 0;
         }
         return *this;
     }
-    ~HostArray() { std::free(p_); }
+    ~HostArray() { release(); }
     bool alloc(size_t n) {
-        std::free(p_);
-        p_ = nullptr, n_ = 0;
+        release();
         if (n == 0) return true;
         const size_t huge = (size_t)2 << 20, bytes = n * sizeof(double);
         if (bytes >= huge) {
-            p_ = (double*)std::aligned_alloc(huge, (bytes + huge - 1) / huge * huge);
-            if (p_) madvise(p_, bytes, MADV_HUGEPAGE);  // advice only: failure is harmless
+            size_t cap = 0;
+            p_ = (double*)PinnedPool::get().take(bytes, &cap);
+            if (p_) {
+                pinned_cap_ = cap;
+            } else {
+                p_ = (double*)std::aligned_alloc(huge, (bytes + huge - 1) / huge * huge);
+                if (p_) madvise(p_, bytes, MADV_HUGEPAGE);  // advice only: failure is harmless
+            }
         } else {
             p_ = (double*)std::malloc(bytes);
         }
@@ -210,13 +270,20 @@ class HostArray {
     }
     size_t size() const { return n_; }
     bool empty() const { return n_ == 0; }
+    bool pinned() const { return pinned_cap_ != 0; }
     double* data() { return p_; }
     const double* data() const { return p_; }
     const double& operator[](size_t i) const { return p_[i]; }
 
   private:
+    void release() {
+        if (p_ && pinned_cap_) PinnedPool::get().give(p_, pinned_cap_);
+        else std::free(p_);
+        p_ = nullptr, n_ = 0, pinned_cap_ = 0;
+    }
     double* p_ = nullptr;
     size_t n_ = 0;
+    size_t pinned_cap_ = 0;  // size of the page-locked block holding p_, or 0
 };
 
 // dst = src[0..n), in up to 8 host threads for large arrays.  bad: how
@@ -635,24 +702,24 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
         E_CUDA(E, cudaMemsetAsync(B.TORQ64 + idb, 0, sizeof(double) * n, s));
         E_CUDA(E, cudaMemsetAsync(B.TORQV64 + idb, 0, sizeof(double) * n, s));
     }
-    // the staged blocks go up as they are (one device scratch sized for the
-    // largest) and a kernel writes them into the packed layout
+    // the staged blocks go up as they are (one device scratch holding them
+    // all, so the copies and kernels of the blocks queue back to back) and a
+    // kernel writes each into the packed layout
     size_t scratch = 0;
-    for (const PBlock& P : c->blocks)
-        scratch = std::max(scratch, P.pos.size() + P.vel.size() + P.nrm.size() + P.T.size() + P.rho.size());
+    for (const PBlock& P : c->blocks) scratch += P.pos.size() + P.vel.size() + P.nrm.size() + P.T.size() + P.rho.size();
     double* d = nullptr;
     E_CUDA(E, cudaMallocAsync((void**)&d, sizeof(double) * std::max<size_t>(scratch, 1), s));
     cudaError_t e = cudaSuccess;
-    std::vector<void*> pinned;  // staging arrays page-locked for the copies of one block
+    std::vector<void*> pinned;  // staging arrays page-locked here for their copies
+    double* q = d;
     for (const PBlock& P : c->blocks) {
-        double* q = d;
         auto up = [&](const HostArray& v) -> const double* {
             if (v.empty() || e != cudaSuccess) return nullptr;
             const size_t bytes = sizeof(double) * v.size();
-            // large arrays are page-locked for the copy (full-rate DMA instead
-            // of the driver's pageable staging); the pageable copy remains if
-            // that is refused
-            if (bytes >= ((size_t)2 << 20)) {
+            // large arrays not already in page-locked memory are locked for the
+            // copy (full-rate DMA instead of the driver's pageable staging);
+            // the pageable copy remains if that is refused
+            if (bytes >= ((size_t)2 << 20) && !v.pinned()) {
                 void* h = const_cast<double*>(v.data());
                 if (cudaHostRegister(h, bytes, cudaHostRegisterDefault) == cudaSuccess) pinned.push_back(h);
                 else (void)cudaGetLastError();
@@ -674,14 +741,13 @@ static sph_status engine_admit(Engine& E, const sph_ctx* c, int64_t steps_req, i
         if (e == cudaSuccess)
             e = launch_admit_block(B, p, (int)P.n, (int)(at + P.first), (int)(idb + P.first), tag, P.kind == 0 ? 1 : 0,
                                    M.rho0, M.T_init, dpos, dvel, dnrm, dT, drho, s);
-        // the scratch is reused by the next block: let this one's kernel finish
-        // first (and, after an error, any copy still in flight)
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        else (void)cudaStreamSynchronize(s);
-        for (void* h : pinned) (void)cudaHostUnregister(h);
-        pinned.clear();
         if (e != cudaSuccess) break;
     }
+    // the copies are done before the staging arrays are unlocked or freed
+    // (and, after an error, nothing is left in flight)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    else (void)cudaStreamSynchronize(s);
+    for (void* h : pinned) (void)cudaHostUnregister(h);
     cudaFreeAsync(d, s);
     if (e != cudaSuccess) return E.fail(SPH_ECUDA, "admission: %s", cudaGetErrorString(e));
     // reference heat content and initial max speed from the appended block
