@@ -272,7 +272,7 @@ sph_status sph_fma_peak(void* stream, int reps, double* tflops, double* ms);
  * particle add each particle's pair terms in two interleaved halves, which
  * changes FP32 rounding only. */
 enum {
-    SPH_TUNE_LIST_BATCH = 0, /* neighbour-list entries each thread loads together: 1, 2, 4 or 8 (default) */
+    SPH_TUNE_LIST_BATCH = 0, /* neighbour-list entries each thread loads together: 1, 2 (default), 4 or 8 */
     SPH_TUNE_TPP = 1,        /* threads per particle in passes VT, M, C: 1 (default; 32 particles
                                 per warp) or 2 (16 particles per warp) */
     SPH_TUNE_BLOCK = 2       /* threads per block of the pair passes: 64, 128 (default) or 256 */

@@ -347,7 +347,7 @@ struct sph_ctx {
     double cellw[3]{};
     double sigma0 = 0.0;
     int kcap = 0;
-    int tune_batch = 8, tune_tpp = 1, tune_block = 128;
+    int tune_batch = 2, tune_tpp = 1, tune_block = 128;
     bool started = false;   // stepped as a single case
     bool admitted = false;  // handed to a batch
     Engine* eng = nullptr;
@@ -479,7 +479,7 @@ static sph_status engine_alloc(Engine& E, int64_t n_cap, int c_cap, int64_t cell
         return E.fail(e == cudaErrorMemoryAllocation ? SPH_ENOMEM : SPH_ECUDA, "device allocation: %s",
                       cudaGetErrorString(e));
     B.nb_stride = (int)n;
-    if (B.tune_batch == 0) B.tune_batch = 8;
+    if (B.tune_batch == 0) B.tune_batch = 2;
     if (B.tune_tpp == 0) B.tune_tpp = 1;
     if (B.tune_block == 0) B.tune_block = 128;
     E.cases.assign(c_cap, HostCase{});
@@ -1662,7 +1662,7 @@ sph_status sph_batch_create(const sph_batch_config* cfg, void* stream, sph_batch
     *out = nullptr;
     sph_batch* b = new sph_batch();
     b->eng.stream = (cudaStream_t)stream;
-    b->eng.B.tune_batch = 8;
+    b->eng.B.tune_batch = 2;
     b->eng.B.uni_fluid = 1;  // batched cases carry a single fluid material
     sph_status s = engine_alloc(b->eng, cfg->max_particles, cfg->max_cases, cfg->max_cells, cfg->history_steps);
     if (s != SPH_OK) {
