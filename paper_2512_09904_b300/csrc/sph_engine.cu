@@ -1549,9 +1549,10 @@ static sph_status engine_autotune(Engine& E, int steps_per_trial, sph_tune_repor
     sph_status r = score(&s_start);
     s_best = s_start;
     for (int k = 0; k < 3 && r == SPH_OK; ++k) {
+        const int scored = best[k];  // this key's value in the best variant so far: already timed
         for (int v = 0; v < 4 && r == SPH_OK; ++v) {
             const int val = vals[k][v];
-            if (val == 0 || val == best[k]) continue;
+            if (val == 0 || val == scored) continue;
             for (int q = 0; q < 3; ++q) *tuning_field(E.B, keys[q]) = best[q];
             *tuning_field(E.B, keys[k]) = val;
             double sc = 0.0;
