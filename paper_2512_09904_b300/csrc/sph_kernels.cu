@@ -617,9 +617,11 @@ constexpr int PART_FLUID = 1, PART_WALL = 2, PART_ALL = 3;
 
 // Walk `cnt` list slots starting at slot k0 with step ks (+1 fluid part,
 // -1 wall part); geometry from the snapshot offsets and the packed cell code.
-// The list entries of a batch are loaded together so that BATCH independent
-// loads of the (DRAM-resident) list stream are in flight per thread.  With
-// TPP threads per particle, thread `sub` takes list slots sub, sub + TPP, ...
+// A thread loads its list entries BATCH at a time, one batch ahead of their
+// use, and prefetches the batch after that from DRAM into L2, so that the
+// (DRAM-resident) list stream is in flight while partners are gathered and
+// summed.  With TPP threads per particle, thread `sub` takes list slots sub,
+// sub + TPP, ...
 template <int BATCH, int TPP, class CC, class F>
 __device__ __forceinline__ void list_walk(const CC& C, const Bufs& B, int i, float4 si, int k0, int ks,
                                           int cnt, int sub, F&& f) {
