@@ -16,6 +16,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -125,9 +126,11 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler (every 100 ms) around the timed region."""
+    """nvidia-smi sampler (every 100 ms) around the timed region; stop()
+    keeps the samples stamped inside [mark(), stop()] (all of them if none
+    falls inside)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -140,10 +143,23 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        self.t0 = None
+
+    def ready(self, timeout=10.0):
+        """Wait until the sampler has written its first sample."""
+        end = time.time() + timeout
+        while self.p is not None and time.time() < end:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
+
+    def mark(self):
+        self.t0 = time.time()
 
     def stop(self):
         if self.p is None:
             return None
+        t1 = time.time()
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -154,21 +170,27 @@ class Clocks:
         with open(self.f.name) as g:
             for line in g:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append((ts, parts[1:]))
         os.unlink(self.f.name)
         if not rows:
             return None
+        inside = [r for ts, r in rows if ts is not None and self.t0 is not None and self.t0 <= ts <= t1]
+        sel = inside or [r for _, r in rows]
         def num(x):
             try:
                 return float(x)
             except ValueError:
                 return float("nan")
-        sm = [num(r[1]) for r in rows]
+        sm = [num(r[1]) for r in sel]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[k] for r in sel for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in sel),
+                "reasons": reasons, "samples": len(sel), "samples_in_timed_region": len(inside)}
 
 
 def cpu_baseline(omega, min_seconds=10.0, max_steps=40):
@@ -300,10 +322,12 @@ def main():
     info0 = ctx.sph_get_info()
 
     clocks = Clocks(local)
+    clocks.ready()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         ctx.sph_step(1)
