@@ -766,3 +766,64 @@ def test_wall_pstar_printed_weakens_the_wall(oracle):
         sim.step(1)
         return sim.field("vel")[:case.n_fluid][idx[:, 2] == 0, 2].mean()
     assert impact(1) < impact(0) < 0.0
+
+
+# ------------------------------------------------------ degenerate cases ---
+def _periodic_lattice(n, v0, c0=10.0, mu=0.02, rho0=1000.0):
+    idx = W._grid((0, 0, 0), (n, n, n))
+    pos = (idx + 0.5) * DX
+    cfg = W._cfg(origin=(0, 0, 0), extent=(n * DX,) * 3, dx=DX, c0=c0, gravity=(0, 0, 0), periodic_mask=0b111)
+    vel = np.tile(np.asarray(v0, float), (len(pos), 1))
+    return W.Case("translating_lattice", cfg, {0: W._mat(rho0, mu, 0.6, 4000.0, 300.0)},
+                  [dict(mat=0, pos=pos, vel=vel, T=None, rho=None)], [])
+
+
+def _head_on_pair(u, gap=DX, mu=1e-3):
+    # two fluid particles on the x axis closing at 2u, alone in a large box
+    pos = np.array([[0.05 - 0.5 * gap, 0.05, 0.05], [0.05 + 0.5 * gap, 0.05, 0.05]])
+    vel = np.array([[u, 0.0, 0.0], [-u, 0.0, 0.0]])
+    cfg = W._cfg(origin=(0, 0, 0), extent=(0.1, 0.1, 0.1), dx=DX, c0=10.0, gravity=(0, 0, 0))
+    return W.Case("head_on_pair", cfg, {0: W._mat(1000.0, mu, 0.6, 4000.0, 300.0)},
+                  [dict(mat=0, pos=pos, vel=vel, T=None, rho=None)], [])
+
+
+def test_uniform_translation_is_galilean(oracle):
+    # a perfect periodic lattice moving as a rigid whole: every pair has
+    # v_i - v_j = 0 and every kernel sum is the rest lattice's sigma0, so
+    # Eqs. (10)-(15) give no force and no density change; the lattice keeps
+    # its velocity and is carried by it, x = x0 + v0 t (minimum image)
+    v0 = np.array([0.3, -0.2, 0.1])
+    n = 8
+    case = _periodic_lattice(n, v0)
+    x0 = W.flatten(case)["pos"].copy()
+    sim = oracle.OracleSim(case)
+    sim.step(5)
+    t = sim.time()["t"]
+    d = sim.field("pos") - (x0 + v0 * t)
+    d -= n * DX * np.round(d / (n * DX))
+    assert np.abs(sim.field("vel") - v0).max() < 1e-10 * np.abs(v0).max()
+    assert np.abs(d).max() < 1e-10 * DX
+    assert np.abs(sim.field("rho") - 1000.0).max() < 1e-10 * 1000.0
+    assert sim.time()["substeps"] >= 5
+
+
+def test_head_on_pair_is_symmetric_and_repels(oracle):
+    # the pair's Riemann dissipation (Eq. 11: beta > 0 while U_L > U_R) and
+    # the density it gains by Eq. (10) continuity push the two apart; past
+    # the bounce, continuity lowers the density below rho0 and the pair swings
+    # back (Eq. 14 keeps the larger density, and the kernel sum of a lone pair
+    # is below sigma0).  The accelerations are equal and opposite (r_ji = -r_ij
+    # exactly in FP64), so the velocities stay opposite and the midpoint stays
+    # put at every step, nothing acts across the axis, and the dissipation
+    # keeps every later speed below the initial one
+    u = 0.1
+    sim = oracle.OracleSim(_head_on_pair(u))
+    sim.step(1)
+    v, rho = sim.field("vel"), sim.field("rho")
+    assert 0.0 < v[0, 0] < u and rho[0] == rho[1] > 1000.0
+    for _ in range(7):
+        sim.step(1)
+        x, v = sim.field("pos"), sim.field("vel")
+        assert v[0, 0] == -v[1, 0] and abs(v[0, 0]) < u
+        assert x[0, 0] + x[1, 0] == pytest.approx(0.1, rel=1e-15)
+        assert np.all(v[:, 1:] == 0.0) and np.all(x[:, 1:] == 0.05)
