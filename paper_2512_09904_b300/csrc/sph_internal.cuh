@@ -227,9 +227,10 @@ __device__ __forceinline__ float row_half_width(const CC& C, float d2) {
 }
 
 // Distance from a point at offset o inside its sort cell (width w) to the
-// slab of the cell d sort cells away on that axis.
+// slab of the cell d sort cells away on that axis: d w - o ahead (d > 0),
+// o - (d + 1) w behind (d < 0), 0 in its own cell, as one branch-free max.
 __device__ __forceinline__ float slab_gap(int d, float w, float o) {
-    return d > 0 ? fmaxf(fmaf((float)(d - 1), w, w - o), 0.f) : (d < 0 ? fmaxf(fmaf((float)(-d - 1), w, o), 0.f) : 0.f);
+    return fmaxf(fmaxf(fmaf((float)d, w, -o), fmaf(-(float)(d + 1), w, o)), 0.f);
 }
 
 // Candidate runs of slot i (sort cell key_i, geometry offsets si): the rows
@@ -322,26 +323,29 @@ __device__ __forceinline__ void for_each_candidate(const CC& C, const uint32_t* 
     const float cy = fmaf(-(float)(sy & 1), wy, si.y);
     const float cz = fmaf(-(float)(sz & 1), wz, si.z);
     const float R2 = C.R2hi, gw = C.gcellwf[0];
+    // rows inside the grid, and the x range within SPLIT_X sort cells of i's
+    const int dz0 = max(-2, -sz), dz1 = min(2, nz - 1 - sz), dy0 = max(-2, -sy), dy1 = min(2, ny - 1 - sy);
+    const int xlo = max(0, sx - SPLIT_X), xhi = min(nx - 1, sx + SPLIT_X);
+    const float cxi = cx * C.inv_scellwf[0];  // i's offset in sort-cell widths
 #pragma unroll 1
-    for (int dz = -2; dz <= 2; ++dz) {
+    for (int dz = dz0; dz <= dz1; ++dz) {
         const int z = sz + dz;
-        if (z < 0 || z >= nz) continue;
         const float gz = slab_gap(dz, wz, cz);
         if (gz * gz >= R2) continue;
         const int dcz = ((sz + dz) >> 1) - (sz >> 1);
         const float oz = fmaf(-(float)dcz, C.gcellwf[2], si.z);
+        const int rowz = C.cell_base + z * ny * nx;
 #pragma unroll 1
-        for (int dy = -2; dy <= 2; ++dy) {
+        for (int dy = dy0; dy <= dy1; ++dy) {
             const int y = sy + dy;
-            if (y < 0 || y >= ny) continue;
             const float gy = slab_gap(dy, wy, cy);
             const float d2 = fmaf(gy, gy, gz * gz);
             if (d2 >= R2) continue;
             const float ex = row_half_width(C, d2);
-            const int xl = max(0, sx + max(-SPLIT_X, (int)floorf((cx - ex) * C.inv_scellwf[0])));
-            const int xh = min(nx - 1, sx + min(SPLIT_X, (int)floorf((cx + ex) * C.inv_scellwf[0])));
+            const int xl = max(xlo, sx + __float2int_rd(fmaf(-ex, C.inv_scellwf[0], cxi)));
+            const int xh = min(xhi, sx + __float2int_rd(fmaf(ex, C.inv_scellwf[0], cxi)));
             if (xl > xh) continue;
-            const int row = C.cell_base + (z * ny + y) * nx;
+            const int row = rowz + y * nx;
             const int dcy = ((sy + dy) >> 1) - (sy >> 1);
             const float oy = fmaf(-(float)dcy, C.gcellwf[1], si.y);
             const int dcx = (xl >> SPLIT_X_SHIFT) - (sx >> SPLIT_X_SHIFT);
