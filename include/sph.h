@@ -45,11 +45,12 @@ typedef enum {
 } sph_status;
 
 /* Case configuration.  The domain box holds every particle for the whole run;
- * it is cut into geometry cells of width >= 2h per axis, each split into 2 x 2
- * x 2 sort cells of width >= h (the cell-linked list; the neighbour search
- * visits the sort cells within two of a particle's that its 2h sphere
- * reaches).  A periodic axis wraps particle positions on this machine and needs
- * at least 3 geometry cells along it. */
+ * it is cut into geometry cells of width >= 2h per axis, each split into 8
+ * sort cells along x (width >= h/4) and 2 along y and z (width >= h): the
+ * cell-linked list.  The neighbour search walks the rows of sort cells within
+ * two of a particle's along y and z whose slab its 2h sphere reaches, and in
+ * each row the sort cells the sphere reaches.  A periodic axis wraps particle
+ * positions on this machine and needs at least 3 geometry cells along it. */
 typedef struct {
     double origin[3], extent[3]; /* domain box, m */
     double dx;                   /* particle spacing, m (mass = rho0 dx^3, wall volume dx^3) */
@@ -230,8 +231,8 @@ typedef struct {
     double last_dt_ad;
     int last_nsub;
     int kcap;                 /* sub-step cap per advection step */
-    int ncell[3];             /* sort cells per axis (2 per geometry cell) */
-    double cell_width[3];     /* sort-cell width (>= h) */
+    int ncell[3];             /* sort cells per axis (8 per geometry cell along x, 2 along y, z) */
+    double cell_width[3];     /* sort-cell width (>= h/4 along x, >= h along y, z) */
     int error_bits;           /* 1 NaN/Inf, 2 fluid left the box */
     int graph_launches;       /* kernels per advection step of the profiling graph (kcap sub-step slots) */
     int kernels_fixed;        /* kernels per advection step of the stepping graph: kernels_fixed + */
