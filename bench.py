@@ -103,6 +103,9 @@ def parse():
     ap.add_argument("--serve-steps", type=int, default=200, help="serving trace: advection steps per request")
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="serving trace: arrivals per s (0 = 4/s scaled by 2000 / serve-steps)")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="instead of the headline line: one JSON line measuring the rows beyond the coupled "
+                         "step (viscous heating, contact factor, two-shaft train, particle relaxation)")
     return ap.parse_args()
 
 
@@ -276,6 +279,78 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def next_rows_line(args):
+    """The rows beyond the coupled step, each measured on one B300: the
+    viscous-dissipation heating term (the gear bath stepped with and without
+    it; its cost sits in pass VT), the contact factor of Eq. (24) (computed in
+    pass VT for every rotating-body particle of the same run), the two-shaft
+    gear train at dx = 0.75 mm, and the particle relaxation of Sec. 2.2 (seeds
+    in a sphere, host arrays in and out, so its rate is end to end)."""
+    import numpy as np
+    import torch
+    from paper_2512_09904_b300 import sph, workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    warm, steps = max(args.warmup, 3), args.steps
+
+    def timed(case):
+        c = sph.from_case(case, stream=stream.cuda_stream)
+        c.sph_step(warm)
+        i0 = c.sph_get_info()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            c.sph_step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sub = c.sph_get_info()["substeps"] - i0["substeps"]
+        th = c.sph_read_torque_heat(0)
+        c.close()
+        # per-pass device times from a replay of the same steps with event records
+        r = sph.from_case(case, stream=stream.cuda_stream)
+        r.sph_step(warm)
+        r.sph_profile(True)
+        r.sph_step(steps)
+        prof = r.sph_profile_read(reset=True)
+        r.close()
+        return {"n_fluid": case.n_fluid, "n_solid": case.n_solid, "ms_per_step": ms / steps, "substeps": sub,
+                "value": case.n_fluid * sub / (ms * 1e-3), "unit": UNIT, "torque_avg_Nm": th["torque_avg"],
+                "heat_J": th["heat"],
+                "per_launch_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}}
+
+    clocks = Clocks(0)
+    clocks.ready()
+    clocks.mark()
+    out = {"metric": "rows beyond the coupled step", "steps": steps, "warmup": warm, "data": "synthetic"}
+    base = workload(args.dx, args.omega)
+    out["gear_bath"] = timed(base)
+    heated = workload(args.dx, args.omega)
+    heated.config = dict(heated.config, viscous_heating=1)
+    out["viscous_heating"] = timed(heated)
+    out["viscous_heating"]["pass_VT_cost"] = (out["viscous_heating"]["per_launch_ms"]["pass_VT"] /
+                                              out["gear_bath"]["per_launch_ms"]["pass_VT"] - 1.0)
+    body = W.flatten(base)["body"]
+    out["contact_factor"] = {"particles": int(np.count_nonzero(body >= 0)),
+                             "where": "pass VT, every advection step (gear_bath.per_launch_ms.pass_VT)"}
+    out["gear_pair"] = timed(W.gear_pair(dx=0.75e-3))
+    rb = W.relax_body("sphere", size=40e-3, dx=1e-3)
+    args_r = (rb["pos"], rb["dx"], rb["h_over_dx"], rb["phi"], rb["phi_origin"], rb["phi_spacing"])
+    sph.sph_relax(*args_r, 2, stream=stream.cuda_stream)  # warm-up
+    iters = 50
+    t0 = time.perf_counter()
+    _, amax = sph.sph_relax(*args_r, iters, stream=stream.cuda_stream)
+    sec = time.perf_counter() - t0
+    out["relaxation"] = {"seeds": len(rb["pos"]), "iterations": iters, "seconds": sec,
+                         "value": len(rb["pos"]) * iters / sec, "unit": "seed-iterations/s (host arrays in and out)",
+                         "max_force_first_last": [float(amax[0]), float(amax[-1])],
+                         "level_set_nodes": int(rb["phi"].size)}
+    out["clocks"] = clocks.stop()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -283,6 +358,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.next_rows:
+        if rank == 0:
+            next_rows_line(args)
         return
     import numpy as np
     import torch

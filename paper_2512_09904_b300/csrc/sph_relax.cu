@@ -8,7 +8,12 @@
 // surface, replaced by the half space at the particle's depth d = -phi:
 // -2 n A(d), A(d) = 2 pi int_d^{2h} W(r) r dr in closed form), the step
 // dt = 0.25 sqrt(h / max |F_p|), r += F_p dt^2 / 2, and particles that end
-// outside moved back onto the surface along the level-set normal.  FP64.
+// outside moved back onto the surface along the level-set normal.  FP64
+// arithmetic; B300's FP64 pipe is the bound, so candidates are rejected
+// first from an FP32 copy of the positions with an error margin (the FP64
+// membership rule still decides every pair that passes), and the kernel and
+// level-set formulas multiply by precomputed reciprocals instead of dividing.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,24 +32,29 @@ using namespace sph;
 
 struct RelaxDev {
     double h, R2, vol;
+    double inv_h;
     double kw, kdw;      // Wendland C2 alpha, -5 alpha / h
+    double kdwh;         // kdw / h: (dW/dr) / r = kdwh (1 - r / 2h)^3
+    float R2f;           // FP32 pre-test: no pair has r2 (from the FP32 copy) at or above this
     double aw;           // 2 pi alpha h^2: A(d) = aw (2/7 - F(d / h))
     const double* phi;
     int nphi[3];
     double phi_o[3], phi_inv, phi_dx;
+    double inv_dx1, inv_dx2;  // 1 / phi_dx, 1 / (2 phi_dx): one- and two-sided differences
     double cell_o[3], cell_w[3];
     int ncell[3];
 };
 
-__device__ __forceinline__ double rx_dW(const RelaxDev& R, double r) {
-    const double q = r / R.h, t = 1.0 - 0.5 * q;
-    return R.kdw * q * t * t * t;
+// (dW/dr) / r = (kdw / h) (1 - q/2)^3 with q = r / h
+__device__ __forceinline__ double rx_dW_over_r(const RelaxDev& R, double r) {
+    const double t = 1.0 - 0.5 * (r * R.inv_h);
+    return R.kdwh * t * t * t;
 }
 
 // A(d) = 2 pi alpha h^2 (2/7 - F(q)), q = d / h, with F the antiderivative of
 // (1 - q/2)^4 (1 + 2q) q: q^7/56 - 5 q^6/32 + q^5/2 - 5 q^4/8 + q^2/2
 __device__ __forceinline__ double rx_A(const RelaxDev& R, double d) {
-    double q = d / R.h;
+    double q = d * R.inv_h;
     if (q < 0.0) q = 0.0;
     if (q >= 2.0) return 0.0;
     const double q2 = q * q, q4 = q2 * q2;
@@ -75,7 +85,7 @@ __device__ double rx_grad_node(const RelaxDev& R, int i, int j, int k, int a) {
     int l[3] = {i, j, k}, u[3] = {i, j, k};
     l[a] = lo;
     u[a] = hi;
-    return (rx_node(R, u[0], u[1], u[2]) - rx_node(R, l[0], l[1], l[2])) / (span * R.phi_dx);
+    return (rx_node(R, u[0], u[1], u[2]) - rx_node(R, l[0], l[1], l[2])) * (span > 1.5 ? R.inv_dx2 : R.inv_dx1);
 }
 
 // trilinear level set, and the normalised trilinear interpolation of the
@@ -106,11 +116,25 @@ __device__ double rx_phi(const RelaxDev& R, const double x[3], double n[3]) {
     return phi;
 }
 
-__global__ void k_rx_force(RelaxDev R, int n, const double* __restrict__ pos, const int* __restrict__ perm,
-                           const int* __restrict__ cs, double* acc, unsigned long long* amax) {
+// FP32 copy of a position, relative to the cell grid's corner
+__device__ __forceinline__ float4 rx_f32(const RelaxDev& R, const double x[3]) {
+    return make_float4((float)(x[0] - R.cell_o[0]), (float)(x[1] - R.cell_o[1]), (float)(x[2] - R.cell_o[2]), 0.f);
+}
+
+__global__ void k_rx_f32(RelaxDev R, int n, const double* __restrict__ pos, float4* pf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    pf[i] = rx_f32(R, x);
+}
+
+__global__ void k_rx_force(RelaxDev R, int n, const double* __restrict__ pos, const float4* __restrict__ pf,
+                           const int* __restrict__ perm, const int* __restrict__ cs, double* acc,
+                           unsigned long long* amax) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double xi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    const float4 fi = pf[i];
     int c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -125,11 +149,14 @@ __global__ void k_rx_force(RelaxDev R, int n, const double* __restrict__ pos, co
                 for (int q = cs[cell]; q < cs[cell + 1]; ++q) {
                     const int j = perm[q];
                     if (j == i) continue;
+                    const float4 fj = pf[j];
+                    const float e0 = fi.x - fj.x, e1 = fi.y - fj.y, e2 = fi.z - fj.z;
+                    if (fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) >= R.R2f) continue;  // beyond 2h even with the FP32 error
                     const double d0 = __dsub_rn(xi[0], pos[3 * j]), d1 = __dsub_rn(xi[1], pos[3 * j + 1]),
                                  d2 = __dsub_rn(xi[2], pos[3 * j + 2]);
                     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
                     if (!(r2 > 0.0 && r2 < R.R2)) continue;
-                    const double r = sqrt(r2), k = -2.0 * R.vol * rx_dW(R, r) / r;
+                    const double k = -2.0 * R.vol * rx_dW_over_r(R, sqrt(r2));
                     ac[0] += k * d0;
                     ac[1] += k * d1;
                     ac[2] += k * d2;
@@ -147,7 +174,7 @@ __global__ void k_rx_force(RelaxDev R, int n, const double* __restrict__ pos, co
     atomicMax(amax, (unsigned long long)__double_as_longlong(am));  // non-negative: bit order = value order
 }
 
-__global__ void k_rx_move(RelaxDev R, int n, double* pos, const double* __restrict__ acc,
+__global__ void k_rx_move(RelaxDev R, int n, double* pos, float4* pf, const double* __restrict__ acc,
                           const unsigned long long* amax) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -165,6 +192,7 @@ __global__ void k_rx_move(RelaxDev R, int n, double* pos, const double* __restri
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) pos[3 * i + a] = x[a];
+    pf[i] = rx_f32(R, x);
 }
 
 }  // namespace
@@ -187,6 +215,10 @@ extern "C" sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* 
     R.kw = alpha;
     R.kdw = -5.0 * alpha / R.h;
     R.aw = 2.0 * M_PI * alpha * R.h * R.h;
+    R.inv_h = 1.0 / R.h;
+    R.kdwh = R.kdw / R.h;
+    R.inv_dx1 = 1.0 / cfg->phi_spacing;
+    R.inv_dx2 = 1.0 / (2.0 * cfg->phi_spacing);
     R.phi_inv = 1.0 / cfg->phi_spacing;
     R.phi_dx = cfg->phi_spacing;
     int64_t nphi = 1, ncells = 1;
@@ -207,7 +239,21 @@ extern "C" sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* 
         sph::set_stateless_error("sph_relax: level-set box too large for the cell grid");
         return SPH_EINVAL;
     }
+    // FP32 pre-test margin.  An FP32 coordinate relative to the grid corner
+    // is off by at most E 2^-24 (E bounds |x - corner|: the box, or a seed
+    // outside it, doubled for the moves), an FP32 difference of two by
+    // delta = 2 E 2^-24 plus its own rounding (differences within the 27
+    // cells are below 8h), so a pair (r < 2h) has r_f32 < 2h + 2 delta; the
+    // factor 1 + 1e-6 covers the FP32 rounding of r^2 and of the bound.
+    double E = 0.0;
+    for (int a = 0; a < 3; ++a) E = std::max(E, (R.nphi[a] - 1) * cfg->phi_spacing);
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) E = std::max(E, std::fabs(pos[3 * i + a] - R.cell_o[a]));
+    E *= 2.0;
+    const double delta = 2.0 * E * 0x1p-24 + 8.0 * R.h * 0x1p-24, rmax = 2.0 * R.h + 2.0 * delta;
+    R.R2f = (float)(rmax * rmax * (1.0 + 1e-6));
     double *d_pos = nullptr, *d_acc = nullptr, *d_phi = nullptr;
+    float4* d_pf = nullptr;
     unsigned long long* d_amax = nullptr;
     uint32_t *keys = nullptr, *rank = nullptr, *cnt = nullptr, *tmp = nullptr, *blk = nullptr;
     int32_t *perm = nullptr, *cs = nullptr;
@@ -217,6 +263,7 @@ extern "C" sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* 
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&(p), (bytes), s)
     RA(d_pos, sizeof(double) * 3 * n);
     RA(d_acc, sizeof(double) * 3 * n);
+    RA(d_pf, sizeof(float4) * n);
     RA(d_phi, sizeof(double) * nphi);
     RA(d_amax, sizeof(unsigned long long) * (size_t)iterations);
     RA(keys, sizeof(uint32_t) * n);
@@ -232,11 +279,15 @@ extern "C" sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* 
     if (e == cudaSuccess) e = cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long) * (size_t)iterations, s);
     R.phi = d_phi;
     const int g = (int)((n + 127) / 128);
+    if (e == cudaSuccess) {
+        k_rx_f32<<<g, 128, 0, s>>>(R, (int)n, d_pos, d_pf);
+        e = cudaGetLastError();
+    }
     for (int it = 0; it < iterations && e == cudaSuccess; ++it) {
         e = launch_cell_sort(d_pos, (int)n, R.cell_o, R.cell_w, R.ncell, keys, rank, cnt, tmp, blk, perm, cs, s);
         if (e == cudaSuccess) {
-            k_rx_force<<<g, 128, 0, s>>>(R, (int)n, d_pos, perm, cs, d_acc, d_amax + it);
-            k_rx_move<<<g, 128, 0, s>>>(R, (int)n, d_pos, d_acc, d_amax + it);
+            k_rx_force<<<g, 128, 0, s>>>(R, (int)n, d_pos, d_pf, perm, cs, d_acc, d_amax + it);
+            k_rx_move<<<g, 128, 0, s>>>(R, (int)n, d_pos, d_pf, d_acc, d_amax + it);
             e = cudaGetLastError();
         }
     }
@@ -245,7 +296,7 @@ extern "C" sph_status sph_relax(const sph_relax_config* cfg, int64_t n, double* 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(am.data(), d_amax, sizeof(unsigned long long) * (size_t)iterations,
                             cudaMemcpyDeviceToHost, s);
-    for (void* p : {(void*)d_pos, (void*)d_acc, (void*)d_phi, (void*)d_amax, (void*)keys, (void*)rank, (void*)tmp,
+    for (void* p : {(void*)d_pos, (void*)d_acc, (void*)d_pf, (void*)d_phi, (void*)d_amax, (void*)keys, (void*)rank, (void*)tmp,
                     (void*)perm, (void*)cnt, (void*)cs, (void*)blk})
         if (p) cudaFreeAsync(p, s);
     const cudaError_t e2 = cudaStreamSynchronize(s);
