@@ -336,6 +336,16 @@ def next_rows_line(args):
     out["contact_factor"] = {"particles": int(np.count_nonzero(body >= 0)),
                              "where": "pass VT, every advection step (gear_bath.per_launch_ms.pass_VT)"}
     out["gear_pair"] = timed(W.gear_pair(dx=0.75e-3))
+    # the plain method in FP64 (pair_precision = 1): the still tank at full
+    # size, and the gear bath's geometry at dx = 1.5 mm beside its FP32 run
+    tank = W.still_tank()
+    tank.config = dict(tank.config, pair_precision=1)
+    out["fp64_still_tank"] = timed(tank)
+    g32 = W.gear_bath(dx=1.5e-3, omega=args.omega, depth_frac=0.5, mu=0.1)
+    out["fp32_gear_bath_1p5mm"] = timed(g32)
+    g64 = W.gear_bath(dx=1.5e-3, omega=args.omega, depth_frac=0.5, mu=0.1)
+    g64.config = dict(g64.config, pair_precision=1)
+    out["fp64_gear_bath_1p5mm"] = timed(g64)
     rb = W.relax_body("sphere", size=40e-3, dx=1e-3)
     args_r = (rb["pos"], rb["dx"], rb["h_over_dx"], rb["phi"], rb["phi_origin"], rb["phi_spacing"])
     sph.sph_relax(*args_r, 2, stream=stream.cuda_stream)  # warm-up
