@@ -1,7 +1,9 @@
 """The 2M-oil gear bath of the bench, in the launch configuration bench.py
 times (autotuned pair-pass variant): pair sets of a seeded sample of
 particles checked bit-exact against the oracle's brute-force search over all
-2.8M snapshot positions, plus pair symmetry on the sample."""
+2.8M snapshot positions, plus pair symmetry on the sample; and, at the same
+particle count, a property that holds at any size: a periodic lattice moving
+as a rigid whole keeps its velocity (Galilean invariance)."""
 import numpy as np
 import pytest
 
@@ -49,4 +51,30 @@ def test_gear_bath_2m_sampled_pair_sets(sph, oracle):
         for j in got[:8]:
             assert i in lst[start[j]:start[j + 1]]
     assert counts[idx].sum() == rc.sum() > 50 * len(idx)
+    ctx.close()
+
+
+def test_galilean_invariance_at_full_size(sph):
+    # a perfect periodic lattice of 140^3 = 2,744,000 particles (the bench's
+    # particle count) moving as a rigid whole, in the pair-pass variant the
+    # autotuner picks on the bench: it keeps its velocity and is carried by
+    # it, within the field-parity norm 1e-5 (k + 1) of u_ref and dx
+    n, steps, dx = 140, 5, 1e-3
+    v0 = np.array([0.3, -0.2, 0.1])
+    idx = W._grid((0, 0, 0), (n, n, n))
+    pos = (idx + 0.5) * dx
+    cfg = W._cfg(origin=(0, 0, 0), extent=(n * dx,) * 3, dx=dx, c0=10.0, gravity=(0, 0, 0), periodic_mask=0b111)
+    case = W.Case("translating_lattice_full", cfg, {0: W._mat(1000.0, 0.02, 0.6, 4000.0, 300.0)},
+                  [dict(mat=0, pos=pos, vel=np.tile(v0, (len(pos), 1)), T=None, rho=None)], [])
+    ctx = sph.from_case(case, stream=0)
+    for key, val in (("list_batch", 2), ("tpp", 1), ("block", 128)):
+        ctx.sph_set_tuning(key, val)
+    ctx.sph_step(steps)
+    t = ctx.sph_get_info()["t"]
+    v = ctx.sph_read_fields("vel")
+    d = ctx.sph_read_fields("pos") - (pos + v0 * t)
+    d -= n * dx * np.round(d / (n * dx))
+    ev, ex = np.abs(v - v0).max() / cfg["u_ref"], np.abs(d).max() / dx
+    print(f"TRANSLATION n={n ** 3} steps={steps} vel={ev:.2e} pos={ex:.2e}")
+    assert ev <= 1e-5 * (steps + 1) and ex <= 1e-5 * (steps + 1)
     ctx.close()
