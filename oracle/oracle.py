@@ -61,6 +61,9 @@ def lib():
         L.orc_relax.restype = C.c_int
         L.orc_relax.argtypes = [C.POINTER(OrcRelaxConfig), I64, PD, C.c_int, PD]
         L.orc_neighbors_of.restype = I64
+        L.orc_sample_vt.restype = C.c_int
+        L.orc_sample_vt.argtypes = [I64, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, C.c_int, PD,
+                                    I64, PI64, PD, PD]
         L.orc_neighbors_of.argtypes = [I64, PD, D, C.c_int, PD, I64, PI64, PI64, PI32, I64]
         L.orc_cell_order.argtypes = [I64, PD, PD, PD, PI, PI64, PI64]
         L.orc_create.restype = C.c_void_p; L.orc_create.argtypes = [C.POINTER(OrcConfig)]
@@ -176,6 +179,33 @@ def neighbors_of(pos, R2, idx, periodic_mask=0, extent=(0, 0, 0)):
                                  lst.ctypes.data_as(PI32), total)
     assert got == total
     return counts, lst[:total]
+
+
+def sample_vt(pos, vel, rho, T, kind, mat, materials, dx, h, free_surface, idx, periodic_mask=0,
+              extent=(0, 0, 0)):
+    """Passes D, V and T of the fluid particles idx only, from the whole state
+    at the start of an advection step (brute force at any size; see
+    orc_sample_vt): (a_visc[m, 3], dT/dt[m])."""
+    n = len(pos)
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = np.ascontiguousarray(vel, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    T = np.ascontiguousarray(T, np.float64)
+    kind = np.ascontiguousarray(kind, np.int32)
+    mat = np.ascontiguousarray(mat, np.int32)
+    idx = np.ascontiguousarray(idx, np.int64)
+    nm = max(materials) + 1
+    mats = (OrcMaterial * nm)()
+    for k, m in materials.items():
+        mats[k] = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])
+    ext = np.ascontiguousarray(extent, np.float64)
+    av = np.zeros((len(idx), 3))
+    dT = np.zeros(len(idx))
+    rc = lib().orc_sample_vt(n, _pd(pos), _pd(vel), _pd(rho), _pd(T), kind.ctypes.data_as(PI),
+                             mat.ctypes.data_as(PI), mats, float(dx), float(h), int(free_surface),
+                             int(periodic_mask), _pd(ext), len(idx), idx.ctypes.data_as(PI64), _pd(av), _pd(dT))
+    assert rc == 0, "sample_vt: an index is out of range or not a fluid particle"
+    return av, dT
 
 
 def cell_order(pos, origin, cellw, ncell):

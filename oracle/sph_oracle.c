@@ -826,6 +826,73 @@ int orc_time(const orc_sim* S, double* t, int64_t* adv, int64_t* sub, double* dt
 int64_t orc_count(const orc_sim* S) { return S->n; }
 
 /* ------------------------------------------------------------------------ */
+/* Pass D and passes V/T of sampled fluid particles at any size.  The whole
+ * state at the start of an advection step is given (positions = the frozen
+ * snapshot, solids already placed, their velocities the wall velocities;
+ * fluid densities before re-initialisation).  For each sampled fluid particle
+ * i: its partners by brute force over all particles (the strict FP64 rule);
+ * the re-initialised density (Eq. 14, or Eq. 15 when free_surface = 0) of i
+ * and of each fluid partner, each from its own kernel sum over its own
+ * brute-force partners (self and walls included); then the viscous
+ * acceleration (Eq. 10 second term; Eq. 18 with the fluid's viscosity on
+ * walls) and dT/dt by the Cleary form (Eq. 22), exactly as orc_step's
+ * passes D, V and T compute them.  O(samples x partners x n): for checking a
+ * few particles of a workload far beyond the stepper's O(N^2). */
+static double reinit_rho(int64_t n, const double* pos, const double* rho, const int* mat_id,
+                         const orc_material* mats, double R2, double h, double sigma0, int free_surface,
+                         int periodic_mask, const double* extent, int64_t i) {
+    double s = orc_W(0.0, h);
+    for (int64_t j = 0; j < n; ++j) {
+        double rv[3];
+        const double r2 = dist2(pos + 3 * i, pos + 3 * j, periodic_mask, extent, rv);
+        if (r2 > 0.0 && r2 < R2) s += orc_W(sqrt(r2), h);
+    }
+    const double rr = mats[mat_id[i]].rho0 * s / sigma0;
+    return free_surface ? (rho[i] > rr ? rho[i] : rr) : rr;
+}
+
+int orc_sample_vt(int64_t n, const double* pos, const double* vel, const double* rho, const double* T,
+                  const int* kind, const int* mat_id, const orc_material* mats, double dx, double h,
+                  int free_surface, int periodic_mask, const double* extent, int64_t m, const int64_t* idx,
+                  double* av, double* dTdt) {
+    const double R2 = 4.0 * h * h, vol = dx * dx * dx, sigma0 = orc_sigma0(dx, h);
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        if (i < 0 || i >= n || kind[i] != 0) { bad = 1; continue; }
+        const orc_material* Mi = &mats[mat_id[i]];
+        const double rho_i = reinit_rho(n, pos, rho, mat_id, mats, R2, h, sigma0, free_surface, periodic_mask,
+                                        extent, i);
+        double a[3] = {0.0, 0.0, 0.0}, sT = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double rv[3];
+            const double r2 = dist2(pos + 3 * i, pos + 3 * j, periodic_mask, extent, rv);
+            if (!(r2 > 0.0 && r2 < R2)) continue;
+            const double r = sqrt(r2), dW = orc_dW(r, h);
+            const orc_material* Mj = &mats[mat_id[j]];
+            double Vj, eta;
+            if (kind[j] == 0) {
+                const double rho_j = reinit_rho(n, pos, rho, mat_id, mats, R2, h, sigma0, free_surface,
+                                                periodic_mask, extent, j);
+                Vj = Mj->rho0 * vol / rho_j;
+                eta = (Mi->mu + Mj->mu > 0.0) ? 2.0 * Mi->mu * Mj->mu / (Mi->mu + Mj->mu) : 0.0;
+            } else {
+                Vj = vol;
+                eta = Mi->mu; /* READING: the wall takes the fluid's viscosity (Eq. 18) */
+            }
+            const double c = 2.0 * Vj / rho_i * eta / r * dW;
+            for (int k = 0; k < 3; ++k) a[k] += c * (vel[3 * i + k] - vel[3 * j + k]);
+            const double K = (Mi->k + Mj->k > 0.0) ? 4.0 * Mi->k * Mj->k / (Mi->k + Mj->k) : 0.0;
+            sT += Vj * K * (T[i] - T[j]) / r * dW;
+        }
+        for (int k = 0; k < 3; ++k) av[3 * q + k] = a[k];
+        dTdt[q] = sT / (rho_i * Mi->cp);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Physics-driven particle relaxation (Sec. 2.2).  Particles move under the
  * constant background pressure p0 (scale-free: p0 / rho0 = 1),
  *   F_p,i = -(2 / m_i) sum_j V_i V_j p0 grad_i W_ij = -2 sum_j V_j W'(r) e_ij,

@@ -71,6 +71,15 @@ int64_t orc_neighbors_of(int64_t n, const double* pos, double R2, int periodic_m
                          int64_t m, const int64_t* idx, int64_t* counts, int32_t* list, int64_t cap);
 int64_t orc_neighbors(int64_t n, const double* pos, double R2, int periodic_mask,
                       const double* extent, int64_t* counts, int32_t* list, int64_t cap);
+/* passes D, V and T of the fluid particles idx[0..m) only, from the whole
+ * state at the start of an advection step (brute force, any size):
+ * av[3m] viscous accelerations (Eqs. 10, 18), dTdt[m] (Eq. 22), with the
+ * re-initialised densities of Eq. (14) (free_surface = 1) or (15).  Returns
+ * -1 if an index is out of range or not a fluid particle. */
+int orc_sample_vt(int64_t n, const double* pos, const double* vel, const double* rho, const double* T,
+                  const int* kind, const int* mat_id, const orc_material* mats, double dx, double h,
+                  int free_surface, int periodic_mask, const double* extent, int64_t m, const int64_t* idx,
+                  double* av, double* dTdt);
 /* expected cell order: key = linear cell index (x fastest) of
  * floor((x - origin)/w) per axis, clamped to the grid; particles sorted by
  * (key, id).  perm[k] = id at sorted position k; cell_start has ncell+1. */

@@ -1,7 +1,9 @@
 """The 2M-oil gear bath of the bench, in the launch configuration bench.py
 times (autotuned pair-pass variant): pair sets of a seeded sample of
 particles checked bit-exact against the oracle's brute-force search over all
-2.8M snapshot positions, plus pair symmetry on the sample; and, at the same
+2.8M snapshot positions, plus pair symmetry on the sample; the held viscous
+acceleration and dT/dt of sampled oil particles against the oracle's
+brute-force passes D, V and T on the same state; and, at the same
 particle count, a property that holds at any size: a periodic lattice moving
 as a rigid whole keeps its velocity (Galilean invariance)."""
 import numpy as np
@@ -78,3 +80,40 @@ def test_galilean_invariance_at_full_size(sph):
     print(f"TRANSLATION n={n ** 3} steps={steps} vel={ev:.2e} pos={ex:.2e}")
     assert ev <= 1e-5 * (steps + 1) and ex <= 1e-5 * (steps + 1)
     ctx.close()
+
+
+def test_gear_bath_2m_sampled_viscous_and_heat(sph, oracle):
+    # passes D, V and T at full size, in the bench's launch configuration: the
+    # whole state read back at the start of an advection step, then that
+    # step's held viscous acceleration (Eqs. 10, 18) and dT/dt (Eq. 22) of 32
+    # oil particles (16 in the bulk, 16 beside the hot rotating gear) against
+    # the oracle's brute-force passes on the same state (its own kernel sums
+    # for the re-initialised densities, Eq. 14), within the field-parity norm
+    # 1e-5 relative to max(|x_ref|, s), s the largest sampled magnitude (and g
+    # for the acceleration)
+    from scipy.spatial import cKDTree
+    case = W.gear_bath(dx=1e-3, omega=600.0)
+    ctx = sph.from_case(case, stream=0)
+    for key, val in (("list_batch", 2), ("tpp", 1), ("block", 128)):
+        ctx.sph_set_tuning(key, val)
+    ctx.sph_step(3)
+    pos, vel, rho, T = (ctx.sph_read_fields(k) for k in ("pos", "vel", "rho", "T"))
+    ctx.sph_step(1)
+    av, dT = ctx.sph_read_fields("a_visc"), ctx.sph_read_fields("dTdt")
+    ctx.close()
+    f = W.flatten(case)
+    fluid = np.flatnonzero(f["kind"] == 0)
+    gear = np.flatnonzero(f["body"] >= 0)
+    near = fluid[cKDTree(pos[gear]).query(pos[fluid], distance_upper_bound=2e-3)[0] < 2e-3]
+    rng = np.random.default_rng(21)
+    idx = np.sort(np.concatenate([rng.choice(fluid, 16, replace=False), rng.choice(near, 16, replace=False)]))
+    cfg = case.config
+    ref_av, ref_dT = oracle.sample_vt(pos, vel, rho, T, f["kind"], f["mat"], case.materials, cfg["dx"],
+                                      cfg["h_over_dx"] * cfg["dx"], cfg["free_surface"], idx)
+    s_a = max(9.81, np.abs(ref_av).max())
+    s_T = np.abs(ref_dT).max()
+    ea = np.abs(av[idx] - ref_av).max(1) / np.maximum(np.abs(ref_av).max(1), s_a)
+    eT = np.abs(dT[idx] - ref_dT) / np.maximum(np.abs(ref_dT), s_T)
+    print(f"SAMPLED_VT a_visc={ea.max():.2e} dTdt={eT.max():.2e} s_a={s_a:.3g} s_T={s_T:.3g}")
+    assert s_T > 0.0
+    assert ea.max() <= 1e-5 and eT.max() <= 1e-5

@@ -827,3 +827,39 @@ def test_head_on_pair_is_symmetric_and_repels(oracle):
         assert v[0, 0] == -v[1, 0] and abs(v[0, 0]) < u
         assert x[0, 0] + x[1, 0] == pytest.approx(0.1, rel=1e-15)
         assert np.all(v[:, 1:] == 0.0) and np.all(x[:, 1:] == 0.05)
+
+
+def _initial_state(case):
+    # the whole state at the start of the first advection step, in id order:
+    # solids at their reference positions (angle 0), wall velocities omega x (r - c)
+    f = W.flatten(case)
+    rho0 = np.array([case.materials[m]["rho0"] for m in f["mat"]])
+    rho = np.where(np.isnan(f["rho"]), rho0, f["rho"])
+    vel = f["vel"].copy()
+    for b, B in case.bodies.items():
+        sel = f["body"] == b
+        w = B["omega"] * np.asarray(B["axis"], float)
+        vel[sel] = np.cross(w, f["pos"][sel] - np.asarray(B["center"], float))
+    return f, vel, rho
+
+
+def test_sampled_passes_match_the_stepper(oracle):
+    # the sampled passes D, V, T (brute force, for full-size checks) against
+    # the stepper's own first advection step on the gear bath's geometry at
+    # dx = 5 mm: oil beside the static walls, beside the hot rotating gear,
+    # and in the bulk
+    case = W.gear_bath(dx=5e-3, omega=600.0)
+    f, vel, rho = _initial_state(case)
+    fluid = np.flatnonzero(f["kind"] == 0)
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(fluid, 24, replace=False))
+    cfg = case.config
+    h = cfg["h_over_dx"] * cfg["dx"]
+    av, dT = oracle.sample_vt(f["pos"], vel, rho, f["T"], f["kind"], f["mat"], case.materials, cfg["dx"], h,
+                              cfg["free_surface"], idx)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    ref_av, ref_dT = sim.field("a_visc")[idx], sim.field("dTdt")[idx]
+    assert np.abs(ref_av).max() > 0 and np.abs(ref_dT).max() > 0
+    assert np.allclose(av, ref_av, rtol=1e-12, atol=1e-12 * np.abs(ref_av).max())
+    assert np.allclose(dT, ref_dT, rtol=1e-12, atol=1e-12 * np.abs(ref_dT).max())
