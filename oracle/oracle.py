@@ -61,6 +61,9 @@ def lib():
         L.orc_relax.restype = C.c_int
         L.orc_relax.argtypes = [C.POINTER(OrcRelaxConfig), I64, PD, C.c_int, PD]
         L.orc_neighbors_of.restype = I64
+        L.orc_sample_ap.restype = C.c_int
+        L.orc_sample_ap.argtypes = [I64, PD, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, PD, D,
+                                    C.c_int, D, C.c_int, PD, I64, PI64, PD]
         L.orc_sample_vt.restype = C.c_int
         L.orc_sample_vt.argtypes = [I64, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, C.c_int, PD,
                                     I64, PI64, PD, PD]
@@ -206,6 +209,30 @@ def sample_vt(pos, vel, rho, T, kind, mat, materials, dx, h, free_surface, idx, 
                              int(periodic_mask), _pd(ext), len(idx), idx.ctypes.data_as(PI64), _pd(av), _pd(dT))
     assert rc == 0, "sample_vt: an index is out of range or not a fluid particle"
     return av, dT
+
+
+def sample_ap(pos, vel, rho, drho, nrm, kind, mat, materials, dx, h, free_surface, gravity, c0, dt, idx,
+              wall_pstar_printed=0, periodic_mask=0, extent=(0, 0, 0)):
+    """Pass M of the fluid particles idx only, for the first acoustic sub-step
+    (size dt) of an advection step, from the whole state at its start (see
+    orc_sample_ap): the pressure acceleration ap[m, 3]."""
+    n = len(pos)
+    arr = [np.ascontiguousarray(a, np.float64) for a in (pos, vel, rho, drho, nrm)]
+    kind = np.ascontiguousarray(kind, np.int32)
+    mat = np.ascontiguousarray(mat, np.int32)
+    idx = np.ascontiguousarray(idx, np.int64)
+    nm = max(materials) + 1
+    mats = (OrcMaterial * nm)()
+    for k, m in materials.items():
+        mats[k] = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])
+    g = np.ascontiguousarray(gravity, np.float64)
+    ext = np.ascontiguousarray(extent, np.float64)
+    ap = np.zeros((len(idx), 3))
+    rc = lib().orc_sample_ap(n, *[_pd(a) for a in arr], kind.ctypes.data_as(PI), mat.ctypes.data_as(PI), mats,
+                             float(dx), float(h), int(free_surface), _pd(g), float(c0), int(wall_pstar_printed),
+                             float(dt), int(periodic_mask), _pd(ext), len(idx), idx.ctypes.data_as(PI64), _pd(ap))
+    assert rc == 0, "sample_ap: an index is out of range or not a fluid particle"
+    return ap
 
 
 def cell_order(pos, origin, cellw, ncell):

@@ -892,6 +892,61 @@ int orc_sample_vt(int64_t n, const double* pos, const double* vel, const double*
     return bad ? -1 : 0;
 }
 
+/* Pass M of sampled fluid particles at any size, for the first acoustic
+ * sub-step of an advection step: the densities re-initialised (Eq. 14/15,
+ * as orc_sample_vt) and half-kicked with the given drho (rho += dt/2 drho),
+ * the EoS (Eq. 2), then the pressure acceleration of Eqs. (10)-(12) over
+ * fluid partners and Eqs. (16)-(19) over wall partners (n_w the wall
+ * normals, the wall velocities in vel), as orc_step's pass M computes it.
+ * The held viscous acceleration and gravity are not included. */
+int orc_sample_ap(int64_t n, const double* pos, const double* vel, const double* rho, const double* drho,
+                  const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
+                  double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed, double dt,
+                  int periodic_mask, const double* extent, int64_t m, const int64_t* idx, double* ap) {
+    const double R2 = 4.0 * h * h, vol = dx * dx * dx, sigma0 = orc_sigma0(dx, h), c02 = c0 * c0;
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        if (i < 0 || i >= n || kind[i] != 0) { bad = 1; continue; }
+        const double r0i = mats[mat_id[i]].rho0;
+        double rho_i = reinit_rho(n, pos, rho, mat_id, mats, R2, h, sigma0, free_surface, periodic_mask, extent, i);
+        rho_i += 0.5 * dt * drho[i];
+        const double p_i = c02 * (rho_i - r0i);
+        double a[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            double rv[3];
+            const double r2 = dist2(pos + 3 * i, pos + 3 * j, periodic_mask, extent, rv);
+            if (!(r2 > 0.0 && r2 < R2)) continue;
+            const double r = sqrt(r2), dW = orc_dW(r, h);
+            double e[3];
+            for (int k = 0; k < 3; ++k) e[k] = rv[k] / r;
+            double pstar, Ustar, Vj;
+            if (kind[j] == 0) {
+                double rho_j = reinit_rho(n, pos, rho, mat_id, mats, R2, h, sigma0, free_surface, periodic_mask,
+                                          extent, j);
+                rho_j += 0.5 * dt * drho[j];
+                const double p_j = c02 * (rho_j - mats[mat_id[j]].rho0);
+                const double UL = -dot3(vel + 3 * i, e), UR = -dot3(vel + 3 * j, e);
+                orc_riemann(rho_i, UL, p_i, rho_j, UR, p_j, c0, &Ustar, &pstar);
+                Vj = mats[mat_id[j]].rho0 * vol / rho_j;
+            } else {
+                /* r_fw = r_w - r_f = -r_ij */
+                const double g_rfw = -dot3(gravity, rv);
+                const double UL = -dot3(nrm + 3 * j, vel + 3 * i), uw = -dot3(nrm + 3 * j, vel + 3 * j);
+                double UR, PR, rhoR;
+                orc_wall_riemann(rho_i, UL, p_i, uw, g_rfw, r0i, c0, wall_pstar_printed, &UR, &PR, &rhoR, &Ustar,
+                                 &pstar);
+                Vj = vol;
+            }
+            const double c = -2.0 * Vj / rho_i * pstar * dW;
+            for (int k = 0; k < 3; ++k) a[k] += c * e[k];
+        }
+        for (int k = 0; k < 3; ++k) ap[3 * q + k] = a[k];
+    }
+    return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Physics-driven particle relaxation (Sec. 2.2).  Particles move under the
  * constant background pressure p0 (scale-free: p0 / rho0 = 1),

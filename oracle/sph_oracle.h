@@ -80,6 +80,14 @@ int orc_sample_vt(int64_t n, const double* pos, const double* vel, const double*
                   const int* kind, const int* mat_id, const orc_material* mats, double dx, double h,
                   int free_surface, int periodic_mask, const double* extent, int64_t m, const int64_t* idx,
                   double* av, double* dTdt);
+/* pass M of the fluid particles idx[0..m) for the first acoustic sub-step
+ * (size dt) of an advection step, from the same state plus drho and the wall
+ * normals: ap[3m] the pressure acceleration (Eqs. 10-12, 16-19; without the
+ * held viscous term and gravity).  -1 as orc_sample_vt. */
+int orc_sample_ap(int64_t n, const double* pos, const double* vel, const double* rho, const double* drho,
+                  const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
+                  double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed, double dt,
+                  int periodic_mask, const double* extent, int64_t m, const int64_t* idx, double* ap);
 /* expected cell order: key = linear cell index (x fastest) of
  * floor((x - origin)/w) per axis, clamped to the grid; particles sorted by
  * (key, id).  perm[k] = id at sorted position k; cell_start has ncell+1. */

@@ -3,7 +3,8 @@ times (autotuned pair-pass variant): pair sets of a seeded sample of
 particles checked bit-exact against the oracle's brute-force search over all
 2.8M snapshot positions, plus pair symmetry on the sample; the held viscous
 acceleration and dT/dt of sampled oil particles against the oracle's
-brute-force passes D, V and T on the same state; and, at the same
+brute-force passes D, V and T on the same state; the velocity kick of pass M
+(one acoustic sub-step per step) against the oracle's sampled passes; and, at the same
 particle count, a property that holds at any size: a periodic lattice moving
 as a rigid whole keeps its velocity (Galilean invariance)."""
 import numpy as np
@@ -117,3 +118,49 @@ def test_gear_bath_2m_sampled_viscous_and_heat(sph, oracle):
     print(f"SAMPLED_VT a_visc={ea.max():.2e} dTdt={eT.max():.2e} s_a={s_a:.3g} s_T={s_T:.3g}")
     assert s_T > 0.0
     assert ea.max() <= 1e-5 and eT.max() <= 1e-5
+
+
+def test_gear_bath_2m_sampled_pressure_kick(sph, oracle):
+    # pass M at full size, in the bench's launch configuration, with one
+    # acoustic sub-step per advection step: the state read back at the start
+    # of a step (the gear's particles at their current angle, with normals and
+    # wall velocities; drho for the half kick), then the velocities after that
+    # step against v + dt (a_p + a_visc + g) from the oracle's brute-force
+    # passes (pressure: Eqs. 10-12, 16-19; viscous: Eqs. 10, 18) for 32 oil
+    # particles, 16 of them beside the rotating gear.  Bound: 1e-5 of the
+    # largest sampled velocity change, plus the FP32 rounding of the stored
+    # velocity (2^-24 |v|)
+    from scipy.spatial import cKDTree
+    case = W.gear_bath(dx=1e-3, omega=600.0)
+    case.config = dict(case.config, max_substeps=1)
+    ctx = sph.from_case(case, stream=0)
+    for key, val in (("list_batch", 2), ("tpp", 1), ("block", 128)):
+        ctx.sph_set_tuning(key, val)
+    ctx.sph_step(3)
+    t0 = ctx.sph_get_info()["t"]
+    pos, vel, rho, drho, T, nrm = (ctx.sph_read_fields(k) for k in ("pos", "vel", "rho", "drho", "T", "normal"))
+    ctx.sph_step(1)
+    dt = ctx.sph_get_info()["t"] - t0
+    v2, x2 = ctx.sph_read_fields("vel"), ctx.sph_read_fields("pos")
+    ctx.close()
+    f = W.flatten(case)
+    fluid = np.flatnonzero(f["kind"] == 0)
+    gear = np.flatnonzero(f["body"] >= 0)
+    near = fluid[cKDTree(pos[gear]).query(pos[fluid], distance_upper_bound=2e-3)[0] < 2e-3]
+    rng = np.random.default_rng(22)
+    idx = np.sort(np.concatenate([rng.choice(fluid, 16, replace=False), rng.choice(near, 16, replace=False)]))
+    cfg = case.config
+    h = cfg["h_over_dx"] * cfg["dx"]
+    ap = oracle.sample_ap(pos, vel, rho, drho, nrm, f["kind"], f["mat"], case.materials, cfg["dx"], h,
+                          cfg["free_surface"], cfg["gravity"], cfg["c0"], dt, idx)
+    av, _ = oracle.sample_vt(pos, vel, rho, T, f["kind"], f["mat"], case.materials, cfg["dx"], h,
+                             cfg["free_surface"], idx)
+    dv = dt * (ap + av + np.asarray(cfg["gravity"]))
+    v_ref = vel[idx] + dv
+    x_ref = pos[idx] + 0.5 * dt * (vel[idx] + v_ref)
+    bound = 1e-5 * np.abs(dv).max() + 2.0 ** -24 * np.abs(v_ref)
+    ev = np.abs(v2[idx] - v_ref)
+    print(f"SAMPLED_M dv_max={np.abs(dv).max():.3g} err/bound={np.max(ev / bound):.2e} "
+          f"err/dv_max={ev.max() / np.abs(dv).max():.2e} x={np.abs(x2[idx] - x_ref).max() / cfg['dx']:.2e}")
+    assert np.all(ev <= bound)
+    assert np.abs(x2[idx] - x_ref).max() <= 1e-5 * cfg["dx"]

@@ -863,3 +863,51 @@ def test_sampled_passes_match_the_stepper(oracle):
     assert np.abs(ref_av).max() > 0 and np.abs(ref_dT).max() > 0
     assert np.allclose(av, ref_av, rtol=1e-12, atol=1e-12 * np.abs(ref_av).max())
     assert np.allclose(dT, ref_dT, rtol=1e-12, atol=1e-12 * np.abs(ref_dT).max())
+
+
+def _rotate(axis, th, d):
+    # Rodrigues' rotation of the rows of d by th about the unit axis
+    a = np.asarray(axis, float)
+    c, s = math.cos(th), math.sin(th)
+    return d * c + np.cross(a, d) * s + np.outer(d @ a, a) * (1.0 - c)
+
+
+def test_sampled_pressure_pass_matches_the_stepper(oracle):
+    # the sampled pass M (brute force, for full-size checks) against the
+    # stepper's second advection step, run with one acoustic sub-step per
+    # step so that the step's velocity change is dt (a_p + a_visc + g): the
+    # state at the step's start is the first step's result, with the gear
+    # turned to omega t1 (positions, normals and wall velocities), and drho
+    # the first step's continuity rate for the second step's half kick
+    case = W.gear_bath(dx=5e-3, omega=600.0)
+    case.config = dict(case.config, max_substeps=1)
+    f = W.flatten(case)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    t1 = sim.time()["t"]
+    pos, vel, rho, drho, T = (sim.field(k).copy() for k in ("pos", "vel", "rho", "drho", "T"))
+    nrm = f["normal"].copy()
+    for b, B in case.bodies.items():
+        sel = f["body"] == b
+        c = np.asarray(B["center"], float)
+        pos[sel] = c + _rotate(B["axis"], B["omega"] * t1, f["pos"][sel] - c)
+        nrm[sel] = _rotate(B["axis"], B["omega"] * t1, f["normal"][sel])
+        vel[sel] = np.cross(B["omega"] * np.asarray(B["axis"], float), pos[sel] - c)
+    sim.step(1)
+    dt = sim.time()["t"] - t1
+    v2, av2, dT2 = sim.field("vel"), sim.field("a_visc"), sim.field("dTdt")
+    fluid = np.flatnonzero(f["kind"] == 0)
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(fluid, 24, replace=False))
+    cfg = case.config
+    h = cfg["h_over_dx"] * cfg["dx"]
+    ap = oracle.sample_ap(pos, vel, rho, drho, nrm, f["kind"], f["mat"], case.materials, cfg["dx"], h,
+                          cfg["free_surface"], cfg["gravity"], cfg["c0"], dt, idx)
+    ref_ap = (v2[idx] - vel[idx]) / dt - av2[idx] - np.asarray(cfg["gravity"])
+    assert np.abs(ref_ap).max() > 1.0
+    assert np.allclose(ap, ref_ap, rtol=1e-8, atol=1e-8 * np.abs(ref_ap).max())
+    # and the sampled passes V and T on the same turned state
+    av, dT = oracle.sample_vt(pos, vel, rho, T, f["kind"], f["mat"], case.materials, cfg["dx"], h,
+                              cfg["free_surface"], idx)
+    assert np.allclose(av, av2[idx], rtol=1e-12, atol=1e-12 * np.abs(av2[idx]).max())
+    assert np.allclose(dT, dT2[idx], rtol=1e-12, atol=1e-12 * np.abs(dT2[idx]).max())
