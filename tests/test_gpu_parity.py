@@ -63,14 +63,25 @@ def test_neighbor_sets_bit_exact(sph, oracle, name, make):
     assert np.array_equal(lst, ref_lst)
 
 
+def _sort_grid(case):
+    # the sort-cell grid fixed by the configuration: geometry cells of width
+    # >= 2h per axis (at least one), split 8 ways along x and 2 along y, z
+    cfg = case.config
+    R = 2.0 * cfg["h_over_dx"] * cfg["dx"]
+    ncell = [s * max(1, int(np.floor(e / R))) for s, e in zip((8, 2, 2), cfg["extent"])]
+    return [e / n for e, n in zip(cfg["extent"], ncell)], ncell
+
+
 @pytest.mark.parametrize("name,make", NEIGHBOR_CASES[:4], ids=[c[0] for c in NEIGHBOR_CASES[:4]])
 def test_cell_order_bit_exact(sph, oracle, name, make):
     case = make()
     ctx = _ctx(sph, case, steps=1)  # the first step sorts the initial positions
     info = ctx.sph_get_info()
+    width, ncell = _sort_grid(case)
+    assert list(info["ncell"]) == ncell and list(info["cell_width"]) == width
     perm = ctx.sph_read_cell_order()
     f = W.flatten(case)
-    ref, _ = oracle.cell_order(f["pos"], case.config["origin"], info["cell_width"], info["ncell"])
+    ref, _ = oracle.cell_order(f["pos"], case.config["origin"], width, ncell)
     assert np.array_equal(perm, ref)
 
 
@@ -81,10 +92,12 @@ def test_cell_boundaries_order_and_pairs_bit_exact(sph, oracle):
     case = W.cell_boundaries()
     ctx = _ctx(sph, case, steps=1)
     info = ctx.sph_get_info()
-    assert list(info["cell_width"]) == list(case.meta["sort_cell_width"])
+    width, ncell = _sort_grid(case)
+    assert list(info["cell_width"]) == list(case.meta["sort_cell_width"]) == width
+    assert list(info["ncell"]) == ncell
     perm = ctx.sph_read_cell_order()
     f = W.flatten(case)
-    ref, _ = oracle.cell_order(f["pos"], case.config["origin"], info["cell_width"], info["ncell"])
+    ref, _ = oracle.cell_order(f["pos"], case.config["origin"], width, ncell)
     assert np.array_equal(perm, ref)
     counts, lst = ctx.sph_read_neighbors()
     ref_counts, ref_lst = oracle.neighbors(f["pos"], case.support_radius() ** 2)
