@@ -133,13 +133,24 @@ def test_gear_bath_2m_sampled_pressure_kick(sph, oracle):
     case.config = dict(case.config, max_substeps=1)
     ctx = _ctx(sph, case)
     ctx.sph_step(1)
-    dt = ctx.sph_get_info()["t"]
+    t1 = ctx.sph_get_info()["t"]
     v1, x1 = ctx.sph_read_fields("vel"), ctx.sph_read_fields("pos")
     ctx.close()
     f, vel, rho = _initial_state(case)
     idx = _sample(f, 16, 22)
     cfg = case.config
     h = cfg["h_over_dx"] * cfg["dx"]
+    # the step size from the oracle's rules (Eqs. 25, 26): the oil is at rest,
+    # so the one sub-step is min(dt_ac, dt_ad, the thermal bound)
+    mats = case.materials
+    fl_mats = set(f["mat"][f["kind"] == 0].tolist())
+    nu_max = max(mats[m]["mu"] / mats[m]["rho0"] for m in fl_mats)
+    dt_ad, dt_ac = oracle.timesteps(h, 0.0, cfg["u_ref"], nu_max, cfg["c0"], cfg["cfl_ad"], cfg["cfl_ac"])
+    heated = fl_mats | {m for m in mats if not mats[m]["fixed_T"]}
+    dt_T = min([oracle.dt_thermal(mats[m]["rho0"], mats[m]["cp"], h, mats[m]["k"], cfg["cfl_T"])
+                for m in heated if mats[m]["k"] > 0] + [np.inf])
+    dt = min(dt_ac, dt_ad, dt_T)
+    assert t1 == pytest.approx(dt, rel=1e-6)
     drho0 = np.zeros(len(rho))  # no continuity rate before the first step
     ap = oracle.sample_ap(f["pos"], vel, rho, drho0, f["normal"], f["kind"], f["mat"], case.materials, cfg["dx"], h,
                           cfg["free_surface"], cfg["gravity"], cfg["c0"], dt, idx)
