@@ -68,7 +68,7 @@ STEP_FLOPS_PER_UNIT = 80 * (55 + 60)
 # Units: pass D and VT per partner found, M and C per directed fluid pair.
 # Valid only for the kernel sources they were taken on (hash below); after
 # any change to them the roofline reports traffic = null.
-TRAFFIC = {"sources_sha256_16": "5cb086cc328b1c42",
+TRAFFIC = {"sources_sha256_16": "df2cdc57fb6760fa",
            "bytes_per_unit": {"pass_D": 6.01, "pass_VT": 5.36, "pass_M": 6.20, "pass_C": 5.45}}
 KERNEL_SOURCES = ("paper_2512_09904_b300/csrc/sph_kernels.cu", "paper_2512_09904_b300/csrc/sph_internal.cuh",
                   "paper_2512_09904_b300/csrc/sph_kernels.cuh")

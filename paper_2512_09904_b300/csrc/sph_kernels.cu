@@ -1638,18 +1638,25 @@ cudaError_t launch_passD(const Bufs& B, int par, const PairTab& T, cudaStream_t 
         }                                                                                          \
     } while (0)
 
+template <bool UNI>
+static void launch_passVT_heat(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
+    const int blk = pair_block(B), grd = grid_1to1(B.n, blk);
+    switch (case_mode(B)) {
+    case CM_ONE: k_passVT<UNI, 2, 1, CM_ONE, true><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_ONE>(T)); break;
+    case CM_TAB: k_passVT<UNI, 2, 1, CM_TAB, true><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_TAB>(T)); break;
+    default: k_passVT<UNI, 2, 1, CM_GLOBAL, true><<<grd, blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T)); break;
+    }
+    k_passVT_ovf<UNI, true><<<kOvfGrid, 128, 0, s>>>(B, par);
+}
+
 cudaError_t launch_passVT(const Bufs& B, int par, const PairTab& T, cudaStream_t s) {
     if (B.fp64) return launch_passVT64(B, par, s);
     if (B.visc_heat) {
-        // cases with viscous-dissipation heating: one variant (8 entries per load, 1 thread per particle)
-        const int blk = pair_block(B);
-        if (B.uni_fluid) {
-            k_passVT<true, 8, 1, CM_GLOBAL, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T));
-            k_passVT_ovf<true, true><<<kOvfGrid, 128, 0, s>>>(B, par);
-        } else {
-            k_passVT<false, 8, 1, CM_GLOBAL, true><<<grid_1to1(B.n, blk), blk, 0, s>>>(B, par, pair_arg<CM_GLOBAL>(T));
-            k_passVT_ovf<false, true><<<kOvfGrid, 128, 0, s>>>(B, par);
-        }
+        // cases with viscous-dissipation heating: 2 entries per load and 1 thread
+        // per particle (the list batch changes no result), case constants from
+        // the parameter block where they fit
+        if (B.uni_fluid) launch_passVT_heat<true>(B, par, T, s);
+        else launch_passVT_heat<false>(B, par, T, s);
         return cudaGetLastError();
     }
     if (B.uni_fluid) {
