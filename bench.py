@@ -284,8 +284,11 @@ def next_rows_line(args):
     viscous-dissipation heating term (the gear bath stepped with and without
     it; its cost sits in pass VT), the contact factor of Eq. (24) (computed in
     pass VT for every rotating-body particle of the same run), the two-shaft
-    gear train at dx = 0.75 mm, and the particle relaxation of Sec. 2.2 (seeds
-    in a sphere, host arrays in and out, so its rate is end to end)."""
+    gear train at dx = 0.75 mm, the thermal dam break of 500k oil particles,
+    the plain FP64 method (the still tank at full size; the gear bath's
+    geometry at dx = 1.5 mm in FP32 and in FP64), and the particle relaxation
+    of Sec. 2.2 (seeds in a sphere, host arrays in and out, so its rate is end
+    to end)."""
     import numpy as np
     import torch
     from paper_2512_09904_b300 import sph, workloads as W
@@ -336,6 +339,7 @@ def next_rows_line(args):
     out["contact_factor"] = {"particles": int(np.count_nonzero(body >= 0)),
                              "where": "pass VT, every advection step (gear_bath.per_launch_ms.pass_VT)"}
     out["gear_pair"] = timed(W.gear_pair(dx=0.75e-3))
+    out["dam_break_500k"] = timed(W.dam_break(dx=2e-3))
     # the plain method in FP64 (pair_precision = 1): the still tank at full
     # size, and the gear bath's geometry at dx = 1.5 mm beside its FP32 run
     tank = W.still_tank()
