@@ -64,6 +64,9 @@ def lib():
         L.orc_sample_ap.restype = C.c_int
         L.orc_sample_ap.argtypes = [I64, PD, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, PD, D,
                                     C.c_int, D, C.c_int, PD, I64, PI64, PD]
+        L.orc_sample_substep.restype = C.c_int
+        L.orc_sample_substep.argtypes = [I64, PD, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, PD,
+                                         D, C.c_int, D, I64, PI64, PD, PD]
         L.orc_sample_vt.restype = C.c_int
         L.orc_sample_vt.argtypes = [I64, PD, PD, PD, PD, PI, PI, C.POINTER(OrcMaterial), D, D, C.c_int, C.c_int, PD,
                                     I64, PI64, PD, PD]
@@ -233,6 +236,31 @@ def sample_ap(pos, vel, rho, drho, nrm, kind, mat, materials, dx, h, free_surfac
                              float(dt), int(periodic_mask), _pd(ext), len(idx), idx.ctypes.data_as(PI64), _pd(ap))
     assert rc == 0, "sample_ap: an index is out of range or not a fluid particle"
     return ap
+
+
+def sample_substep(pos, vel, rho, drho, nrm, kind, mat, materials, dx, h, free_surface, gravity, c0, dt, idx,
+                   wall_pstar_printed=0):
+    """The first acoustic sub-step (size dt) of an advection step for the
+    fluid particles idx only (see orc_sample_substep; the arrays may be the
+    part of the state within three support radii of every sample): the
+    kicked velocities v_new[m, 3] and pass C's rates drho_new[m]."""
+    n = len(pos)
+    arr = [np.ascontiguousarray(a, np.float64) for a in (pos, vel, rho, drho, nrm)]
+    kind = np.ascontiguousarray(kind, np.int32)
+    mat = np.ascontiguousarray(mat, np.int32)
+    idx = np.ascontiguousarray(idx, np.int64)
+    nm = max(materials) + 1
+    mats = (OrcMaterial * nm)()
+    for k, m in materials.items():
+        mats[k] = OrcMaterial(m["rho0"], m["mu"], m["k"], m["cp"], m["T_init"], m["fixed_T"])
+    g = np.ascontiguousarray(gravity, np.float64)
+    v_new = np.zeros((len(idx), 3))
+    d_new = np.zeros(len(idx))
+    rc = lib().orc_sample_substep(n, *[_pd(a) for a in arr], kind.ctypes.data_as(PI), mat.ctypes.data_as(PI), mats,
+                                  float(dx), float(h), int(free_surface), _pd(g), float(c0), int(wall_pstar_printed),
+                                  float(dt), len(idx), idx.ctypes.data_as(PI64), _pd(v_new), _pd(d_new))
+    assert rc == 0, "sample_substep: an index is out of range or not a fluid particle"
+    return v_new, d_new
 
 
 def cell_order(pos, origin, cellw, ncell):

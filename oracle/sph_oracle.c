@@ -947,6 +947,146 @@ int orc_sample_ap(int64_t n, const double* pos, const double* vel, const double*
     return bad ? -1 : 0;
 }
 
+/* The first acoustic sub-step of an advection step for sampled fluid
+ * particles, at any size: from the whole state at the step's start, or any
+ * part of it that holds every particle within three support radii of each
+ * sample (a sample's pass C reads its partners' kicked velocities, their pass
+ * M reads their own partners' half-kicked densities, and those densities'
+ * re-initialisation reads the next ring's positions).  In the order of
+ * orc_step: re-initialised densities (Eq. 14/15), held viscous accelerations
+ * (Eqs. 10, 18), the half kick of density and the EoS (Eq. 2), the velocity
+ * kick of pass M (Eqs. 10-12, 16-19, plus g), then pass C's continuity rate
+ * (Eqs. 10, 13 in the adopted reading of v*; walls Eqs. 16-17).  Outputs per
+ * sample: the kicked velocity v_new[3] and the rate drho_new.  Work: one
+ * brute-force scan per particle of the three rings.  Non-periodic cases. */
+static int64_t partners_of(int64_t n, const double* pos, double R2, int64_t i, int64_t** buf, int64_t* cap) {
+    int64_t k = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        double rv[3];
+        const double r2 = dist2(pos + 3 * i, pos + 3 * j, 0, NULL, rv);
+        if (!(r2 > 0.0 && r2 < R2)) continue;
+        if (k == *cap) {
+            *cap = *cap ? 2 * *cap : 256;
+            *buf = (int64_t*)realloc(*buf, sizeof(int64_t) * (size_t)*cap);
+        }
+        (*buf)[k++] = j;
+    }
+    return k;
+}
+
+/* the members of ring r + 1 (flag bit r + 1) from the partners of ring r */
+static void next_ring(int64_t n, const double* pos, const int* kind, double R2, unsigned char* ring, int r) {
+    int64_t* buf = NULL;
+    int64_t cap = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(ring[i] & (1u << r)) || kind[i] != 0) continue;
+        const int64_t k = partners_of(n, pos, R2, i, &buf, &cap);
+        for (int64_t q = 0; q < k; ++q) ring[buf[q]] |= (unsigned char)(1u << (r + 1));
+    }
+    free(buf);
+}
+
+int orc_sample_substep(int64_t n, const double* pos, const double* vel, const double* rho, const double* drho,
+                       const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
+                       double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed,
+                       double dt, int64_t m, const int64_t* idx, double* v_new, double* drho_new) {
+    const double R2 = 4.0 * h * h, vol = dx * dx * dx, sigma0 = orc_sigma0(dx, h), c02 = c0 * c0;
+    for (int64_t q = 0; q < m; ++q)
+        if (idx[q] < 0 || idx[q] >= n || kind[idx[q]] != 0) return -1;
+    unsigned char* ring = (unsigned char*)calloc((size_t)n, 1);
+    double* rho_re = (double*)malloc(sizeof(double) * (size_t)n);  /* re-initialised density */
+    double* rho_h = (double*)malloc(sizeof(double) * (size_t)n);   /* half-kicked density */
+    double* vk = (double*)malloc(sizeof(double) * 3 * (size_t)n);  /* kicked velocity */
+    for (int64_t q = 0; q < m; ++q) ring[idx[q]] |= 1u;
+    next_ring(n, pos, kind, R2, ring, 0); /* partners of the samples */
+    next_ring(n, pos, kind, R2, ring, 1); /* their partners */
+    /* re-initialisation and half kick of every fluid particle of the three rings */
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        if (!ring[i] || kind[i] != 0) continue;
+        rho_re[i] = reinit_rho(n, pos, rho, mat_id, mats, R2, h, sigma0, free_surface, 0, NULL, i);
+        rho_h[i] = rho_re[i] + 0.5 * dt * drho[i];
+    }
+    /* viscous and pressure accelerations, velocity kick: samples and their partners */
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(ring[i] & 3u) || kind[i] != 0) continue;
+        const orc_material* Mi = &mats[mat_id[i]];
+        const double p_i = c02 * (rho_h[i] - Mi->rho0);
+        double av[3] = {0, 0, 0}, ap[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double rv[3];
+            const double r2 = dist2(pos + 3 * i, pos + 3 * j, 0, NULL, rv);
+            if (!(r2 > 0.0 && r2 < R2)) continue;
+            const double r = sqrt(r2), dW = orc_dW(r, h);
+            double e[3];
+            for (int k = 0; k < 3; ++k) e[k] = rv[k] / r;
+            double eta, Vre, Vh, pstar, Ustar;
+            if (kind[j] == 0) {
+                const orc_material* Mj = &mats[mat_id[j]];
+                eta = (Mi->mu + Mj->mu > 0.0) ? 2.0 * Mi->mu * Mj->mu / (Mi->mu + Mj->mu) : 0.0;
+                Vre = Mj->rho0 * vol / rho_re[j];
+                Vh = Mj->rho0 * vol / rho_h[j];
+                const double p_j = c02 * (rho_h[j] - Mj->rho0);
+                orc_riemann(rho_h[i], -dot3(vel + 3 * i, e), p_i, rho_h[j], -dot3(vel + 3 * j, e), p_j, c0, &Ustar,
+                            &pstar);
+            } else {
+                eta = Mi->mu; /* READING: the wall takes the fluid's viscosity (Eq. 18) */
+                Vre = Vh = vol;
+                double UR, PR, rhoR;
+                orc_wall_riemann(rho_h[i], -dot3(nrm + 3 * j, vel + 3 * i), p_i, -dot3(nrm + 3 * j, vel + 3 * j),
+                                 -dot3(gravity, rv), Mi->rho0, c0, wall_pstar_printed, &UR, &PR, &rhoR, &Ustar,
+                                 &pstar);
+            }
+            const double cv = 2.0 * Vre / rho_re[i] * eta / r * dW, cp = -2.0 * Vh / rho_h[i] * pstar * dW;
+            for (int k = 0; k < 3; ++k) {
+                av[k] += cv * (vel[3 * i + k] - vel[3 * j + k]);
+                ap[k] += cp * e[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) vk[3 * i + k] = vel[3 * i + k] + dt * (ap[k] + av[k] + gravity[k]);
+    }
+    /* pass C of the samples, from the kicked velocities (walls keep theirs) */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        const orc_material* Mi = &mats[mat_id[i]];
+        const double p_i = c02 * (rho_h[i] - Mi->rho0);
+        double d = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double rv[3];
+            const double r2 = dist2(pos + 3 * i, pos + 3 * j, 0, NULL, rv);
+            if (!(r2 > 0.0 && r2 < R2)) continue;
+            const double r = sqrt(r2), dW = orc_dW(r, h);
+            double e[3];
+            for (int k = 0; k < 3; ++k) e[k] = rv[k] / r;
+            double pstar, Ustar;
+            const double UL = -dot3(vk + 3 * i, e);
+            if (kind[j] == 0) {
+                const orc_material* Mj = &mats[mat_id[j]];
+                const double p_j = c02 * (rho_h[j] - Mj->rho0);
+                orc_riemann(rho_h[i], UL, p_i, rho_h[j], -dot3(vk + 3 * j, e), p_j, c0, &Ustar, &pstar);
+                d += 2.0 * rho_h[i] * (Mj->rho0 * vol / rho_h[j]) * (Ustar - UL) * dW;
+            } else {
+                /* READING: wall interface velocity -U* n_w plus the fluid's tangential velocity */
+                const double* nw = nrm + 3 * j;
+                const double ULw = -dot3(nw, vk + 3 * i), uw = -dot3(nw, vel + 3 * j);
+                double UR, PR, rhoR;
+                orc_wall_riemann(rho_h[i], ULw, p_i, uw, -dot3(gravity, rv), Mi->rho0, c0, wall_pstar_printed, &UR,
+                                 &PR, &rhoR, &Ustar, &pstar);
+                d += 2.0 * rho_h[i] * vol * (Ustar - ULw) * dot3(nw, e) * dW;
+            }
+        }
+        drho_new[q] = d;
+        for (int k = 0; k < 3; ++k) v_new[3 * q + k] = vk[3 * i + k];
+    }
+    free(ring);
+    free(rho_re);
+    free(rho_h);
+    free(vk);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Physics-driven particle relaxation (Sec. 2.2).  Particles move under the
  * constant background pressure p0 (scale-free: p0 / rho0 = 1),

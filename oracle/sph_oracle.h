@@ -88,6 +88,15 @@ int orc_sample_ap(int64_t n, const double* pos, const double* vel, const double*
                   const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
                   double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed, double dt,
                   int periodic_mask, const double* extent, int64_t m, const int64_t* idx, double* ap);
+/* the first acoustic sub-step of an advection step for the fluid particles
+ * idx[0..m) (non-periodic cases): from the state at the step's start, or any
+ * part of it holding every particle within three support radii of each
+ * sample, the kicked velocities v_new[3m] (pass M with the held viscous term
+ * and g) and pass C's continuity rates drho_new[m].  -1 as orc_sample_vt. */
+int orc_sample_substep(int64_t n, const double* pos, const double* vel, const double* rho, const double* drho,
+                       const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
+                       double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed,
+                       double dt, int64_t m, const int64_t* idx, double* v_new, double* drho_new);
 /* expected cell order: key = linear cell index (x fastest) of
  * floor((x - origin)/w) per axis, clamped to the grid; particles sorted by
  * (key, id).  perm[k] = id at sorted position k; cell_start has ncell+1. */

@@ -10,7 +10,7 @@ step), never a state read back from the GPU:
   them beside the hot, turning gear) against the oracle's brute-force passes
   D, V and T;
 - with one acoustic sub-step per advection step, the velocity kick of pass M
-  against the oracle's sampled pressure pass;
+  and the continuity rate of pass C against the oracle's sampled sub-step;
 - and, at the same particle count, a property that holds at any size: a
   periodic lattice moving as a rigid whole keeps its velocity (Galilean
   invariance).
@@ -121,20 +121,23 @@ def test_gear_bath_2m_sampled_viscous_and_heat(sph, oracle):
     assert ea.max() <= 1e-5 and eT.max() <= 1e-5
 
 
-def test_gear_bath_2m_sampled_pressure_kick(sph, oracle):
-    # pass M of the first advection step, run with one acoustic sub-step per
-    # step: the velocities after it against v0 + dt (a_p + a_visc + g) from
-    # the oracle's brute-force passes (pressure: Eqs. 10-12 and 16-19 on the
-    # re-initialised densities; viscous: Eqs. 10, 18) for 32 oil particles,
-    # 16 beside the turning gear.  Bound: 1e-5 of the largest sampled
-    # velocity change, plus the FP32 rounding of the stored velocity
-    # (2^-24 |v|)
+def test_gear_bath_2m_sampled_first_substep(sph, oracle):
+    # passes M and C of the first advection step, run with one acoustic
+    # sub-step per step: the kicked velocities v0 + dt (a_p + a_visc + g) and
+    # the continuity rates of 32 oil particles (16 beside the turning gear)
+    # against the oracle's sampled sub-step (re-initialisation, viscous,
+    # half kick, pressure kick, continuity) on the generator's initial state,
+    # restricted to the particles within three support radii of the samples
+    # (all that the samples' results read).  Bounds: velocity 1e-5 of the
+    # largest sampled velocity change plus the FP32 rounding of the stored
+    # velocity (2^-24 |v|); rate 1e-5 of max(|ref|, the largest sampled rate)
+    from scipy.spatial import cKDTree
     case = W.gear_bath(dx=1e-3, omega=600.0)
     case.config = dict(case.config, max_substeps=1)
     ctx = _ctx(sph, case)
     ctx.sph_step(1)
     t1 = ctx.sph_get_info()["t"]
-    v1, x1 = ctx.sph_read_fields("vel"), ctx.sph_read_fields("pos")
+    v1, x1, d1 = ctx.sph_read_fields("vel"), ctx.sph_read_fields("pos"), ctx.sph_read_fields("drho")
     ctx.close()
     f, vel, rho = _initial_state(case)
     idx = _sample(f, 16, 22)
@@ -151,20 +154,25 @@ def test_gear_bath_2m_sampled_pressure_kick(sph, oracle):
                 for m in heated if mats[m]["k"] > 0] + [np.inf])
     dt = min(dt_ac, dt_ad, dt_T)
     assert t1 == pytest.approx(dt, rel=1e-6)
-    drho0 = np.zeros(len(rho))  # no continuity rate before the first step
-    ap = oracle.sample_ap(f["pos"], vel, rho, drho0, f["normal"], f["kind"], f["mat"], case.materials, cfg["dx"], h,
-                          cfg["free_surface"], cfg["gravity"], cfg["c0"], dt, idx)
-    av, _ = oracle.sample_vt(f["pos"], vel, rho, f["T"], f["kind"], f["mat"], case.materials, cfg["dx"], h,
-                             cfg["free_surface"], idx)
-    dv = dt * (ap + av + np.asarray(cfg["gravity"]))
-    v_ref = vel[idx] + dv
-    x_ref = f["pos"][idx] + 0.5 * dt * (vel[idx] + v_ref)
+    pos = f["pos"]
+    near = np.flatnonzero(cKDTree(pos[idx]).query(pos, distance_upper_bound=3.0 * case.support_radius() * (1 + 1e-9))[0]
+                          < np.inf)
+    drho0 = np.zeros(len(near))  # no continuity rate before the first step
+    v_ref, d_ref = oracle.sample_substep(pos[near], vel[near], rho[near], drho0, f["normal"][near], f["kind"][near],
+                                         f["mat"][near], mats, cfg["dx"], h, cfg["free_surface"], cfg["gravity"],
+                                         cfg["c0"], dt, np.searchsorted(near, idx))
+    dv = v_ref - vel[idx]
+    x_ref = pos[idx] + 0.5 * dt * (vel[idx] + v_ref)
     bound = 1e-5 * np.abs(dv).max() + 2.0 ** -24 * np.abs(v_ref)
     ev = np.abs(v1[idx] - v_ref)
-    print(f"SAMPLED_M dv_max={np.abs(dv).max():.3g} err/bound={np.max(ev / bound):.2e} "
-          f"err/dv_max={ev.max() / np.abs(dv).max():.2e} x={np.abs(x1[idx] - x_ref).max() / cfg['dx']:.2e}")
+    s_d = np.abs(d_ref).max()
+    ed = np.abs(d1[idx] - d_ref) / np.maximum(np.abs(d_ref), s_d)
+    print(f"SAMPLED_SUBSTEP ring={len(near)} dv_max={np.abs(dv).max():.3g} v err/bound={np.max(ev / bound):.2e} "
+          f"v err/dv_max={ev.max() / np.abs(dv).max():.2e} x={np.abs(x1[idx] - x_ref).max() / cfg['dx']:.2e} "
+          f"drho={ed.max():.2e} s_d={s_d:.3g}")
     assert np.all(ev <= bound)
     assert np.abs(x1[idx] - x_ref).max() <= 1e-5 * cfg["dx"]
+    assert s_d > 0.0 and ed.max() <= 1e-5
 
 
 def test_galilean_invariance_at_full_size(sph):

@@ -911,3 +911,48 @@ def test_sampled_pressure_pass_matches_the_stepper(oracle):
                               cfg["free_surface"], idx)
     assert np.allclose(av, av2[idx], rtol=1e-12, atol=1e-12 * np.abs(av2[idx]).max())
     assert np.allclose(dT, dT2[idx], rtol=1e-12, atol=1e-12 * np.abs(dT2[idx]).max())
+
+
+def test_sampled_substep_matches_the_stepper(oracle):
+    # the sampled first sub-step (passes D, V, M and C of the samples and of
+    # the rings they read) against the stepper's second advection step with
+    # one acoustic sub-step per step: its kicked velocities and its
+    # continuity rates, from the first step's state with the gear turned to
+    # omega t1; then the same from only the particles within three support
+    # radii of the samples (the part of the state the samples can read)
+    case = W.gear_bath(dx=5e-3, omega=600.0)
+    case.config = dict(case.config, max_substeps=1)
+    f = W.flatten(case)
+    sim = oracle.OracleSim(case)
+    sim.step(1)
+    t1 = sim.time()["t"]
+    pos, vel, rho, drho = (sim.field(k).copy() for k in ("pos", "vel", "rho", "drho"))
+    nrm = f["normal"].copy()
+    for b, B in case.bodies.items():
+        sel = f["body"] == b
+        c = np.asarray(B["center"], float)
+        pos[sel] = c + _rotate(B["axis"], B["omega"] * t1, f["pos"][sel] - c)
+        nrm[sel] = _rotate(B["axis"], B["omega"] * t1, f["normal"][sel])
+        vel[sel] = np.cross(B["omega"] * np.asarray(B["axis"], float), pos[sel] - c)
+    sim.step(1)
+    dt = sim.time()["t"] - t1
+    v2, d2 = sim.field("vel"), sim.field("drho")
+    fluid = np.flatnonzero(f["kind"] == 0)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(fluid, 12, replace=False))
+    cfg = case.config
+    h = cfg["h_over_dx"] * cfg["dx"]
+    args = (f["kind"], f["mat"], case.materials, cfg["dx"], h, cfg["free_surface"], cfg["gravity"], cfg["c0"], dt)
+    vn, dn = oracle.sample_substep(pos, vel, rho, drho, nrm, *args, idx)
+    assert np.abs(d2[idx]).max() > 0
+    assert np.allclose(vn, v2[idx], rtol=1e-12, atol=1e-12 * np.abs(v2[idx]).max())
+    assert np.allclose(dn, d2[idx], rtol=1e-12, atol=1e-12 * np.abs(d2[idx]).max())
+    # only the particles within three support radii of a sample
+    R = case.support_radius()
+    near = np.flatnonzero(cKDTree(pos[idx]).query(pos, distance_upper_bound=3.0 * R * (1 + 1e-9))[0] < np.inf)
+    where = np.searchsorted(near, idx)
+    kind_s, mat_s = f["kind"][near], f["mat"][near]
+    vs, ds = oracle.sample_substep(pos[near], vel[near], rho[near], drho[near], nrm[near], kind_s, mat_s,
+                                   *args[2:], where)
+    assert len(near) < len(pos) // 2
+    assert np.array_equal(vs, vn) and np.array_equal(ds, dn)
