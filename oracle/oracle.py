@@ -259,7 +259,8 @@ def sample_substep(pos, vel, rho, drho, nrm, kind, mat, materials, dx, h, free_s
     rc = lib().orc_sample_substep(n, *[_pd(a) for a in arr], kind.ctypes.data_as(PI), mat.ctypes.data_as(PI), mats,
                                   float(dx), float(h), int(free_surface), _pd(g), float(c0), int(wall_pstar_printed),
                                   float(dt), len(idx), idx.ctypes.data_as(PI64), _pd(v_new), _pd(d_new))
-    assert rc == 0, "sample_substep: an index is out of range or not a fluid particle"
+    assert rc == 0, "sample_substep: an index is out of range or not a fluid particle" if rc == -1 else \
+        "sample_substep: out of host memory"
     return v_new, d_new
 
 

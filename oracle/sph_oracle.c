@@ -967,7 +967,9 @@ static int64_t partners_of(int64_t n, const double* pos, double R2, int64_t i, i
         if (!(r2 > 0.0 && r2 < R2)) continue;
         if (k == *cap) {
             *cap = *cap ? 2 * *cap : 256;
-            *buf = (int64_t*)realloc(*buf, sizeof(int64_t) * (size_t)*cap);
+            int64_t* grown = (int64_t*)realloc(*buf, sizeof(int64_t) * (size_t)*cap);
+            if (!grown) abort(); /* test infrastructure: out of host memory ends the run */
+            *buf = grown;
         }
         (*buf)[k++] = j;
     }
@@ -997,6 +999,13 @@ int orc_sample_substep(int64_t n, const double* pos, const double* vel, const do
     double* rho_re = (double*)malloc(sizeof(double) * (size_t)n);  /* re-initialised density */
     double* rho_h = (double*)malloc(sizeof(double) * (size_t)n);   /* half-kicked density */
     double* vk = (double*)malloc(sizeof(double) * 3 * (size_t)n);  /* kicked velocity */
+    if (!ring || !rho_re || !rho_h || !vk) {
+        free(ring);
+        free(rho_re);
+        free(rho_h);
+        free(vk);
+        return -2;
+    }
     for (int64_t q = 0; q < m; ++q) ring[idx[q]] |= 1u;
     next_ring(n, pos, kind, R2, ring, 0); /* partners of the samples */
     next_ring(n, pos, kind, R2, ring, 1); /* their partners */

@@ -92,7 +92,8 @@ int orc_sample_ap(int64_t n, const double* pos, const double* vel, const double*
  * idx[0..m) (non-periodic cases): from the state at the step's start, or any
  * part of it holding every particle within three support radii of each
  * sample, the kicked velocities v_new[3m] (pass M with the held viscous term
- * and g) and pass C's continuity rates drho_new[m].  -1 as orc_sample_vt. */
+ * and g) and pass C's continuity rates drho_new[m].  -1 as orc_sample_vt,
+ * -2 if host memory runs out. */
 int orc_sample_substep(int64_t n, const double* pos, const double* vel, const double* rho, const double* drho,
                        const double* nrm, const int* kind, const int* mat_id, const orc_material* mats, double dx,
                        double h, int free_surface, const double* gravity, double c0, int wall_pstar_printed,
