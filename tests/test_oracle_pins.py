@@ -956,3 +956,35 @@ def test_sampled_substep_matches_the_stepper(oracle):
                                    *args[2:], where)
     assert len(near) < len(pos) // 2
     assert np.array_equal(vs, vn) and np.array_equal(ds, dn)
+
+
+def test_mirror_symmetry_of_the_step(oracle):
+    # the dam break mirrored about the tank's mid-plane x = c: every term of
+    # the step (Eqs. 10-19, 22) must map to its mirror image, so after three
+    # advection steps x -> 2c - x, v_x -> -v_x and rho, T unchanged (to FP64
+    # rounding of the mirrored coordinates); a sign or axis slip in any
+    # x-dependent term breaks it
+    case = W.dam_break(dx=10e-3)
+    cfg = case.config
+    c = cfg["origin"][0] + 0.5 * cfg["extent"][0]
+    mir = W.dam_break(dx=10e-3)
+    for b in mir.fluids + mir.solids:
+        b["pos"] = b["pos"].copy()
+        b["pos"][:, 0] = 2.0 * c - b["pos"][:, 0]
+    for b in mir.solids:
+        b["normal"] = b["normal"].copy()
+        b["normal"][:, 0] = -b["normal"][:, 0]
+    a, m = oracle.OracleSim(case), oracle.OracleSim(mir)
+    a.step(3)
+    m.step(3)
+    assert a.time()["t"] == pytest.approx(m.time()["t"], rel=1e-12)
+    fl = W.flatten(case)["kind"] == 0
+    pa, pm = a.field("pos")[fl], m.field("pos")[fl]
+    va, vm = a.field("vel")[fl], m.field("vel")[fl]
+    assert np.abs(va).max() > 1e-3
+    assert np.abs(pm[:, 0] - (2.0 * c - pa[:, 0])).max() < 1e-9 * cfg["dx"]
+    assert np.abs(pm[:, 1:] - pa[:, 1:]).max() < 1e-9 * cfg["dx"]
+    assert np.abs(vm[:, 0] + va[:, 0]).max() < 1e-9 * np.abs(va).max()
+    assert np.abs(vm[:, 1:] - va[:, 1:]).max() < 1e-9 * np.abs(va).max()
+    assert np.abs(m.field("rho")[fl] - a.field("rho")[fl]).max() < 1e-9
+    assert np.abs(m.field("T") - a.field("T")).max() < 1e-9
