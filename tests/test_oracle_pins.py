@@ -988,3 +988,46 @@ def test_mirror_symmetry_of_the_step(oracle):
     assert np.abs(vm[:, 1:] - va[:, 1:]).max() < 1e-9 * np.abs(va).max()
     assert np.abs(m.field("rho")[fl] - a.field("rho")[fl]).max() < 1e-9
     assert np.abs(m.field("T") - a.field("T")).max() < 1e-9
+
+
+def _mirror_x(case, c):
+    # the case mirrored about the plane x = c; a rotation about an axis along
+    # y turns the other way in the mirror image (omega -> -omega)
+    for b in case.fluids + case.solids:
+        b["pos"] = b["pos"].copy()
+        b["pos"][:, 0] = 2.0 * c - b["pos"][:, 0]
+    for b in case.solids:
+        b["normal"] = b["normal"].copy()
+        b["normal"][:, 0] = -b["normal"][:, 0]
+    for B in case.bodies.values():
+        assert B["axis"] == [0.0, 1.0, 0.0]
+        B["center"] = [2.0 * c - B["center"][0]] + list(B["center"][1:])
+        B["omega"] = -B["omega"]
+    return case
+
+
+def test_mirror_symmetry_with_a_turning_gear(oracle):
+    # the gear bath mirrored about the sump's mid-plane, the gear turning the
+    # other way: the wall velocities omega x (r - c) and the torque's cross
+    # product must follow, so after two steps the flow is the mirror image,
+    # the torque about the axis changes sign and the heat into the oil is the
+    # same
+    case = W.gear_bath(dx=5e-3, omega=600.0)
+    cfg = case.config
+    c = cfg["origin"][0] + 0.5 * cfg["extent"][0]
+    mir = _mirror_x(W.gear_bath(dx=5e-3, omega=600.0), c)
+    a, m = oracle.OracleSim(case), oracle.OracleSim(mir)
+    a.step(2)
+    m.step(2)
+    fl = W.flatten(case)["kind"] == 0
+    va, vm = a.field("vel")[fl], m.field("vel")[fl]
+    pa, pm = a.field("pos")[fl], m.field("pos")[fl]
+    assert np.abs(va).max() > 1.0
+    assert np.abs(vm[:, 0] + va[:, 0]).max() < 1e-9 * np.abs(va).max()
+    assert np.abs(vm[:, 1:] - va[:, 1:]).max() < 1e-9 * np.abs(va).max()
+    assert np.abs(pm[:, 0] - (2.0 * c - pa[:, 0])).max() < 1e-9 * cfg["dx"]
+    ta, tm = a.torque_heat(0), m.torque_heat(0)
+    assert abs(ta["torque_avg"]) > 0
+    assert tm["torque_avg"] == pytest.approx(-ta["torque_avg"], rel=1e-9)
+    assert tm["torque"] == pytest.approx(-ta["torque"], rel=1e-9)
+    assert tm["heat"] == pytest.approx(ta["heat"], rel=1e-9)
